@@ -339,6 +339,8 @@ static void sec_copy(sec *dst, const sec *src, const lev *g) {
  * finest width selects lossless storage (oracle-only, used by pins). */
 static int Wu(const cmgo_ctx *c, int l) { return c->P.b1 == 0 ? 0 : c->P.ku * (c->L - l) + c->P.b1; }
 static int Wr(const cmgo_ctx *c, int l) { return c->P.b2 == 0 ? 0 : c->P.kr * (c->L - l) + c->P.b2; }
+/* Table 1: u^ and t^ in fmgResidual carry (p+1)L + b1 bits */
+static int Wt(const cmgo_ctx *c) { return c->P.b1 == 0 ? 0 : c->P.ku * c->L + c->P.b1; }
 
 int cmgo_width(const cmgo_ctx *c, int which, int level) {
   return which == CMGO_U ? Wu(c, level) : Wr(c, level);
@@ -530,8 +532,8 @@ int cmgo_decode_solution(const cmgo_ctx *c, double *out) {
 }
 
 /* Algorithm 2 (fmgResidual): decode u^_L, t_L = f_L - A_L u^_L, r_L = round(t_L);
- * with no pre-smoothing the hierarchy t_l = R_(l+1) t_(l+1), r_l = round(t_l) is
- * formed from the unrounded t as well, to feed the cycle. */
+ * with no pre-smoothing the hierarchy t_l = R_(l+1) t_(l+1), r_l = round(t_l)
+ * feeds the cycle as well. */
 int cmgo_residual(cmgo_ctx *c) {
   int L = c->L, d = c->P.dim;
   lev g = mklev(d, L);
@@ -556,23 +558,28 @@ int cmgo_residual(cmgo_ctx *c) {
   free(uh);
   free(Au);
   int st = round_dense(&g, c->t, Wr(c, L), &c->r[L]);
-  if (c->P.nu1 == 0 && L > 1) {
-    double *tf = (double *)malloc((size_t)g.np * sizeof(double));
-    if (!tf) return setst(c, CMGO_ENOMEM);
-    memcpy(tf, c->t, (size_t)g.np * sizeof(double));
+  if (c->P.nu1 == 0 && L > 1 && st == CMGO_OK) {
+    /* Table 1 keeps t^ at (p+1)L + b1 bits in fmgResidual: every level of the
+     * restriction chain rounds t_l = R_(l+1) t_(l+1) to that width (here BFP
+     * blocks of that width) before r_l = round(t_l) is formed from it. */
+    sec tb;
+    lev gm = mklev(d, L);
+    if (sec_alloc(&tb, &gm) != CMGO_OK) return setst(c, CMGO_ENOMEM);
+    st = round_dense(&g, c->t, Wt(c), &tb);
     for (int l = L - 1; l >= 1 && st == CMGO_OK; l--) {
       lev gf = mklev(d, l + 1), gc = mklev(d, l);
       double *tc = (double *)malloc((size_t)gc.np * sizeof(double));
       if (!tc) {
-        free(tf);
-        return setst(c, CMGO_ENOMEM);
+        st = CMGO_ENOMEM;
+        break;
       }
-      restrict_(&gf, &gc, tf, tc, &cnt);
-      st = round_dense(&gc, tc, Wr(c, l), &c->r[l]);
-      free(tf);
-      tf = tc;
+      restrict_(&gf, &gc, tb.v, tc, &cnt);
+      st = round_dense(&gc, tc, Wt(c), &tb);
+      if (st == CMGO_OK) st = round_dense(&gc, tb.v, Wr(c, l), &c->r[l]);
+      free(tc);
     }
-    free(tf);
+    free(tb.v);
+    free(tb.e);
   }
   c->inexact += cnt;
   return setst(c, st);
