@@ -1,0 +1,343 @@
+"""Benchmark: compact FMG (Algorithm 3) DoF/s to discretization error on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+
+A step is one whole compact FMG solve (L = 1 .. L_max, N IR iterations per
+level) of the workload with its right-hand side already on the device.  Under
+torchrun each rank solves its own replica (weak scaling; the method has no
+exchange step across replicas).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compact-FMG DoF/s to discretization error"
+
+WORKLOADS = {
+    # name: (problem generator, L_max, description)
+    "poisson3d_2049": ("poisson3d_manufactured", 11,
+                       "3-D Poisson 2049^3 grid (2047^3 = 8.58e9 interior DoF), zero Dirichlet, "
+                       "RHS matrix-free from u=sin(pi x)sin(pi y)sin(pi z)(1+x^2yz)"),
+    "poisson3d_257": ("poisson3d_fourier", 8,
+                      "3-D Poisson 257^3 grid (255^3 DoF), RHS = 8 seeded Fourier modes"),
+    "poisson2d_257": ("poisson2d_manufactured", 8,
+                      "2-D Poisson 257^2 grid, u=sin(pi x)sin(pi y)(1+x^2 y)"),
+}
+DEFAULT_WORKLOAD = "poisson3d_2049"
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2511_19036_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel: str, workload: str):
+    """Per-DoF DRAM traffic of ``kernel`` from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    m_val = re.search(r"dram_bytes_per_dof:\s*([0-9.eE+-]+)", txt)
+    if not m_sha or not m_val or m_sha.group(1) != source_sha():
+        return None
+    return float(m_val.group(1))
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_fmg_rate(prob_name: str, L: int, cfg, max_seconds: float = 30.0):
+    """Time the CPU oracle's compact FMG on the same problem at level L.
+    Returns (DoF/s, seconds, dofs)."""
+    import cmg_problems
+    import oracle
+    prob = cmg_problems.make_problem(prob_name, L)
+    o = oracle.Oracle.for_problem(prob, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1, nu2=cfg.nu2,
+                                  omega=cfg.omega)
+    t0 = time.perf_counter()
+    o.fmg()
+    dt = time.perf_counter() - t0
+    dofs = ((1 << L) - 1) ** prob.dim
+    return dofs / dt, dt, dofs
+
+
+def pick_sample_level(prob_name: str, Lmax: int, dim: int) -> int:
+    # bounded oracle sample: about 10-30 s of host work
+    return min(Lmax, 7 if dim == 3 else 10)
+
+
+def run_reference(args, wl):
+    prob_name, Lmax, desc = WORKLOADS[wl]
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+    import oracle
+    oracle.build()
+    from paper_2511_19036_gb300.cmg_config import config_for
+    cfg = config_for(prob_name, Lmax)
+    dim = cfg.dim
+    Ls = pick_sample_level(prob_name, Lmax, dim)
+    for _ in range(args.warmup):
+        oracle_fmg_rate(prob_name, max(2, Ls - 2), cfg)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt, dofs = oracle_fmg_rate(prob_name, Ls, cfg)
+        rates.append(r)
+        times.append(dt)
+    value = statistics.median(rates)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    sample = "oracle compact FMG of the same problem at L_max=%d (%d DoF) per step" % (Ls, dofs)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl, "description": desc, "dim": dim, "L_max": Lmax, "b1": cfg.b1,
+                   "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": "V(%d,%d)" % (cfg.nu1, cfg.nu2),
+                   "omega": cfg.omega},
+        "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args, wl):
+    import numpy as np
+    import torch
+
+    import cmg_problems
+    from paper_2511_19036_gb300 import _build
+    _build.build()
+    from paper_2511_19036_gb300 import cmg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prob_name, Lmax, desc = WORKLOADS[wl]
+    prob = cmg_problems.make_problem(prob_name, Lmax, seed=rank)
+    cfg = cmg.config_for(prob_name, Lmax)
+    stream = torch.cuda.Stream()
+    solver = cmg.Solver(cfg, stream=stream, timing=True)
+    solver.set_rhs(prob.tables, prob.scale_exp)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        solver.fmg_solve()
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reports = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        reports.append(solver.fmg_solve())
+    ev1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    dofs = reports[0]["dofs"]
+    value = world * dofs / (ms_step * 1e-3)
+
+    # dominant kernel: the finest-level Jacobi sweep (events on the solver's stream)
+    sw_ms = sum(r["sweep_ms_total"] for r in reports)
+    sw_n = sum(r["sweep_launches"] for r in reports)
+    sw_bytes = sum(r["sweep_alg_bytes"] for r in reports)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = (sw_bytes / sw_n) / (sw_ms / sw_n * 1e-3) / 1e9 if sw_n and sw_ms > 0 else None
+    traffic_per_dof = read_traffic("k_sweep", wl)
+    roofline = {"kernel": "k_sweep<3> finest level" if cfg.dim == 3 else "k_sweep<2> finest level",
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": traffic_per_dof * dofs if traffic_per_dof else None,
+                "alg_bytes_per_launch": sw_bytes / sw_n if sw_n else None,
+                "avg_launch_ms": sw_ms / sw_n if sw_n else None,
+                "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
+    whole_frac = (reports[0]["alg_bytes"] / (ms_step * 1e-3) / 1e9) / peak
+
+    # end to end through the public API: H2D of the step's inputs (the RHS tables,
+    # from pinned memory) and D2H of the step's result (the compact solution).
+    tab_pinned = torch.from_numpy(np.ascontiguousarray(prob.tables)).pin_memory()
+    nb = [int(cmg.lib().cmg_section_blocks(cfg.dim, l)) for l in range(1, Lmax + 1)]
+    Wu = [cfg.k_u * (Lmax - l) + cfg.b1 for l in range(1, Lmax + 1)]
+    out_w = [torch.empty(nb[i] * Wu[i], dtype=torch.int32).pin_memory() for i in range(Lmax)]
+    out_e = [torch.empty(nb[i], dtype=torch.int8).pin_memory() for i in range(Lmax)]
+    h2d = tab_pinned.numel() * 4
+    d2h = sum(w.numel() * 4 + e.numel() for w, e in zip(out_w, out_e))
+    e2e_times = []
+    lib = cmg.lib()
+    for it in range(max(1, min(args.steps, 3))):
+        barrier()
+        t0 = time.perf_counter()
+        st = lib.cmg_set_rhs_separable(solver._h, prob.nterms, tab_pinned.data_ptr(), prob.scale_exp)
+        assert st == 0
+        solver.fmg_solve()
+        for l in range(1, Lmax + 1):
+            st = lib.cmg_get_section(solver._h, 0, l, out_w[l - 1].data_ptr(), out_e[l - 1].data_ptr())
+            assert st == 0
+        barrier()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # discretization-error check on sampled planes of the decoded solution
+    n = (1 << Lmax) - 1
+    h = 2.0 ** -Lmax
+    planes = [n // 4, n // 2, (3 * n) // 4] if cfg.dim == 3 else [0]
+    errs, norms = [], []
+    x = (np.arange(n) + 1.0) * h
+    for z in planes:
+        u = solver.decode_solution(z, 1).cpu().numpy()[0]
+        Y, X = np.meshgrid(x, x, indexing="ij")
+        ue = prob.exact_u(X, Y, (z + 1) * h) if cfg.dim == 3 else prob.exact_u(X, Y)
+        errs.append(float(np.max(np.abs(u - ue))))
+        norms.append(float(np.max(np.abs(ue))))
+    nodal_rel = max(errs) / max(norms)
+
+    if rank != 0:
+        return 0
+    # CPU oracle baseline on a bounded sample of the same problem (rank 0, N = 1)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+        import oracle
+        oracle.build()
+        Ls = pick_sample_level(prob_name, Lmax, cfg.dim)
+        r, dt, sdofs = oracle_fmg_rate(prob_name, Ls, cfg)
+        cpu = {"value": r, "unit": "DoF/s", "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+               "sample": "oracle compact FMG of the same problem at L_max=%d (%d DoF), %.1f s" % (Ls, sdofs, dt)}
+    launches = int(sum(r["launches"] for r in reports))
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": wl, "description": desc, "dim": cfg.dim, "L_max": Lmax, "dofs": dofs,
+                   "b1": cfg.b1, "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": "V(%d,%d)" % (cfg.nu1, cfg.nu2),
+                   "omega": cfg.omega, "l2": "working set larger than L2" if dofs > 1e8 else
+                   "working set fits L2 (state per step re-read from L2)",
+                   "parallelism": "replicas x%d" % world},
+        "bits_per_dof": reports[0]["persistent_bits"] / dofs,
+        "temp_bytes_per_dof": reports[0]["temp_bytes"] / dofs,
+        "alg_bytes_per_step": reports[0]["alg_bytes"],
+        "whole_solve_hbm_frac": whole_frac,
+        "nodal_rel_err_sampled": nodal_rel,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * dofs / e2e_s, "unit": "DoF/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args, args.workload)
+    return run_gpu(args, args.workload)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

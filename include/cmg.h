@@ -1,0 +1,176 @@
+/*
+ * cmg.h -- C ABI of the GB300 compact full multigrid (CMG) library.
+ *
+ * The library solves -Lap u = f with zero Dirichlet data on the unit square
+ * (d = 2) or cube (d = 3), P1 elements on the structured Kuhn triangulation,
+ * by compact FMG with iterative refinement (Algorithm 3 of "Multigrid with
+ * Linear Storage Complexity", Bauer, Kohl, McCormick, Tamstorf).  The solution
+ * u~, the residual r and the correction y~ live in the compact representation
+ * (Sec. 2, eq. compact-to-standard): one block-floating-point (BFP) section per
+ * grid level, widths regressive in the level (Table 1, eq. regressive).
+ *
+ * Conventions
+ *  - Every call returns a cmg_status; nothing aborts or throws across the ABI.
+ *    CUDA failures map to CMG_ECUDA, with the text in cmg_last_error().
+ *  - Work is enqueued on the CUDA stream given at creation (or per call for the
+ *    stand-alone codec).  Calls marked "synchronises" wait for that stream.
+ *  - Device pointers ("_dev") may come from any allocator (e.g. torch); the
+ *    library never frees memory it did not allocate.  Host pointers ("_host")
+ *    are read or written before the call returns.
+ *  - Levels: level l has 2^l - 1 interior nodes per axis (h = 2^-l); level 1 is
+ *    the coarsest (one unknown).  Dense level arrays are x-fastest, then y, z.
+ *
+ * BFP layout (bit-exact contract).  A section on level l stores each x-row of
+ * 2^l - 1 values as ceil((2^l - 1)/32) blocks of 32 (zero padded).  A block has
+ * one int8 exponent e and W uint32 words holding 32 W-bit two's-complement codes
+ * q_i (2 <= W <= 32, sign bit included): value_i = q_i * 2^(e-W+1); code i sits
+ * at bits [iW, iW+W) of the block's little-endian word stream.  e is the
+ * smallest integer with max|x| < 2^e, codes are rounded to nearest with ties to
+ * even (Sec. 4), and the exponent is raised by one when a code would reach
+ * 2^(W-1).  An all-zero block stores e = -128.  Blocks are ordered by row
+ * (x-block fastest, then y, then z); words are stored block after block.
+ */
+#ifndef CMG_H
+#define CMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CMG_OK = 0,
+  CMG_EINVAL = 1,       /* bad argument or parameter combination */
+  CMG_ENOMEM = 2,       /* device or host allocation failed */
+  CMG_ERANGE = 3,       /* exponent outside [-127, 127], or the exact integer
+                           arithmetic would need more than 62 bits */
+  CMG_ECUDA = 4,        /* CUDA runtime error (see cmg_last_error) */
+  CMG_ECORRUPT = 5,     /* code -2^(W-1) met while decoding */
+  CMG_ETIMEOUT = 6,     /* reserved: no call waits on a device flag */
+  CMG_EUNSUPPORTED = 7  /* valid request this build does not implement */
+} cmg_status;
+
+/* Parameters of Algorithm 3 with the precisions of Table 1 (P1: p = 1, m = 1).
+ * Intermediate arithmetic is exact (fixed-point integers on the GPU); values are
+ * rounded only where they are stored, as the paper's rounding rules prescribe. */
+typedef struct {
+  int dim;             /* 2 or 3 */
+  int L_max;           /* finest level, 1 <= L_max <= 14 */
+  int b1;              /* finest-level width of u~ (Table 1 b_1), 2..32 */
+  int b2;              /* finest-level width of r and y~ (Table 1 b_2), 2..32 */
+  int k_u;             /* regressive increment of u~, p + 1 = 2 */
+  int k_r;             /* regressive increment of r and y~, m = 1 */
+  int N_ir;            /* IR iterations per FMG level (Algorithm 3 N) */
+  int nu1, nu2;        /* pre-/post-smoothing Jacobi sweeps, nu1 >= 0, nu2 >= 1 */
+  int omega_num;       /* Jacobi weight omega = omega_num / 2^omega_log2den, */
+  int omega_log2den;   /* which must make omega / (2d) a dyadic rational */
+} cmg_params;
+
+/* Per-solve report filled by cmg_fmg_solve. */
+typedef struct {
+  double solve_ms;        /* device time of the whole FMG (CUDA events) */
+  int64_t dofs;           /* interior unknowns on the finest level */
+  int64_t launches;       /* kernels launched by the solve */
+  double alg_bytes;       /* algorithmic bytes moved by all kernels (model) */
+  double persistent_bits; /* compact u~, r, y~ (x2) storage at L_max, all levels,
+                             mantissas + exponents + padding */
+  double temp_bytes;      /* int64 temporaries (levels <= L_max-1) */
+  /* dominant kernel statistics (finest-level Jacobi sweep); valid when the
+   * context was created with timing enabled (cmg_set_timing). */
+  double sweep_ms_total;
+  int64_t sweep_launches;
+  double sweep_alg_bytes;
+  double resid_ms_total;
+  int64_t resid_launches;
+  double resid_alg_bytes;
+} cmg_report;
+
+/* Section selectors for cmg_get_section / cmg_set_section. */
+enum { CMG_SEC_U = 0, CMG_SEC_R = 1, CMG_SEC_RC = 2, CMG_SEC_Y = 3 };
+
+typedef struct cmg_ctx cmg_ctx;
+
+/* ---------------------------------------------------------------------------
+ * Stand-alone BFP codec (Sec. 6.1.3).  n values, blocks of 32 consecutive
+ * values (the last one zero padded).  words_dev: ceil(n/32)*W uint32,
+ * exps_dev: ceil(n/32) int8, all device memory owned by the caller.
+ * encode: CMG_EINVAL for W outside 2..32 or a non-finite input, CMG_ERANGE for
+ * an exponent outside [-127, 127].  decode: CMG_ECORRUPT for a code -2^(W-1)
+ * (the value is then written as if the code were valid).  Both synchronise
+ * the given stream to report data-dependent errors. */
+cmg_status cmg_encode(const double *x_dev, int64_t n, int W, uint32_t *words_dev,
+                      int8_t *exps_dev, void *cuda_stream);
+cmg_status cmg_decode(const uint32_t *words_dev, const int8_t *exps_dev, int64_t n, int W,
+                      double *x_dev, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Solver context: allocates the compact hierarchy for L_max (device memory it
+ * owns) and binds a CUDA stream (NULL = default stream).  Validation only,
+ * no device work: cmg_params_check. */
+cmg_status cmg_params_check(const cmg_params *p);
+cmg_status cmg_create(const cmg_params *p, void *cuda_stream, cmg_ctx **out);
+void cmg_destroy(cmg_ctx *ctx);
+const char *cmg_last_error(const cmg_ctx *ctx); /* never NULL */
+cmg_status cmg_set_timing(cmg_ctx *ctx, int enable); /* per-kernel CUDA events */
+
+/* Right-hand side (matrix-free, Sec. 5.1): F(x) = 2^scale_exp * sum_t prod_a
+ * T[t][a][i_a], with T an int32 table [nterms][dim][2^L_max - 1] sampled at the
+ * finest interior nodes (copied; the caller keeps ownership).  The nodal load
+ * f_L = h_L^d F is rounded to nearest-even on the grid 50 bits below the bound
+ * sum_t prod_a max|T[t][a]|.  |T| must be <= 2^30 and nterms <= 64. */
+cmg_status cmg_set_rhs_separable(cmg_ctx *ctx, int nterms, const int32_t *tables_host,
+                                 int scale_exp);
+
+/* Algorithm 3 end to end (coarse solve, then L = 2..L_max with N_ir IR
+ * iterations each).  Synchronises; fills *report when non-NULL. */
+cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *report);
+
+/* Individual steps of Algorithm 3 (unfused kernels), for step-wise checking.
+ * cmg_start: L = 1, u~_1 = round(f_1 / A_1).  cmg_prolongate: FMG level step
+ * (zero new section, widen the coarser ones by k_u bits).  cmg_residual:
+ * Algorithm 2 at the current level.  cmg_down(l): nu1 sweeps on level l from
+ * y~ = 0 and the restriction rc_(l-1) = round(R_l (rc_l - A_l y~_l)).
+ * cmg_coarse: y~_1 = round(rc_1 / A_1).  cmg_up(l): nu2 sweeps on level l with
+ * z_l = P_l w_(l-1), then w_l = y~_l + z_l.  cmg_correct: u~_l += y~_l (all l).
+ * cmg_vcycle: the down legs, coarse solve and up legs.  cmg_ir_iteration: one
+ * residual + cycle + correction with the fused production kernels. */
+cmg_status cmg_start(cmg_ctx *ctx);
+cmg_status cmg_prolongate(cmg_ctx *ctx);
+cmg_status cmg_residual(cmg_ctx *ctx);
+cmg_status cmg_down(cmg_ctx *ctx, int level);
+cmg_status cmg_coarse(cmg_ctx *ctx);
+cmg_status cmg_up(cmg_ctx *ctx, int level);
+cmg_status cmg_correct(cmg_ctx *ctx);
+cmg_status cmg_vcycle(cmg_ctx *ctx);
+cmg_status cmg_ir_iteration(cmg_ctx *ctx);
+int cmg_level(const cmg_ctx *ctx); /* current FMG level L (0 before cmg_start) */
+/* Waits for the stream and reports data-dependent errors (CMG_ERANGE, ...). */
+cmg_status cmg_sync(cmg_ctx *ctx);
+
+/* Section access (synchronises).  words_host: nblocks * W uint32 where W is
+ * cmg_section_width(); exps_host: nblocks int8.  cmg_set_section replaces a
+ * section (for checkpoint restore and step-wise checking). */
+int64_t cmg_section_blocks(int dim, int level);
+int cmg_section_width(const cmg_ctx *ctx, int which, int level);
+cmg_status cmg_get_section(cmg_ctx *ctx, int which, int level, uint32_t *words_host,
+                           int8_t *exps_host);
+cmg_status cmg_set_section(cmg_ctx *ctx, int which, int level, int W,
+                           const uint32_t *words_host, const int8_t *exps_host);
+
+/* Decode the standard representation u^_L (eq. compact-to-standard) of planes
+ * z0 .. z0+nz-1 of the current finest level into out_dev (nz * n * n doubles,
+ * dense, device memory of the caller; n = 2^L - 1; in 2-D z0 = 0, nz = 1).
+ * Values needing more than 53 bits are rounded to nearest by the conversion. */
+cmg_status cmg_decode_solution(cmg_ctx *ctx, int64_t z0, int64_t nz, double *out_dev);
+
+/* Checkpoint of the compact solution state (level, widths, sections).
+ * cmg_state_save with buf == NULL returns the needed size in *len. */
+cmg_status cmg_state_save(cmg_ctx *ctx, void *buf, size_t *len);
+cmg_status cmg_state_load(cmg_ctx *ctx, const void *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CMG_H */

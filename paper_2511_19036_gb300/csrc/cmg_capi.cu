@@ -1,0 +1,1092 @@
+// Host driver and C ABI of the compact FMG library (see include/cmg.h).
+//
+// The driver owns the compact hierarchy on the device and enqueues the kernels
+// of cmg_kernels.cu on one CUDA stream.  Nothing here computes method
+// arithmetic on the host except the load value at the single level-1 node and
+// the Jacobi constants; every sweep over a grid runs in a kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cmg.h"
+#include "cmg_device.cuh"
+#include "cmg_kernels.h"
+
+using namespace cmg;
+
+namespace {
+
+constexpr int MAXL = 14;
+constexpr int META_CAP = 1 << 20;  // ints in the metadata pool (2 per section write)
+
+struct SecBuf {
+  uint32_t *words = nullptr;
+  int8_t *exps = nullptr;
+  size_t cap_words = 0;  // allocated words
+  int W = 0;
+  int *meta = nullptr;   // current metadata slot
+};
+
+struct Level {
+  Geo g{};
+  SecBuf u, u_alt, r, rc, y[2];
+  int ycur = 0;
+  bool y_zero = true;
+  SecBuf t;                       // t^_l of the restriction chain (no pre-smoothing)
+  long long *uh = nullptr, *w = nullptr, *acc = nullptr;
+  short *uhg = nullptr, *wg = nullptr;  // per-block grids of u^_l and w_l
+  int *accmeta = nullptr;
+};
+
+struct KStat {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  double bytes = 0;
+  double ms = 0;
+  long long launches = 0;
+};
+
+}  // namespace
+
+struct cmg_ctx {
+  cmg_params P{};
+  cudaStream_t st = nullptr;
+  int L = 0;
+  Level lv[MAXL + 1];
+  int *meta_pool = nullptr;
+  int meta_next = 1;  // slot 0 stays all-zero: the metadata of an all-zero section
+  int *err = nullptr;
+  int32_t *tables = nullptr;
+  int nterms = 0, scale_exp = 0, fsh = 0;
+  std::vector<int32_t> tables_host;
+  bool have_rhs = false;
+  int uh_upto = 0;  // u^_1 .. u^_uh_upto agree with the current u~
+  int c_num2 = 0, c_exp2 = 0;  // omega / (2d) = c_num2 2^c_exp2 (level-free part)
+  std::string msg;
+  bool timing = false;
+  KStat st_sweep, st_resid;
+  long long launches = 0;
+  double alg_bytes = 0;
+};
+
+// ---------------------------------------------------------------- helpers
+static cmg_status fail(cmg_ctx *c, cmg_status s, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->msg = buf;
+  }
+  return s;
+}
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(ctx, CMG_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static Geo make_geo(int dim, int l) {
+  Geo g;
+  g.l = l;
+  g.n = (1 << l) - 1;
+  g.nz = dim == 3 ? g.n : 1;
+  g.nbx = (g.n + 31) / 32;
+  g.R = 32 * g.nbx;
+  g.nblocks = (long long)g.nz * g.n * g.nbx;
+  return g;
+}
+
+static int Wu(const cmg_ctx *c, int l, int L) { return c->P.k_u * (L - l) + c->P.b1; }
+static int Wr(const cmg_ctx *c, int l, int L) { return c->P.k_r * (L - l) + c->P.b2; }
+
+static int *new_meta(cmg_ctx *c) {
+  if (c->meta_next >= META_CAP / 2) return nullptr;
+  return c->meta_pool + 2 * (c->meta_next++);
+}
+
+static int bitlen_int(int v) {
+  int b = 0;
+  while (v) {
+    b++;
+    v >>= 1;
+  }
+  return b;
+}
+
+// Jacobi factor on level l: c_l = omega / (2d h_l^(d-2)) = c_num 2^c_exp
+static void jacobi_factor(const cmg_ctx *c, int l, int &num, int &ex, int &bits) {
+  num = c->c_num2;
+  ex = c->c_exp2 + (c->P.dim - 2) * l;
+  bits = bitlen_int(num);
+}
+
+static Sec sec_of(const SecBuf &b) {
+  Sec s;
+  s.words = b.words;
+  s.exps = b.exps;
+  s.W = b.W;
+  s.meta = b.meta;
+  return s;
+}
+
+static Tmp tmp_of(long long *v, short *gr, int *meta) {
+  Tmp t;
+  t.v = v;
+  t.gr = gr;
+  t.meta = meta;
+  return t;
+}
+
+static cmg_status launched(cmg_ctx *ctx, double bytes) {
+  ctx->launches++;
+  ctx->alg_bytes += bytes;
+  CU(cudaGetLastError());
+  return CMG_OK;
+}
+
+static double sec_bytes(const Geo &g, int W) { return (double)g.nblocks * (4.0 * W + 1.0); }
+static double tmp_bytes(const Geo &g) { return 8.0 * (double)g.nz * g.n * g.n; }
+
+static void ev_begin(cmg_ctx *c, KStat &k) {
+  if (!c->timing) return;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, c->st);
+  k.ev.push_back({a, b});
+}
+
+static void ev_end(cmg_ctx *c, KStat &k, double bytes) {
+  k.launches++;
+  k.bytes += bytes;
+  if (!c->timing) return;
+  cudaEventRecord(k.ev.back().second, c->st);
+}
+
+static void ev_collect(KStat &k) {
+  for (auto &p : k.ev) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) k.ms += ms;
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  k.ev.clear();
+}
+
+static void stat_reset(KStat &k) {
+  ev_collect(k);
+  k.ms = 0;
+  k.bytes = 0;
+  k.launches = 0;
+}
+
+// ---------------------------------------------------------------- validation
+extern "C" cmg_status cmg_params_check(const cmg_params *p) {
+  if (!p) return CMG_EINVAL;
+  if (p->dim != 2 && p->dim != 3) return CMG_EINVAL;
+  if (p->L_max < 1 || p->L_max > MAXL) return CMG_EINVAL;
+  if (p->b1 < 2 || p->b2 < 2 || p->k_u < 0 || p->k_r < 0) return CMG_EINVAL;
+  if (p->k_u * (p->L_max - 1) + p->b1 > 32 || p->k_r * (p->L_max - 1) + p->b2 > 32) return CMG_ERANGE;
+  if (p->N_ir < 1 || p->nu1 < 0 || p->nu2 < 1 || p->nu1 > 64 || p->nu2 > 64) return CMG_EINVAL;
+  // without pre-smoothing the restriction chain carries t^ at (p+1)L + b1 bits
+  if (p->nu1 == 0 && p->k_u * p->L_max + p->b1 > 32) return CMG_ERANGE;
+  if (p->omega_num <= 0 || p->omega_log2den < 0 || p->omega_log2den > 30) return CMG_EINVAL;
+  if (p->dim == 3 && p->omega_num % 3 != 0) return CMG_EINVAL;  // omega/6 must be dyadic
+  // keep the Jacobi numerator small (it widens the exact integers by its bit length)
+  int num = p->dim == 3 ? p->omega_num / 3 : p->omega_num;
+  while (num % 2 == 0) num /= 2;
+  if (num >= (1 << 10)) return CMG_EINVAL;
+  return CMG_OK;
+}
+
+// ---------------------------------------------------------------- lifetime
+static cmg_status alloc_sec(cmg_ctx *ctx, SecBuf &b, const Geo &g, int Wmax) {
+  b.cap_words = (size_t)g.nblocks * Wmax;
+  CU(cudaMalloc(&b.words, b.cap_words * sizeof(uint32_t)));
+  CU(cudaMalloc(&b.exps, (size_t)g.nblocks));
+  b.W = Wmax;
+  b.meta = ctx->meta_pool;  // slot 0: empty
+  return CMG_OK;
+}
+
+static void free_sec(SecBuf &b) {
+  cudaFree(b.words);
+  cudaFree(b.exps);
+  b.words = nullptr;
+  b.exps = nullptr;
+}
+
+extern "C" void cmg_destroy(cmg_ctx *ctx) {
+  if (!ctx) return;
+  for (int l = 1; l <= MAXL; l++) {
+    Level &v = ctx->lv[l];
+    free_sec(v.u);
+    free_sec(v.u_alt);
+    free_sec(v.r);
+    free_sec(v.rc);
+    free_sec(v.y[0]);
+    free_sec(v.y[1]);
+    free_sec(v.t);
+    cudaFree(v.uh);
+    cudaFree(v.w);
+    cudaFree(v.acc);
+    cudaFree(v.uhg);
+    cudaFree(v.wg);
+  }
+  stat_reset(ctx->st_sweep);
+  stat_reset(ctx->st_resid);
+  cudaFree(ctx->meta_pool);
+  cudaFree(ctx->err);
+  cudaFree(ctx->tables);
+  delete ctx;
+}
+
+extern "C" cmg_status cmg_create(const cmg_params *p, void *stream, cmg_ctx **out) {
+  if (!out) return CMG_EINVAL;
+  *out = nullptr;
+  cmg_status s = cmg_params_check(p);
+  if (s != CMG_OK) return s;
+  cmg_ctx *ctx = new (std::nothrow) cmg_ctx();
+  if (!ctx) return CMG_ENOMEM;
+  ctx->P = *p;
+  ctx->st = (cudaStream_t)stream;
+  {
+    int num = p->dim == 3 ? p->omega_num / 3 : p->omega_num;
+    int ex = -p->omega_log2den - (p->dim == 3 ? 1 : 2);  // 2-D: /4; 3-D: /6 = /3 /2
+    while (num % 2 == 0) {
+      num /= 2;
+      ex++;
+    }
+    ctx->c_num2 = num;
+    ctx->c_exp2 = ex;
+  }
+  cmg_status r = CMG_OK;
+  auto chk = [&](cudaError_t e) {
+    if (e != cudaSuccess && r == CMG_OK) r = fail(ctx, e == cudaErrorMemoryAllocation ? CMG_ENOMEM : CMG_ECUDA,
+                                                  "allocation: %s", cudaGetErrorString(e));
+  };
+  chk(cudaMalloc(&ctx->meta_pool, META_CAP * sizeof(int)));
+  chk(cudaMalloc(&ctx->err, 8 * sizeof(int)));
+  if (r == CMG_OK) {
+    chk(cudaMemsetAsync(ctx->meta_pool, 0, META_CAP * sizeof(int), ctx->st));
+    chk(cudaMemsetAsync(ctx->err, 0, 8 * sizeof(int), ctx->st));
+  }
+  for (int l = 1; l <= p->L_max && r == CMG_OK; l++) {
+    Level &v = ctx->lv[l];
+    v.g = make_geo(p->dim, l);
+    const Geo &g = v.g;
+    int wu = Wu(ctx, l, p->L_max), wr = Wr(ctx, l, p->L_max);
+    if ((r = alloc_sec(ctx, v.u, g, wu)) != CMG_OK) break;
+    if (l < p->L_max && (r = alloc_sec(ctx, v.u_alt, g, wu)) != CMG_OK) break;
+    if ((r = alloc_sec(ctx, v.r, g, wr)) != CMG_OK) break;
+    if (l < p->L_max && (r = alloc_sec(ctx, v.rc, g, wr)) != CMG_OK) break;
+    if ((r = alloc_sec(ctx, v.y[0], g, wr)) != CMG_OK) break;
+    if ((r = alloc_sec(ctx, v.y[1], g, wr)) != CMG_OK) break;
+    if (p->nu1 == 0 && (r = alloc_sec(ctx, v.t, g, p->k_u * p->L_max + p->b1)) != CMG_OK) break;
+    if (l < p->L_max || l == 1) {
+      size_t nt = (size_t)g.nz * g.n * g.R;
+      chk(cudaMalloc(&v.uh, nt * 8));
+      chk(cudaMalloc(&v.w, nt * 8));
+      chk(cudaMalloc(&v.acc, nt * 8));
+      chk(cudaMalloc(&v.uhg, (size_t)g.nblocks * sizeof(short)));
+      chk(cudaMalloc(&v.wg, (size_t)g.nblocks * sizeof(short)));
+      if (r == CMG_OK) {
+        chk(cudaMemsetAsync(v.acc, 0, nt * 8, ctx->st));
+        chk(cudaMemsetAsync(v.uh, 0, nt * 8, ctx->st));
+        chk(cudaMemsetAsync(v.w, 0, nt * 8, ctx->st));
+      }
+    }
+  }
+  if (r != CMG_OK) {
+    cmg_destroy(ctx);
+    return r;
+  }
+  *out = ctx;
+  return CMG_OK;
+}
+
+extern "C" const char *cmg_last_error(const cmg_ctx *ctx) { return ctx ? ctx->msg.c_str() : "null context"; }
+
+extern "C" cmg_status cmg_set_timing(cmg_ctx *ctx, int enable) {
+  if (!ctx) return CMG_EINVAL;
+  ctx->timing = enable != 0;
+  return CMG_OK;
+}
+
+extern "C" int cmg_level(const cmg_ctx *ctx) { return ctx ? ctx->L : -1; }
+
+extern "C" int64_t cmg_section_blocks(int dim, int level) {
+  if ((dim != 2 && dim != 3) || level < 1 || level > MAXL) return -1;
+  return make_geo(dim, level).nblocks;
+}
+
+// ---------------------------------------------------------------- right-hand side
+extern "C" cmg_status cmg_set_rhs_separable(cmg_ctx *ctx, int nterms, const int32_t *tab, int scale_exp) {
+  if (!ctx || !tab || nterms < 1 || nterms > 64) return CMG_EINVAL;
+  const int d = ctx->P.dim, n1 = (1 << ctx->P.L_max) - 1;
+  size_t cnt = (size_t)nterms * d * n1;
+  unsigned __int128 bound = 0;
+  for (int t = 0; t < nterms; t++) {
+    unsigned __int128 prod = 1;
+    for (int a = 0; a < d; a++) {
+      long long m = 0;
+      for (int i = 0; i < n1; i++) {
+        long long v = std::llabs((long long)tab[((size_t)t * d + a) * n1 + i]);
+        if (v > (1ll << 30)) return fail(ctx, CMG_EINVAL, "table entry above 2^30");
+        m = std::max(m, v);
+      }
+      prod *= (unsigned __int128)m;
+    }
+    bound += prod;
+  }
+  int B = 0;
+  for (unsigned __int128 t = bound; t; t >>= 1) B++;
+  cudaFree(ctx->tables);
+  ctx->tables = nullptr;
+  CU(cudaMalloc(&ctx->tables, cnt * sizeof(int32_t)));
+  CU(cudaMemcpyAsync(ctx->tables, tab, cnt * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  ctx->tables_host.assign(tab, tab + cnt);
+  ctx->nterms = nterms;
+  ctx->scale_exp = scale_exp;
+  ctx->fsh = B > 50 ? B - 50 : 0;
+  ctx->have_rhs = true;
+  return CMG_OK;
+}
+
+// F_q at the level-1 node (coordinates 1/2): exact table product, RNE shift
+static long long rhs_level1(const cmg_ctx *c) {
+  const int d = c->P.dim, n1 = (1 << c->P.L_max) - 1, idx = (1 << (c->P.L_max - 1)) - 1;
+  __int128 F = 0;
+  for (int t = 0; t < c->nterms; t++) {
+    __int128 p = 1;
+    for (int a = 0; a < d; a++) p *= (__int128)c->tables_host[((size_t)t * d + a) * n1 + idx];
+    F += p;
+  }
+  int s = c->fsh;
+  if (s <= 0) return (long long)F;
+  __int128 q = F >> s, rem = F - (q << s), half = (__int128)1 << (s - 1);
+  if (rem > half || (rem == half && (q & 1))) q += 1;
+  return (long long)q;
+}
+
+// ---------------------------------------------------------------- building blocks
+static cmg_status set_zero_section(cmg_ctx *ctx, SecBuf &b, const Geo &g, int W) {
+  b.W = W;
+  b.meta = ctx->meta_pool;
+  CU(cudaMemsetAsync(b.exps, 0x80, (size_t)g.nblocks, ctx->st));
+  CU(cudaMemsetAsync(b.words, 0, (size_t)g.nblocks * W * sizeof(uint32_t), ctx->st));
+  return CMG_OK;
+}
+
+static cmg_status fresh_tmp_meta(cmg_ctx *ctx, int *&slot) {
+  slot = new_meta(ctx);
+  if (!slot) return fail(ctx, CMG_ERANGE, "metadata pool exhausted");
+  return CMG_OK;
+}
+
+static cmg_status fresh_meta(cmg_ctx *ctx, SecBuf &b) {
+  b.meta = new_meta(ctx);
+  if (!b.meta) return fail(ctx, CMG_ERANGE, "metadata pool exhausted");
+  return CMG_OK;
+}
+
+static cmg_status run_chain(cmg_ctx *ctx, int upto) {
+  for (int l = 1; l <= upto; l++) {
+    Level &v = ctx->lv[l];
+    ChainArgs a{};
+    a.g = v.g;
+    a.gc = l > 1 ? ctx->lv[l - 1].g : v.g;
+    a.u = sec_of(v.u);
+    a.has_uhc = l > 1;
+    if (l > 1) a.uhc = tmp_of(ctx->lv[l - 1].uh, ctx->lv[l - 1].uhg, nullptr);
+    a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
+    a.err = ctx->err;
+    launch_chain(ctx->P.dim, a, ctx->st);
+    cmg_status s = launched(ctx, sec_bytes(v.g, v.u.W) + tmp_bytes(v.g) + (l > 1 ? tmp_bytes(a.gc) : 0));
+    if (s) return s;
+  }
+  return CMG_OK;
+}
+
+static Level &LV(cmg_ctx *c, int l) { return c->lv[l]; }
+
+// rc section of level l at the current FMG level
+static SecBuf &rc_of(cmg_ctx *c, int l) {
+  if (l == c->L) return c->lv[l].r;
+  if (c->P.nu1 == 0) return c->lv[l].r;
+  return c->lv[l].rc;
+}
+
+static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
+  const int L = ctx->L, d = ctx->P.dim;
+  if (ctx->uh_upto < L - 1) {
+    cmg_status s = run_chain(ctx, L - 1);
+    if (s) return s;
+    ctx->uh_upto = L - 1;
+  }
+  Level &v = LV(ctx, L);
+  ResidArgs a{};
+  a.g = v.g;
+  a.gc = L > 1 ? LV(ctx, L - 1).g : v.g;
+  a.u = sec_of(v.u);
+  a.has_uhc = L > 1;
+  if (L > 1) a.uhc = tmp_of(LV(ctx, L - 1).uh, LV(ctx, L - 1).uhg, nullptr);
+  a.tables = ctx->tables;
+  a.nterms = ctx->nterms;
+  a.n1max = (1 << ctx->P.L_max) - 1;
+  a.Lmax = ctx->P.L_max;
+  a.fsh = ctx->fsh;
+  a.Gf = ctx->scale_exp + ctx->fsh - d * L;
+  v.r.W = Wr(ctx, L, L);
+  cmg_status s = fresh_meta(ctx, v.r);
+  if (s) return s;
+  a.r_out = sec_of(v.r);
+  a.first_sweep = first_sweep;
+  jacobi_factor(ctx, L, a.c_num, a.c_exp, a.cbits);
+  if (first_sweep) {
+    SecBuf &y = v.y[0];
+    y.W = Wr(ctx, L, L);
+    if ((s = fresh_meta(ctx, y))) return s;
+    a.y_out = sec_of(y);
+    v.ycur = 0;
+    v.y_zero = false;
+  }
+  // without pre-smoothing, t^ (Table 1 width (p+1)L + b1) feeds the restriction chain
+  const bool chain = ctx->P.nu1 == 0 && L > 1;
+  const int Wt = ctx->P.k_u * L + ctx->P.b1;
+  a.write_t = chain;
+  if (chain) {
+    v.t.W = Wt;
+    if ((s = fresh_meta(ctx, v.t))) return s;
+    a.t_out = sec_of(v.t);
+  }
+  a.err = ctx->err;
+  double bytes = sec_bytes(v.g, v.u.W) + (L > 1 ? tmp_bytes(a.gc) : 0) + sec_bytes(v.g, v.r.W) +
+                 (first_sweep ? sec_bytes(v.g, v.r.W) : 0) + (chain ? sec_bytes(v.g, Wt) : 0);
+  ev_begin(ctx, ctx->st_resid);
+  launch_residual(d, a, ctx->st);
+  ev_end(ctx, ctx->st_resid, bytes);
+  if ((s = launched(ctx, bytes))) return s;
+  if (chain) {  // t^_l = round(R t^_(l+1)), r_l = round(t^_l) (Algorithm 2)
+    for (int l = L; l >= 2; l--) {
+      Level &f = LV(ctx, l), &c = LV(ctx, l - 1);
+      RestrictArgs ra{};
+      ra.g = f.g;
+      ra.gc = c.g;
+      ra.has_y = 0;
+      ra.rc = sec_of(f.t);
+      if ((s = fresh_tmp_meta(ctx, c.accmeta))) return s;
+      ra.acc = tmp_of(c.acc, nullptr, c.accmeta);
+      ra.err = ctx->err;
+      launch_restrict(d, ra, ctx->st);
+      if ((s = launched(ctx, sec_bytes(f.g, Wt) + 2 * tmp_bytes(c.g)))) return s;
+      AccArgs b{};
+      b.g = c.g;
+      b.acc = tmp_of(c.acc, nullptr, c.accmeta);
+      c.r.W = Wr(ctx, l - 1, L);
+      if ((s = fresh_meta(ctx, c.r))) return s;
+      b.r_out = sec_of(c.r);
+      b.chain = 1;
+      c.t.W = Wt;
+      if ((s = fresh_meta(ctx, c.t))) return s;
+      b.t_out = sec_of(c.t);
+      jacobi_factor(ctx, l - 1, b.c_num, b.c_exp, b.cbits);
+      b.err = ctx->err;
+      launch_acc_encode(d, b, ctx->st);
+      if ((s = launched(ctx, 2 * tmp_bytes(c.g) + sec_bytes(c.g, c.r.W) + sec_bytes(c.g, Wt)))) return s;
+    }
+  }
+  return CMG_OK;
+}
+
+// one Jacobi sweep on level l reading y[ycur] (unless y_zero), writing y[1-ycur]
+struct SweepOpts {
+  bool has_z = false, write_y = true, corr = false, write_w = false, write_uh = false;
+};
+
+static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
+  const int L = ctx->L, d = ctx->P.dim;
+  Level &v = LV(ctx, l);
+  SweepArgs a{};
+  a.g = v.g;
+  a.gc = l > 1 ? LV(ctx, l - 1).g : v.g;
+  a.has_y = !v.y_zero;
+  a.has_z = o.has_z;
+  a.write_y = o.write_y;
+  a.corr = o.corr;
+  a.write_w = o.write_w;
+  a.write_uh = o.write_uh;
+  a.has_uhc = l > 1;
+  a.Wy = Wr(ctx, l, L);
+  if (a.has_y) a.y_in = sec_of(v.y[v.ycur]);
+  a.rc = sec_of(rc_of(ctx, l));
+  cmg_status s;
+  SecBuf &yo = v.y[1 - v.ycur];
+  if (o.write_y) {
+    yo.W = a.Wy;
+    if ((s = fresh_meta(ctx, yo))) return s;
+    a.y_out = sec_of(yo);
+  }
+  if (o.corr) {
+    a.u_in = sec_of(v.u);
+    SecBuf un = v.u;  // in place: each block is read and rewritten by one warp
+    un.W = Wu(ctx, l, L);
+    if ((s = fresh_meta(ctx, un))) return s;
+    a.u_out = sec_of(un);
+    v.u.meta = un.meta;
+    v.u.W = un.W;
+  }
+  if (o.has_z) a.wc = tmp_of(LV(ctx, l - 1).w, LV(ctx, l - 1).wg, nullptr);
+  if (l > 1) a.uhc = tmp_of(LV(ctx, l - 1).uh, LV(ctx, l - 1).uhg, nullptr);
+  if (o.write_w) a.w_out = tmp_of(v.w, v.wg, nullptr);
+  if (o.write_uh) a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
+  jacobi_factor(ctx, l, a.c_num, a.c_exp, a.cbits);
+  a.err = ctx->err;
+  double bytes = (a.has_y ? sec_bytes(v.g, a.Wy) : 0) + sec_bytes(v.g, a.rc.W) +
+                 (o.has_z ? tmp_bytes(a.gc) : 0) + (o.write_y ? sec_bytes(v.g, a.Wy) : 0) +
+                 (o.corr ? 2 * sec_bytes(v.g, a.u_out.W) : 0) + (o.write_w ? tmp_bytes(v.g) : 0) +
+                 (o.write_uh ? tmp_bytes(v.g) + tmp_bytes(a.gc) : 0);
+  const bool finest = (l == L);
+  if (finest) ev_begin(ctx, ctx->st_sweep);
+  launch_sweep(d, a, ctx->st);
+  if (finest) ev_end(ctx, ctx->st_sweep, bytes);
+  if ((s = launched(ctx, bytes))) return s;
+  if (o.write_y) {
+    v.ycur = 1 - v.ycur;
+    v.y_zero = false;
+  }
+  return CMG_OK;
+}
+
+static cmg_status do_restrict(cmg_ctx *ctx, int l, bool first_sweep_below) {
+  const int L = ctx->L, d = ctx->P.dim;
+  Level &v = LV(ctx, l), &c = LV(ctx, l - 1);
+  RestrictArgs a{};
+  a.g = v.g;
+  a.gc = c.g;
+  a.has_y = !v.y_zero;
+  a.y = sec_of(v.y[v.ycur]);
+  a.rc = sec_of(rc_of(ctx, l));
+  {
+    cmg_status s1 = fresh_tmp_meta(ctx, c.accmeta);
+    if (s1) return s1;
+  }
+  a.acc = tmp_of(c.acc, nullptr, c.accmeta);
+  a.err = ctx->err;
+  launch_restrict(d, a, ctx->st);
+  cmg_status s = launched(ctx, sec_bytes(v.g, a.y.W) + sec_bytes(v.g, a.rc.W) + 2 * tmp_bytes(c.g));
+  if (s) return s;
+  AccArgs b{};
+  b.g = c.g;
+  b.acc = tmp_of(c.acc, nullptr, c.accmeta);
+  c.rc.W = Wr(ctx, l - 1, L);
+  if ((s = fresh_meta(ctx, c.rc))) return s;
+  b.r_out = sec_of(c.rc);
+  b.first_sweep = first_sweep_below;
+  if (first_sweep_below) {
+    SecBuf &y = c.y[0];
+    y.W = Wr(ctx, l - 1, L);
+    if ((s = fresh_meta(ctx, y))) return s;
+    b.y_out = sec_of(y);
+    c.ycur = 0;
+    c.y_zero = false;
+  }
+  b.chain = 0;
+  jacobi_factor(ctx, l - 1, b.c_num, b.c_exp, b.cbits);
+  b.err = ctx->err;
+  launch_acc_encode(d, b, ctx->st);
+  return launched(ctx, 2 * tmp_bytes(c.g) + sec_bytes(c.g, c.rc.W) * (first_sweep_below ? 2 : 1));
+}
+
+static cmg_status do_coarse(cmg_ctx *ctx, bool start, bool corr) {
+  Level &v = LV(ctx, 1);
+  CoarseArgs a{};
+  a.dim = ctx->P.dim;
+  a.mode_start = start;
+  a.err = ctx->err;
+  cmg_status s;
+  if (start) {
+    a.f1 = rhs_level1(ctx);
+    a.Gf1 = ctx->scale_exp + ctx->fsh - ctx->P.dim * 1;
+    v.u.W = Wu(ctx, 1, 1);
+    if ((s = fresh_meta(ctx, v.u))) return s;
+    a.u_out = sec_of(v.u);
+    a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
+  } else {
+    a.rc = sec_of(rc_of(ctx, 1));
+    SecBuf &y = v.y[0];
+    y.W = Wr(ctx, 1, ctx->L);
+    if ((s = fresh_meta(ctx, y))) return s;
+    a.y_out = sec_of(y);
+    v.ycur = 0;
+    v.y_zero = false;
+    a.corr = corr;
+    if (corr) {
+      a.u_in = sec_of(v.u);
+      SecBuf &ua = v.u_alt;  // level 1 < L_max here, so the spare buffer exists
+      ua.W = Wu(ctx, 1, ctx->L);
+      if ((s = fresh_meta(ctx, ua))) return s;
+      a.u_out = sec_of(ua);
+    }
+    a.w_out = tmp_of(v.w, v.wg, nullptr);
+    if (corr) a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
+  }
+  launch_coarse(a, ctx->st);
+  if ((s = launched(ctx, 64))) return s;
+  if (!start && corr) std::swap(v.u, v.u_alt);
+  return CMG_OK;
+}
+
+// ---------------------------------------------------------------- steps
+static cmg_status need(cmg_ctx *ctx, bool cond, const char *what) {
+  return cond ? CMG_OK : fail(ctx, CMG_EINVAL, "%s", what);
+}
+
+extern "C" cmg_status cmg_start(cmg_ctx *ctx) {
+  if (!ctx) return CMG_EINVAL;
+  cmg_status s = need(ctx, ctx->have_rhs, "no right-hand side set");
+  if (s) return s;
+  ctx->meta_next = 1;
+  CU(cudaMemsetAsync(ctx->meta_pool + 2 * ctx->meta_next, 0,
+                     (size_t)(META_CAP - 2 * ctx->meta_next) * sizeof(int), ctx->st));
+  CU(cudaMemsetAsync(ctx->err, 0, 8 * sizeof(int), ctx->st));
+  for (int l = 1; l <= ctx->P.L_max; l++) {
+    Level &v = LV(ctx, l);
+    v.u.meta = v.r.meta = v.rc.meta = v.y[0].meta = v.y[1].meta = ctx->meta_pool;
+    v.y_zero = true;
+  }
+  ctx->L = 1;
+  s = do_coarse(ctx, true, false);
+  ctx->uh_upto = 1;
+  return s;
+}
+
+extern "C" cmg_status cmg_prolongate(cmg_ctx *ctx) {
+  if (!ctx) return CMG_EINVAL;
+  cmg_status s = need(ctx, ctx->L >= 1 && ctx->L < ctx->P.L_max, "cannot prolongate at this level");
+  if (s) return s;
+  const int L = ctx->L + 1;
+  // widen every coarser section by k_u bits (exact: appended zero bits)
+  for (int l = 1; l < L; l++) {
+    Level &v = LV(ctx, l);
+    int Wn = Wu(ctx, l, L);
+    if (Wn == v.u.W) continue;
+    RepackArgs a{};
+    a.in = sec_of(v.u);
+    v.u_alt.W = Wn;
+    if ((s = fresh_meta(ctx, v.u_alt))) return s;
+    a.out = sec_of(v.u_alt);
+    a.nblocks = v.g.nblocks;
+    launch_repack(a, ctx->st);
+    if ((s = launched(ctx, sec_bytes(v.g, v.u.W) + sec_bytes(v.g, Wn)))) return s;
+    std::swap(v.u, v.u_alt);
+  }
+  Level &f = LV(ctx, L);
+  if ((s = set_zero_section(ctx, f.u, f.g, Wu(ctx, L, L)))) return s;
+  ctx->L = L;
+  for (int l = 1; l <= L; l++) LV(ctx, l).y_zero = true;
+  // u^_l for l < L keep their values (widening does not change values)
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_residual(cmg_ctx *ctx) {
+  if (!ctx || ctx->L < 1) return CMG_EINVAL;
+  return do_residual(ctx, false);
+}
+
+extern "C" cmg_status cmg_down(cmg_ctx *ctx, int l) {
+  if (!ctx) return CMG_EINVAL;
+  cmg_status s = need(ctx, l >= 2 && l <= ctx->L, "bad level");
+  if (s) return s;
+  Level &v = LV(ctx, l);
+  v.y_zero = true;
+  for (int k = 0; k < ctx->P.nu1; k++) {
+    SweepOpts o;
+    if ((s = do_sweep(ctx, l, o))) return s;
+  }
+  if (ctx->P.nu1 > 0) return do_restrict(ctx, l, false);
+  return CMG_OK;  // rc_(l-1) = r_(l-1) from the residual chain
+}
+
+extern "C" cmg_status cmg_coarse(cmg_ctx *ctx) {
+  if (!ctx || ctx->L < 1) return CMG_EINVAL;
+  if (ctx->P.L_max == 1) return fail(ctx, CMG_EUNSUPPORTED, "cycle on a one-level hierarchy");
+  return do_coarse(ctx, false, false);
+}
+
+extern "C" cmg_status cmg_up(cmg_ctx *ctx, int l) {
+  if (!ctx) return CMG_EINVAL;
+  cmg_status s = need(ctx, l >= 2 && l <= ctx->L, "bad level");
+  if (s) return s;
+  for (int k = 0; k < ctx->P.nu2; k++) {
+    SweepOpts o;
+    o.has_z = true;
+    o.write_w = (k == ctx->P.nu2 - 1) && l < ctx->P.L_max;
+    if ((s = do_sweep(ctx, l, o))) return s;
+  }
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_correct(cmg_ctx *ctx) {
+  if (!ctx || ctx->L < 1) return CMG_EINVAL;
+  cmg_status s;
+  for (int l = 1; l <= ctx->L; l++) {
+    Level &v = LV(ctx, l);
+    if (v.y_zero) continue;
+    AxpyArgs a{};
+    a.g = v.g;
+    a.u_in = sec_of(v.u);
+    a.y = sec_of(v.y[v.ycur]);
+    SecBuf un = v.u;  // in place
+    un.W = Wu(ctx, l, ctx->L);
+    if ((s = fresh_meta(ctx, un))) return s;
+    a.u_out = sec_of(un);
+    a.err = ctx->err;
+    launch_axpy(a, ctx->st);
+    if ((s = launched(ctx, 2 * sec_bytes(v.g, un.W) + sec_bytes(v.g, a.y.W)))) return s;
+    v.u.meta = un.meta;
+  }
+  ctx->uh_upto = 0;
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_vcycle(cmg_ctx *ctx) {
+  if (!ctx || ctx->L < 1) return CMG_EINVAL;
+  cmg_status s = CMG_OK;
+  for (int l = ctx->L; l >= 2 && !s; l--) s = cmg_down(ctx, l);
+  if (!s) s = cmg_coarse(ctx);
+  for (int l = 2; l <= ctx->L && !s; l++) s = cmg_up(ctx, l);
+  return s;
+}
+
+// the production IR iteration: residual with the first sweep fused, restriction
+// with the next level's first sweep fused, corrections fused into the last up
+// sweep of every level, u^ refreshed on the way up.
+static cmg_status ir_fused(cmg_ctx *ctx, bool need_uh_top) {
+  const int L = ctx->L, nu1 = ctx->P.nu1, nu2 = ctx->P.nu2;
+  cmg_status s = do_residual(ctx, nu1 >= 1);
+  if (s) return s;
+  for (int l = L; l >= 2; l--) {
+    Level &v = LV(ctx, l);
+    if (nu1 == 0) {
+      v.y_zero = true;
+      continue;
+    }
+    for (int k = 1; k < nu1; k++) {
+      SweepOpts o;
+      if ((s = do_sweep(ctx, l, o))) return s;
+    }
+    if ((s = do_restrict(ctx, l, l - 1 >= 2))) return s;
+  }
+  if ((s = do_coarse(ctx, false, true))) return s;
+  for (int l = 2; l <= L; l++) {
+    for (int k = 0; k < nu2; k++) {
+      const bool last = (k == nu2 - 1);
+      SweepOpts o;
+      o.has_z = true;
+      o.write_y = !last;
+      o.corr = last;
+      o.write_w = last && l < L;
+      o.write_uh = last && (l < L || need_uh_top) && l < ctx->P.L_max;
+      if ((s = do_sweep(ctx, l, o))) return s;
+    }
+  }
+  ctx->uh_upto = (need_uh_top && L < ctx->P.L_max) ? L : L - 1;
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_ir_iteration(cmg_ctx *ctx) {
+  if (!ctx || ctx->L < 2) return ctx ? fail(ctx, CMG_EINVAL, "IR needs L >= 2") : CMG_EINVAL;
+  return ir_fused(ctx, ctx->L < ctx->P.L_max);
+}
+
+extern "C" cmg_status cmg_sync(cmg_ctx *ctx) {
+  if (!ctx) return CMG_EINVAL;
+  CU(cudaStreamSynchronize(ctx->st));
+  int e[8] = {0};
+  CU(cudaMemcpy(e, ctx->err, sizeof e, cudaMemcpyDeviceToHost));
+  if (e[0] & ERR_CORRUPT) return fail(ctx, CMG_ECORRUPT, "invalid BFP code");
+  if (e[0] & ERR_EXP) return fail(ctx, CMG_ERANGE, "block exponent outside [-127, 127]");
+  if (e[0] & ERR_RANGE)
+    return fail(ctx, CMG_ERANGE, "exact integer range exceeds 62 bits (site %d: |v| < 2^%d on grid 2^%d)", e[1], e[2],
+                e[3]);
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *rep) {
+  if (!ctx) return CMG_EINVAL;
+  stat_reset(ctx->st_sweep);
+  stat_reset(ctx->st_resid);
+  ctx->launches = 0;
+  ctx->alg_bytes = 0;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, ctx->st));
+  cmg_status s = cmg_start(ctx);
+  for (int L = 2; L <= ctx->P.L_max && !s; L++) {
+    s = cmg_prolongate(ctx);
+    for (int it = 0; it < ctx->P.N_ir && !s; it++) s = ir_fused(ctx, it == ctx->P.N_ir - 1 && L < ctx->P.L_max);
+  }
+  CU(cudaEventRecord(e1, ctx->st));
+  cmg_status s2 = cmg_sync(ctx);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s) return s;
+  if (s2) return s2;
+  if (rep) {
+    std::memset(rep, 0, sizeof *rep);
+    const int d = ctx->P.dim, Lm = ctx->P.L_max;
+    rep->solve_ms = ms;
+    rep->dofs = (int64_t)make_geo(d, Lm).nz * make_geo(d, Lm).n * make_geo(d, Lm).n;
+    rep->launches = ctx->launches;
+    rep->alg_bytes = ctx->alg_bytes;
+    double bits = 0, tb = 0;
+    for (int l = 1; l <= Lm; l++) {
+      Geo g = make_geo(d, l);
+      bits += (double)g.nblocks * (32.0 * (Wu(ctx, l, Lm) + 3 * Wr(ctx, l, Lm)) + 8.0 * 4);
+      if (l < Lm) tb += 3.0 * 8.0 * g.nz * g.n * g.R;
+    }
+    rep->persistent_bits = bits;
+    rep->temp_bytes = tb;
+    ev_collect(ctx->st_sweep);
+    ev_collect(ctx->st_resid);
+    rep->sweep_ms_total = ctx->st_sweep.ms;
+    rep->sweep_launches = ctx->st_sweep.launches;
+    rep->sweep_alg_bytes = ctx->st_sweep.bytes;
+    rep->resid_ms_total = ctx->st_resid.ms;
+    rep->resid_launches = ctx->st_resid.launches;
+    rep->resid_alg_bytes = ctx->st_resid.bytes;
+  }
+  return CMG_OK;
+}
+
+// ---------------------------------------------------------------- section access
+static SecBuf *pick(cmg_ctx *ctx, int which, int l) {
+  Level &v = LV(ctx, l);
+  switch (which) {
+    case CMG_SEC_U: return &v.u;
+    case CMG_SEC_R: return &v.r;
+    case CMG_SEC_RC: return &rc_of(ctx, l);
+    case CMG_SEC_Y: return &v.y[v.ycur];
+  }
+  return nullptr;
+}
+
+extern "C" int cmg_section_width(const cmg_ctx *ctx, int which, int level) {
+  if (!ctx || level < 1 || level > ctx->P.L_max) return -1;
+  int L = ctx->L < level ? level : ctx->L;
+  return which == CMG_SEC_U ? Wu(ctx, level, L) : Wr(ctx, level, L);
+}
+
+extern "C" cmg_status cmg_get_section(cmg_ctx *ctx, int which, int level, uint32_t *words, int8_t *exps) {
+  if (!ctx || level < 1 || level > ctx->L || !exps) return CMG_EINVAL;
+  SecBuf *b = pick(ctx, which, level);
+  if (!b) return CMG_EINVAL;
+  cmg_status s = cmg_sync(ctx);
+  if (s) return s;
+  const Geo &g = LV(ctx, level).g;
+  if (which == CMG_SEC_Y && LV(ctx, level).y_zero) {
+    std::memset(exps, 0x80, (size_t)g.nblocks);
+    if (words) std::memset(words, 0, (size_t)g.nblocks * Wr(ctx, level, ctx->L) * 4);
+    return CMG_OK;
+  }
+  CU(cudaMemcpy(exps, b->exps, (size_t)g.nblocks, cudaMemcpyDeviceToHost));
+  if (words) CU(cudaMemcpy(words, b->words, (size_t)g.nblocks * b->W * 4, cudaMemcpyDeviceToHost));
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_set_section(cmg_ctx *ctx, int which, int level, int W, const uint32_t *words,
+                                      const int8_t *exps) {
+  if (!ctx || level < 1 || level > ctx->L || !words || !exps || W < 2 || W > 32) return CMG_EINVAL;
+  SecBuf *b = pick(ctx, which, level);
+  if (!b) return CMG_EINVAL;
+  const Geo &g = LV(ctx, level).g;
+  if ((size_t)g.nblocks * W > b->cap_words) return fail(ctx, CMG_EINVAL, "width above the allocated width");
+  int emax = 0, eminn = 0;
+  for (long long i = 0; i < g.nblocks; i++)
+    if (exps[i] != -128) {
+      emax = std::max(emax, exps[i] + META_BIAS);
+      eminn = std::max(eminn, META_BIAS - exps[i]);
+    }
+  cmg_status s = fresh_meta(ctx, *b);
+  if (s) return s;
+  int m[2] = {emax, eminn};
+  CU(cudaStreamSynchronize(ctx->st));
+  CU(cudaMemcpy(b->meta, m, sizeof m, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(b->exps, exps, (size_t)g.nblocks, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(b->words, words, (size_t)g.nblocks * W * 4, cudaMemcpyHostToDevice));
+  b->W = W;
+  if (which == CMG_SEC_Y) LV(ctx, level).y_zero = false;
+  if (which == CMG_SEC_U) ctx->uh_upto = std::min(ctx->uh_upto, level - 1);
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_decode_solution(cmg_ctx *ctx, int64_t z0, int64_t nz, double *out) {
+  if (!ctx || !out || ctx->L < 1) return CMG_EINVAL;
+  const int L = ctx->L;
+  const Geo &g = LV(ctx, L).g;
+  if (z0 < 0 || nz < 0 || z0 + nz > g.nz) return CMG_EINVAL;
+  cmg_status s;
+  if (ctx->uh_upto < L - 1) {
+    if ((s = run_chain(ctx, L - 1))) return s;
+    ctx->uh_upto = L - 1;
+  }
+  DecodeSolArgs a{};
+  a.g = g;
+  a.gc = L > 1 ? LV(ctx, L - 1).g : g;
+  a.u = sec_of(LV(ctx, L).u);
+  a.has_uhc = L > 1;
+  if (L > 1) a.uhc = tmp_of(LV(ctx, L - 1).uh, LV(ctx, L - 1).uhg, nullptr);
+  a.z0 = z0;
+  a.nz = nz;
+  a.out = out;
+  a.err = ctx->err;
+  launch_decode_solution(ctx->P.dim, a, ctx->st);
+  if ((s = launched(ctx, 0))) return s;
+  return cmg_sync(ctx);
+}
+
+// ---------------------------------------------------------------- checkpoint
+struct StateHeader {
+  char magic[8];
+  cmg_params P;
+  int L;
+};
+
+extern "C" cmg_status cmg_state_save(cmg_ctx *ctx, void *buf, size_t *len) {
+  if (!ctx || !len || ctx->L < 1) return CMG_EINVAL;
+  size_t need_b = sizeof(StateHeader);
+  for (int l = 1; l <= ctx->L; l++) {
+    const Geo &g = LV(ctx, l).g;
+    need_b += sizeof(int) + (size_t)g.nblocks + (size_t)g.nblocks * LV(ctx, l).u.W * 4;
+  }
+  if (!buf) {
+    *len = need_b;
+    return CMG_OK;
+  }
+  if (*len < need_b) return fail(ctx, CMG_EINVAL, "buffer too small");
+  cmg_status s = cmg_sync(ctx);
+  if (s) return s;
+  char *p = (char *)buf;
+  StateHeader h;
+  std::memcpy(h.magic, "CMGSTAT1", 8);
+  h.P = ctx->P;
+  h.L = ctx->L;
+  std::memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  for (int l = 1; l <= ctx->L; l++) {
+    const SecBuf &u = LV(ctx, l).u;
+    const Geo &g = LV(ctx, l).g;
+    std::memcpy(p, &u.W, sizeof(int));
+    p += sizeof(int);
+    CU(cudaMemcpy(p, u.exps, (size_t)g.nblocks, cudaMemcpyDeviceToHost));
+    p += g.nblocks;
+    CU(cudaMemcpy(p, u.words, (size_t)g.nblocks * u.W * 4, cudaMemcpyDeviceToHost));
+    p += (size_t)g.nblocks * u.W * 4;
+  }
+  *len = need_b;
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_state_load(cmg_ctx *ctx, const void *buf, size_t len) {
+  if (!ctx || !buf || len < sizeof(StateHeader)) return CMG_EINVAL;
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, "CMGSTAT1", 8) || std::memcmp(&h.P, &ctx->P, sizeof h.P) || h.L < 1 ||
+      h.L > ctx->P.L_max)
+    return fail(ctx, CMG_EINVAL, "checkpoint does not match this context");
+  const char *p = (const char *)buf + sizeof h;
+  size_t left = len - sizeof h;
+  ctx->L = h.L;
+  for (int l = 1; l <= h.L; l++) {
+    const Geo &g = LV(ctx, l).g;
+    int W;
+    if (left < sizeof(int)) return fail(ctx, CMG_EINVAL, "truncated checkpoint");
+    std::memcpy(&W, p, sizeof W);
+    size_t need_b = sizeof(int) + (size_t)g.nblocks + (size_t)g.nblocks * W * 4;
+    if (W < 2 || W > 32 || left < need_b) return fail(ctx, CMG_EINVAL, "truncated checkpoint");
+    const int8_t *e = (const int8_t *)(p + sizeof(int));
+    const uint32_t *w = (const uint32_t *)(p + sizeof(int) + g.nblocks);
+    std::vector<uint32_t> wtmp(w, w + (size_t)g.nblocks * W);  // alignment
+    cmg_status s = cmg_set_section(ctx, CMG_SEC_U, l, W, wtmp.data(), e);
+    if (s) return s;
+    p += need_b;
+    left -= need_b;
+  }
+  for (int l = 1; l <= h.L; l++) LV(ctx, l).y_zero = true;
+  ctx->uh_upto = 0;
+  return CMG_OK;
+}
+
+// ---------------------------------------------------------------- stand-alone codec
+static cmg_status codec_finish(int *err, cudaStream_t st) {
+  int e = 0;
+  if (cudaGetLastError() != cudaSuccess) {
+    cudaFree(err);
+    return CMG_ECUDA;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaMemcpy(&e, err, sizeof e, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaFree(err);
+    return CMG_ECUDA;
+  }
+  cudaFree(err);
+  if (e & ERR_INPUT) return CMG_EINVAL;
+  if (e & ERR_CORRUPT) return CMG_ECORRUPT;
+  if (e & ERR_EXP) return CMG_ERANGE;
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_encode(const double *x, int64_t n, int W, uint32_t *words, int8_t *exps, void *stream) {
+  if (n < 0 || W < 2 || W > 32 || (n > 0 && (!x || !words || !exps))) return CMG_EINVAL;
+  if (n == 0) return CMG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int *err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return CMG_ENOMEM;
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
+    cudaFree(err);
+    return CMG_ECUDA;
+  }
+  CodecArgs a{};
+  a.x = const_cast<double *>(x);
+  a.n = n;
+  a.W = W;
+  a.words = words;
+  a.exps = exps;
+  a.err = err;
+  launch_encode_f64(a, st);
+  return codec_finish(err, st);
+}
+
+extern "C" cmg_status cmg_decode(const uint32_t *words, const int8_t *exps, int64_t n, int W, double *x,
+                                 void *stream) {
+  if (n < 0 || W < 2 || W > 32 || (n > 0 && (!x || !words || !exps))) return CMG_EINVAL;
+  if (n == 0) return CMG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int *err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return CMG_ENOMEM;
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
+    cudaFree(err);
+    return CMG_ECUDA;
+  }
+  CodecArgs a{};
+  a.x = x;
+  a.n = n;
+  a.W = W;
+  a.words = const_cast<uint32_t *>(words);
+  a.exps = const_cast<int8_t *>(exps);
+  a.err = err;
+  launch_decode_f64(a, st);
+  return codec_finish(err, st);
+}

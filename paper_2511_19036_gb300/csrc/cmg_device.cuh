@@ -1,0 +1,323 @@
+// Device-side building blocks of the compact FMG kernels (sm_103a).
+//
+// Number representation on the GPU.  Every quantity of the method is a dyadic
+// rational.  Kernels compute exactly in int64 fixed point: a value v on grid G
+// stands for v * 2^G.  Grids are chosen locally, never globally, because the
+// BFP blocks of a section adapt to the local magnitude (blocks next to the
+// Dirichlet boundary are orders of magnitude smaller, with much finer last
+// bits, than interior blocks), so one grid per array would need far more than
+// 64 bits:
+//   * BFP sections carry their grid in each block exponent (e - W + 1);
+//   * int64 temporaries (decoded solution chain, w = y~ + z) carry one grid per
+//     32-value block, written by the warp that produced the block;
+//   * a stencil kernel converts its operand to one grid per CTA tile, the
+//     finest grid found in the tile's footprint;
+//   * each warp chooses the grid of its output block from its own inputs.
+// Exact arithmetic makes the order of evaluation irrelevant; the only rounding
+// is the round-to-nearest-even into a BFP section (Sec. 4 of the paper).  Every
+// shift and constant multiply of a computed value is checked (shl_ck, mul_ck);
+// a value that would not fit raises ERR_RANGE rather than wrapping.
+//
+// Section metadata (two ints per written section, fresh for every write):
+//   m[0] = max over nonzero blocks of (e + META_BIAS)  (0: no nonzero block)
+//   m[1] = max over nonzero blocks of (META_BIAS - e)
+// Restriction accumulators (exact sums from many CTAs by integer atomics) use
+// one global grid: m[0] = G.
+#pragma once
+#include <cstdint>
+
+namespace cmg {
+
+constexpr int META_BIAS = 1000;
+constexpr int GRID_NONE = 1 << 20;    // grid of an all-zero input: no constraint
+constexpr int MAG_NONE = -(1 << 20);  // magnitude exponent of an all-zero input
+constexpr short GR_NONE = 32767;      // per-block grid of an all-zero temporary block
+
+// error flags accumulated in a device word
+constexpr int ERR_EXP = 1;      // block exponent outside [-127, 127]
+constexpr int ERR_RANGE = 2;    // exact integer range would exceed 62 bits
+constexpr int ERR_CORRUPT = 4;  // code -2^(W-1) met in decoding
+constexpr int ERR_INPUT = 8;    // non-finite input to the codec
+
+constexpr int TY = 8;     // rows per CTA in the stencil kernels (one warp per row)
+constexpr int ZC = 32;    // z-planes marched per CTA
+constexpr int NT = 32 * TY;
+
+struct Geo {
+  int l;        // level
+  int n;        // interior nodes per axis
+  int nz;       // n in 3-D, 1 in 2-D
+  int R;        // padded row length (multiple of 32)
+  int nbx;      // blocks per row
+  long long nblocks;
+};
+
+struct Sec {
+  uint32_t *words;  // nblocks * W words
+  int8_t *exps;     // nblocks exponents
+  int W;
+  int *meta;        // 2 ints (see above)
+};
+
+struct Tmp {
+  long long *v;     // padded layout ((k*n + j)*R + i)
+  short *gr;        // per 32-value block grid (temporaries); nullptr for accumulators
+  int *meta;        // accumulators: {G, unused}
+};
+
+__host__ __device__ inline int imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }
+
+// Range failures record the first offending site and its (M, G) pair in
+// err[1..3] so that the host can report them.
+__device__ inline void flag_range(int *err, int site, int M, int G) {
+  atomicOr(err, ERR_RANGE);
+  if (atomicCAS(err + 1, 0, site) == 0) {
+    err[2] = M;
+    err[3] = G;
+  }
+}
+
+// ---------------------------------------------------------------- metadata
+__device__ inline int sec_lsb(const Sec &s) {  // finest grid of a section's values
+  int m1 = __ldg(s.meta + 1);
+  if (m1 == 0) return GRID_NONE;
+  int emin = META_BIAS - m1;
+  return emin - s.W + 1;
+}
+__device__ inline int sec_msb(const Sec &s) {  // |value| < 2^msb
+  int m0 = __ldg(s.meta);
+  if (m0 == 0) return MAG_NONE;
+  return m0 - META_BIAS;
+}
+__device__ __forceinline__ int blk_lsb(int e, int W) { return e == -128 ? GRID_NONE : e - W + 1; }
+__device__ __forceinline__ int gr_of(short g) { return g == GR_NONE ? GRID_NONE : (int)g; }
+
+// ---------------------------------------------------------------- checked integer ops
+// exact left shift of an int64 (0 stays 0)
+__device__ __forceinline__ long long shl(long long v, int s) {
+  return (s >= 63) ? 0 : (long long)((unsigned long long)v << s);
+}
+
+// left shift that records whether the result leaves (-2^62, 2^62)
+__device__ __forceinline__ long long shl_ck(long long v, int s, bool &ovf) {
+  if (s >= 63) {
+    ovf |= (v != 0);
+    return 0;
+  }
+  long long hi = v >> (62 - s);
+  ovf |= (unsigned long long)(hi + 1) > 1ull;
+  return (long long)((unsigned long long)v << s);
+}
+
+// v * c for a constant with bit length cbits, recording a possible overflow
+__device__ __forceinline__ long long mul_ck(long long v, int c, int cbits, bool &ovf) {
+  long long hi = v >> (62 - cbits);
+  ovf |= (unsigned long long)(hi + 1) > 1ull;
+  return v * (long long)c;
+}
+
+// |v| < 2^62 check of a computed value before rounding
+__device__ __forceinline__ void ck62(long long v, bool &ovf) {
+  ovf |= (unsigned long long)((v >> 62) + 1) > 1ull;
+}
+// |v| < 2^58: stencil operands (a 7-point sum stays in 62 bits) and restriction
+// contributions (a sum of at most 15 stays in 62 bits)
+__device__ __forceinline__ void ck58(long long v, bool &ovf) {
+  ovf |= (unsigned long long)((v >> 58) + 1) > 1ull;
+}
+
+// ---------------------------------------------------------------- decoding
+// W-bit two's-complement code i of a block (words of that block)
+__device__ __forceinline__ int code_at(const uint32_t *bw, int W, int lane) {
+  int pos = lane * W, wd = pos >> 5, off = pos & 31;
+  uint32_t lo = __ldg(bw + wd);
+  uint32_t hi = (off + W > 32) ? __ldg(bw + wd + 1) : 0u;
+  uint32_t bits = __funnelshift_r(lo, hi, off);
+  return ((int)(bits << (32 - W))) >> (32 - W);
+}
+
+__device__ __forceinline__ bool inside(const Geo &g, int i, int j, int k) {
+  return (unsigned)i < (unsigned)g.n && (unsigned)j < (unsigned)g.n && (unsigned)k < (unsigned)g.nz;
+}
+__device__ __forceinline__ long long blk_index(const Geo &g, int i, int j, int k) {
+  return ((long long)k * g.n + j) * g.nbx + (i >> 5);
+}
+
+// value of section s at 0-based (i, j, k) on grid 2^G (G <= its block's grid);
+// zero outside the interior.
+__device__ __forceinline__ long long sec_val_ck(const Sec &s, const Geo &g, int i, int j, int k, int G,
+                                                bool &ovf) {
+  if (!inside(g, i, j, k)) return 0;
+  long long b = blk_index(g, i, j, k);
+  int e = __ldg(s.exps + b);
+  if (e == -128) return 0;
+  int q = code_at(s.words + b * s.W, s.W, i & 31);
+  return shl_ck((long long)q, e - s.W + 1 - G, ovf);
+}
+
+// temporary value and grid at 0-based (i, j, k); zero outside the interior
+__device__ __forceinline__ long long tmp_raw(const Tmp &t, const Geo &g, int i, int j, int k, int &G) {
+  if (!inside(g, i, j, k)) {
+    G = GRID_NONE;
+    return 0;
+  }
+  G = gr_of(__ldg(t.gr + blk_index(g, i, j, k)));
+  return __ldg(t.v + ((long long)k * g.n + j) * g.R + i);
+}
+
+// coarse parents of fine node (I, J, K) (1-based) for P_l: an all-even node has
+// one parent I/2, any other node the two parents (I -+ e_S)/2 (S = odd axes).
+template <int DIM>
+struct Parents {
+  int ia, ja, ka, ib, jb, kb;
+  bool two;
+  __device__ __forceinline__ Parents(int I, int J, int K) {
+    int sx = I & 1, sy = J & 1, sz = (DIM == 3) ? (K & 1) : 0;
+    two = (sx | sy | sz) != 0;
+    ia = ((I - sx) >> 1) - 1;
+    ja = ((J - sy) >> 1) - 1;
+    ka = (DIM == 3) ? ((K - sz) >> 1) - 1 : 0;
+    ib = ((I + sx) >> 1) - 1;
+    jb = ((J + sy) >> 1) - 1;
+    kb = (DIM == 3) ? ((K + sz) >> 1) - 1 : 0;
+  }
+};
+
+// (P_l c)(I, J, K) on grid G: linear interpolation along the Kuhn edge through
+// the node (Sec. 3.1 prolongation of the nested P1 spaces)
+template <int DIM>
+__device__ __forceinline__ long long prolong_tmp(const Tmp &c, const Geo &gc, int I, int J, int K, int G,
+                                                 bool &ovf) {
+  Parents<DIM> p(I, J, K);
+  int ga, gb;
+  long long a = tmp_raw(c, gc, p.ia, p.ja, p.ka, ga);
+  if (!p.two) return a ? shl_ck(a, ga - G, ovf) : 0;
+  long long b = tmp_raw(c, gc, p.ib, p.jb, p.kb, gb);
+  return (a ? shl_ck(a, ga - 1 - G, ovf) : 0) + (b ? shl_ck(b, gb - 1 - G, ovf) : 0);
+}
+
+// grid on which (P_l c)(I, J, K) is exact
+template <int DIM>
+__device__ __forceinline__ int prolong_grid(const Tmp &c, const Geo &gc, int I, int J, int K) {
+  Parents<DIM> p(I, J, K);
+  int G = GRID_NONE;
+  if (inside(gc, p.ia, p.ja, p.ka)) G = gr_of(__ldg(c.gr + blk_index(gc, p.ia, p.ja, p.ka)));
+  if (!p.two) return G;
+  if (inside(gc, p.ib, p.jb, p.kb)) G = imin(G, gr_of(__ldg(c.gr + blk_index(gc, p.ib, p.jb, p.kb))));
+  return G >= GRID_NONE / 2 ? G : G - 1;
+}
+
+// ---------------------------------------------------------------- rounding
+// round-to-nearest-even of v / 2^s for s > 0; v * 2^-s (exact) for s <= 0
+__device__ __forceinline__ long long rne_shift(long long v, int s) {
+  if (s <= 0) return shl(v, -s);
+  long long q = v >> s;  // floor
+  unsigned long long rem = (unsigned long long)v & ((1ull << s) - 1ull);
+  unsigned long long half = 1ull << (s - 1);
+  if (rem > half || (rem == half && (q & 1))) q += 1;
+  return q;
+}
+
+__device__ __forceinline__ int bitlen64(long long v) {
+  unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  return a ? 64 - __clzll((long long)a) : 0;
+}
+
+// Warp-collective BFP rounding of one block: every lane passes its exact value
+// v on grid 2^G (padding lanes pass 0).  Returns the W-bit code; e receives the
+// block exponent (-128 for an all-zero block) and s the drop shift, so that the
+// rounded value on grid G is rne_shift(v, s) << s when s > 0, else v itself.
+__device__ __forceinline__ int encode_block(long long v, int G, int W, int &e, int &s, int *err) {
+  int bl = bitlen64(v);
+  int bmax = __reduce_max_sync(0xffffffffu, bl);
+  if (bmax == 0) {
+    e = -128;
+    s = 0;
+    return 0;
+  }
+  e = bmax + G;  // 2^(e-1) <= max|v| 2^G < 2^e
+  s = bmax - (W - 1);
+  long long q = rne_shift(v, s);
+  long long lim = 1ll << (W - 1);
+  if (__any_sync(0xffffffffu, q == lim || q == -lim)) {
+    e += 1;
+    s += 1;
+    q = rne_shift(v, s);
+  }
+  if ((e > 127 || e < -127) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_EXP);
+  return (int)q;
+}
+
+__device__ __forceinline__ long long rounded_value(long long v, int q, int s) {
+  return s > 0 ? shl((long long)q, s) : v;
+}
+
+// Warp-collective packing of 32 W-bit codes into W words (code i at bits
+// [iW, iW+W)), through a per-warp scratch of 33 shared words.
+__device__ __forceinline__ void pack_block(int q, int W, uint32_t *scratch, uint32_t *out) {
+  int lane = threadIdx.x & 31;
+  if (lane < W + 1) scratch[lane] = 0u;
+  __syncwarp();
+  unsigned long long code = (unsigned long long)((unsigned)q & (W == 32 ? 0xffffffffu : ((1u << W) - 1u)));
+  int pos = lane * W, wd = pos >> 5, off = pos & 31;
+  unsigned long long sh = code << off;
+  if ((uint32_t)sh) atomicOr(scratch + wd, (uint32_t)sh);
+  if ((uint32_t)(sh >> 32)) atomicOr(scratch + wd + 1, (uint32_t)(sh >> 32));
+  __syncwarp();
+  if (lane < W) out[lane] = scratch[lane];
+  __syncwarp();
+}
+
+// Warp-collective store of one 32-value block of a temporary: the values v on
+// grid G are renormalised to the coarsest grid that holds them all exactly
+// (common trailing zero bits removed) and written with that block grid.
+__device__ __forceinline__ void store_tmp_block(long long v, int G, long long *dst, short *gr, bool active,
+                                                bool &ovf) {
+  unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)(unsigned long long)v);
+  unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)((unsigned long long)v >> 32));
+  int lane = threadIdx.x & 31;
+  if (!(lo | hi)) {  // all-zero block
+    if (active) *dst = 0;
+    if (lane == 0) *gr = GR_NONE;
+    return;
+  }
+  int tz = lo ? __ffs(lo) - 1 : 32 + __ffs(hi) - 1;
+  int g = G + tz;
+  if (g > 32000 || g < -32000) ovf = true;
+  if (active) *dst = v >> tz;
+  if (lane == 0) *gr = (short)g;
+}
+
+// CTA-level reduction of written exponents into the section metadata.
+struct MetaAcc {
+  int emax, emin_neg;  // running max of (e + BIAS) and (BIAS - e)
+  __device__ void init() { emax = 0; emin_neg = 0; }
+  __device__ void add(int e) {
+    if (e != -128) {
+      emax = imax(emax, e + META_BIAS);
+      emin_neg = imax(emin_neg, META_BIAS - e);
+    }
+  }
+};
+
+// lane 0 of each warp holds a MetaAcc; reduce over the CTA and publish once
+__device__ inline void meta_flush(MetaAcc a, int *meta, int *sm2) {
+  // sm2: 2 shared ints, zero-initialised by the caller before a __syncthreads
+  if ((threadIdx.x & 31) == 0 && a.emax) {
+    atomicMax(sm2, a.emax);
+    atomicMax(sm2 + 1, a.emin_neg);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0 && sm2[0]) {
+    atomicMax(meta, sm2[0]);
+    atomicMax(meta + 1, sm2[1]);
+  }
+}
+
+// warp-collective: report per-thread overflow flags once
+__device__ inline void ovf_flush(bool ovf, int *err, int site) {
+  if (__any_sync(0xffffffffu, ovf) && (threadIdx.x & 31) == 0) flag_range(err, site, 0, 0);
+}
+
+}  // namespace cmg

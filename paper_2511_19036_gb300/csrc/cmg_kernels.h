@@ -1,0 +1,125 @@
+// Launch interface of the compact FMG kernels (host side, internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cmg_device.cuh"
+
+namespace cmg {
+
+struct SweepArgs {
+  Geo g, gc;           // level l and level l-1
+  int has_y;           // y~ input present (else y~ = 0)
+  int has_z;           // z_l = P w_(l-1) present
+  int write_y;         // store y~'
+  int corr;            // fused u~ <- round(u~ + y~')
+  int write_w;         // w_l = y~' + z_l
+  int write_uh;        // u^_l = u~' + P u^_(l-1)
+  int has_uhc;         // u^_(l-1) present (l >= 2)
+  int Wy;              // width of y~'
+  Sec y_in, rc, y_out, u_in, u_out;
+  Tmp wc, w_out, uhc, uh_out;
+  int c_num, c_exp, cbits;  // Jacobi factor c_l = c_num 2^c_exp, cbits = bitlen(c_num)
+  int *err;
+};
+
+struct ResidArgs {
+  Geo g, gc;
+  Sec u;               // u~_L
+  int has_uhc;
+  Tmp uhc;             // u^_(L-1)
+  const int32_t *tables;
+  int nterms, n1max, Lmax, fsh;
+  int Gf;              // grid of f_L: scale_exp + fsh - d L
+  Sec r_out;
+  int first_sweep;     // also y~ = round(c r)
+  Sec y_out;
+  int write_t;         // also store t^_L at the width of Table 1 (no pre-smoothing)
+  Sec t_out;
+  int c_num, c_exp, cbits;
+  int *err;
+};
+
+struct RestrictArgs {
+  Geo g, gc;
+  int has_y;           // d = rc - A y~ (else d = rc)
+  Sec y, rc;
+  Tmp acc;             // exact R_l d on one global grid
+  int *err;
+};
+
+struct AccArgs {
+  Geo g, gc;
+  Tmp acc;             // exact values on level l (zeroed after reading)
+  Sec r_out;
+  int first_sweep;
+  Sec y_out;
+  int chain;           // restriction chain of t^: t^ = round(R t^) at the width
+  Sec t_out;           // of Table 1, stored, and r = round(t^)
+  int c_num, c_exp, cbits;
+  int *err;
+};
+
+struct CoarseArgs {
+  int dim;
+  int mode_start;      // 1: u~_1 = round(f_1 / A_1); 0: y~_1 = round(rc_1 / A_1)
+  long long f1;        // F_q at the level-1 node (start mode)
+  int Gf1;             // its grid
+  Sec rc, y_out, u_in, u_out;
+  int corr;            // fused u~_1 += y~_1 (cycle mode)
+  Tmp w_out, uh_out;
+  int *err;
+};
+
+struct RepackArgs {
+  Sec in, out;
+  long long nblocks;
+};
+
+struct ChainArgs {
+  Geo g, gc;
+  Sec u;
+  int has_uhc;
+  Tmp uhc, uh_out;
+  int *err;
+};
+
+struct AxpyArgs {
+  Geo g;
+  Sec u_in, y, u_out;
+  int *err;
+};
+
+struct DecodeSolArgs {
+  Geo g, gc;
+  Sec u;
+  int has_uhc;
+  Tmp uhc;
+  long long z0, nz;
+  double *out;
+  int *err;
+};
+
+struct CodecArgs {
+  double *x;
+  long long n;
+  int W;
+  uint32_t *words;
+  int8_t *exps;
+  int *err;
+};
+
+void launch_sweep(int dim, const SweepArgs &a, cudaStream_t st);
+void launch_residual(int dim, const ResidArgs &a, cudaStream_t st);
+void launch_restrict(int dim, const RestrictArgs &a, cudaStream_t st);
+void launch_acc_encode(int dim, const AccArgs &a, cudaStream_t st);
+void launch_coarse(const CoarseArgs &a, cudaStream_t st);
+void launch_repack(const RepackArgs &a, cudaStream_t st);
+void launch_chain(int dim, const ChainArgs &a, cudaStream_t st);
+void launch_axpy(const AxpyArgs &a, cudaStream_t st);
+void launch_decode_solution(int dim, const DecodeSolArgs &a, cudaStream_t st);
+void launch_encode_f64(const CodecArgs &a, cudaStream_t st);
+void launch_decode_f64(const CodecArgs &a, cudaStream_t st);
+
+}  // namespace cmg

@@ -1,0 +1,67 @@
+"""The C-ABI library loads and exports every entry point that include/cmg.h
+declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions(header):
+    src = open(header).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(cmg_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2511_19036_gb300 import _build
+    try:
+        return _build.build()
+    except (RuntimeError, FileNotFoundError) as e:  # nvcc missing on this host
+        pytest.skip("nvcc unavailable: %s" % e)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions(os.path.join(ROOT, "include", "cmg.h"))
+    for need in ("cmg_encode", "cmg_decode", "cmg_create", "cmg_fmg_solve", "cmg_residual",
+                 "cmg_down", "cmg_up", "cmg_prolongate", "cmg_vcycle", "cmg_decode_solution"):
+        assert need in names
+    assert len(names) >= 25
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    names = declared_functions(os.path.join(ROOT, "include", "cmg.h"))
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(cmg_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_binding_covers_every_symbol(libpath):
+    from paper_2511_19036_gb300 import cmg
+    names = declared_functions(os.path.join(ROOT, "include", "cmg.h"))
+    assert set(names) <= set(cmg.exported_symbols())
+
+
+def test_host_side_parameter_validation(libpath):
+    from paper_2511_19036_gb300 import cmg
+    good = cmg.config_for("poisson3d_fourier", 11)
+    assert cmg.params_check(good) == cmg.OK
+    assert cmg.params_check(cmg.config_for("poisson2d_manufactured", 8)) == cmg.OK
+    for k, v in [("dim", 1), ("L_max", 0), ("b2", 1), ("nu2", 0), ("omega_num", 0), ("omega_num", 2)]:
+        bad = cmg.config_for("poisson3d_fourier", 8)
+        setattr(bad, k, v)
+        assert cmg.params_check(bad) == cmg.EINVAL, k
+    wide = cmg.config_for("poisson3d_fourier", 14)
+    wide.b1 = 12
+    assert cmg.params_check(wide) == cmg.ERANGE
+    assert cmg.lib().cmg_section_blocks(3, 8) == 255 * 255 * 8
+    assert cmg.lib().cmg_section_blocks(2, 8) == 255 * 8
+    assert cmg.lib().cmg_section_blocks(4, 8) == -1

@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+The bar is bit-exact: codes, exponents and packed words of every section after
+every step, and the decoded solution.  Exact arithmetic on both sides (the
+oracle certifies zero inexact FP64 operations) makes this the correct bar.
+"""
+import numpy as np
+import pytest
+
+import cmg_problems as P
+import oracle
+from cmg_problems import random_block_values
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cmg():
+    from paper_2511_19036_gb300 import cmg as m
+    return m
+
+
+def make_pair(cmg, name, Lmax, **over):
+    prob = P.make_problem(name, Lmax)
+    cfg = cmg.config_for(name, Lmax)
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    s = cmg.Solver(cfg)
+    s.set_rhs(prob.tables, prob.scale_exp)
+    o = oracle.Oracle.for_problem(prob, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1, nu2=cfg.nu2,
+                                  omega=cfg.omega)
+    return prob, cfg, s, o
+
+
+def same_section(cmg, s, o, which_g, which_o, level, what=""):
+    gw, ge = s.get_section(which_g, level)
+    ow, oe, _ = o.get_section(which_o, level)
+    assert s.width(which_g, level) == o.width(which_o, level)
+    assert np.array_equal(ge, oe), "exponents differ: %s level %d (%d blocks)" % (
+        what, level, int(np.sum(ge != oe)))
+    assert np.array_equal(gw, ow), "words differ: %s level %d (%d words)" % (what, level, int(np.sum(gw != ow)))
+
+
+# ---------------------------------------------------------------- codec
+@pytest.mark.parametrize("W", [2, 3, 4, 5, 7, 8, 13, 16, 25, 31, 32])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 32 * 257 + 5])
+def test_codec_bit_exact(cmg, W, n):
+    x = random_block_values(n, seed=1000 + W + n)
+    ow, oe, st = oracle.encode(x, W)
+    assert st == 0
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+    gw, ge = cmg.encode(xt, W)
+    torch.cuda.synchronize()
+    assert np.array_equal(ge.cpu().numpy(), oe)
+    assert np.array_equal(gw.cpu().numpy().view(np.uint32), ow)
+    y = cmg.decode(gw, ge, n, W).cpu().numpy()
+    yo, _ = oracle.decode(ow, oe, n, W)
+    assert np.array_equal(y, yo)
+
+
+def test_codec_ties_and_edges(cmg):
+    x = np.zeros(64)
+    x[:6] = [1.5, 0.25, 0.75, -0.25, -0.75, 1.9]
+    x[32:36] = [2.0 ** -120, -(2.0 ** -121), 3 * 2.0 ** -122, 0.0]
+    for W in (2, 3, 4):
+        ow, oe, _ = oracle.encode(x, W)
+        gw, ge = cmg.encode(torch.tensor(x, device="cuda"), W)
+        assert np.array_equal(ge.cpu().numpy(), oe)
+        assert np.array_equal(gw.cpu().numpy().view(np.uint32), ow)
+
+
+def test_codec_errors(cmg):
+    big = torch.zeros(32, dtype=torch.float64, device="cuda")
+    big[0] = 2.0 ** 200
+    with pytest.raises(cmg.CmgError) as ei:
+        cmg.encode(big, 8)
+    assert ei.value.status == cmg.ERANGE
+    bad = torch.zeros(32, dtype=torch.float64, device="cuda")
+    bad[3] = float("nan")
+    with pytest.raises(cmg.CmgError) as ei:
+        cmg.encode(bad, 8)
+    assert ei.value.status == cmg.EINVAL
+    words = torch.zeros(4, dtype=torch.int32, device="cuda")
+    words[0] = 0b1000
+    exps = torch.zeros(1, dtype=torch.int8, device="cuda")
+    with pytest.raises(cmg.CmgError) as ei:
+        cmg.decode(words, exps, 32, 4)
+    assert ei.value.status == cmg.ECORRUPT
+
+
+# ---------------------------------------------------------------- steps
+STEP_CASES = [("poisson2d_manufactured", 6, {}), ("poisson3d_fourier", 5, {}),
+              ("poisson3d_manufactured", 4, {"nu1": 0, "nu2": 1}),
+              ("poisson2d_fourier", 6, {"nu1": 1, "nu2": 2}),
+              ("poisson3d_fourier", 4, {"nu1": 3, "nu2": 1})]
+
+
+@pytest.mark.parametrize("name,Lmax,over", STEP_CASES)
+def test_step_parity(cmg, name, Lmax, over):
+    prob, cfg, s, o = make_pair(cmg, name, Lmax, **over)
+    s.start()
+    o.start()
+    same_section(cmg, s, o, cmg.SEC_U, oracle.U, 1, "start")
+    for L in range(2, Lmax + 1):
+        s.prolongate()
+        o.next_level()
+        for l in range(1, L + 1):
+            same_section(cmg, s, o, cmg.SEC_U, oracle.U, l, "prolongate L=%d" % L)
+        for it in range(2):
+            s.residual()
+            o.residual()
+            same_section(cmg, s, o, cmg.SEC_R, oracle.R, L, "residual L=%d" % L)
+            if cfg.nu1 == 0:
+                for l in range(1, L):
+                    same_section(cmg, s, o, cmg.SEC_R, oracle.R, l, "residual chain L=%d" % L)
+            for l in range(L, 1, -1):
+                s.down(l)
+                o.down(l)
+                same_section(cmg, s, o, cmg.SEC_Y, oracle.Y, l, "down L=%d" % L)
+                same_section(cmg, s, o, cmg.SEC_RC, oracle.RC, l - 1, "restrict L=%d" % L)
+            s.coarse()
+            o.coarse()
+            same_section(cmg, s, o, cmg.SEC_Y, oracle.Y, 1, "coarse L=%d" % L)
+            for l in range(2, L + 1):
+                s.up(l)
+                o.up(l)
+                same_section(cmg, s, o, cmg.SEC_Y, oracle.Y, l, "up L=%d" % L)
+            s.correct()
+            o.correct()
+            for l in range(1, L + 1):
+                same_section(cmg, s, o, cmg.SEC_U, oracle.U, l, "correct L=%d" % L)
+    assert o.inexact == 0
+
+
+# ---------------------------------------------------------------- full solves
+FMG_CASES = [("poisson2d_manufactured", 8, {}),       # 257^2, the 2-D workload
+             ("poisson2d_manufactured", 3, {}),
+             ("poisson2d_fourier", 7, {"nu1": 0, "nu2": 1}),
+             ("poisson3d_fourier", 2, {}),
+             ("poisson3d_fourier", 6, {}),
+             ("poisson3d_manufactured", 6, {"nu1": 1, "nu2": 1}),
+             ("poisson3d_fourier", 5, {"nu1": 0, "nu2": 2, "N_ir": 4})]
+
+
+@pytest.mark.parametrize("name,Lmax,over", FMG_CASES)
+def test_fmg_parity(cmg, name, Lmax, over):
+    prob, cfg, s, o = make_pair(cmg, name, Lmax, **over)
+    s.fmg_solve()
+    o.fmg()
+    assert o.inexact == 0
+    for l in range(1, Lmax + 1):
+        same_section(cmg, s, o, cmg.SEC_U, oracle.U, l, "fmg")
+    u = s.decode_solution().cpu().numpy()
+    assert np.array_equal(u, o.decode_solution())
+
+
+def test_fmg_repeatable(cmg):
+    prob, cfg, s, o = make_pair(cmg, "poisson3d_fourier", 6)
+    s.fmg_solve()
+    a = [s.get_section(cmg.SEC_U, l) for l in range(1, 7)]
+    s.fmg_solve()
+    b = [s.get_section(cmg.SEC_U, l) for l in range(1, 7)]
+    for (w1, e1), (w2, e2) in zip(a, b):
+        assert np.array_equal(w1, w2) and np.array_equal(e1, e2)
+
+
+def test_ir_iteration_matches_oracle(cmg):
+    """The fused production IR iteration equals the oracle's residual + cycle + correction."""
+    prob, cfg, s, o = make_pair(cmg, "poisson3d_fourier", 5)
+    s.start()
+    o.start()
+    for L in range(2, 6):
+        s.prolongate()
+        o.next_level()
+        for _ in range(cfg.N_ir):
+            s.ir_iteration()
+            o.ir_iteration()
+        for l in range(1, L + 1):
+            same_section(cmg, s, o, cmg.SEC_U, oracle.U, l, "ir L=%d" % L)
+
+
+def test_checkpoint_roundtrip(cmg):
+    prob, cfg, s, o = make_pair(cmg, "poisson2d_manufactured", 6)
+    s.fmg_solve()
+    blob = s.state_save()
+    s2 = cmg.Solver(cfg)
+    s2.set_rhs(prob.tables, prob.scale_exp)
+    s2.state_load(blob)
+    assert s2.level == 6
+    assert np.array_equal(s.decode_solution().cpu().numpy(), s2.decode_solution().cpu().numpy())
+    # a further IR iteration continues identically on both
+    s.ir_iteration()
+    s2.ir_iteration()
+    for l in range(1, 7):
+        a, b = s.get_section(cmg.SEC_U, l), s2.get_section(cmg.SEC_U, l)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_invalid_parameters(cmg):
+    bad = [dict(dim=4), dict(L_max=0), dict(L_max=15), dict(b1=1), dict(nu2=0), dict(N_ir=0),
+           dict(omega_num=4, omega_log2den=2)]  # 4/4 / 6 is not dyadic in 3-D
+    for over in bad:
+        cfg = cmg.config_for("poisson3d_fourier", 5)
+        for k, v in over.items():
+            setattr(cfg, k, v)
+        assert cmg.params_check(cfg) in (cmg.EINVAL, cmg.ERANGE)
+        with pytest.raises(cmg.CmgError):
+            cmg.Solver(cfg)
+    cfg = cmg.config_for("poisson3d_fourier", 14)
+    cfg.b1 = 12  # u~ on level 1 would need 2*13 + 12 > 32 bits
+    assert cmg.params_check(cfg) == cmg.ERANGE
+
+
+def test_solve_without_rhs_is_rejected(cmg):
+    s = cmg.Solver(cmg.config_for("poisson2d_manufactured", 4))
+    with pytest.raises(cmg.CmgError) as ei:
+        s.fmg_solve()
+    assert ei.value.status == cmg.EINVAL
