@@ -170,6 +170,39 @@ cmg_status cmg_decode_solution(cmg_ctx *ctx, int64_t z0, int64_t nz, double *out
 cmg_status cmg_state_save(cmg_ctx *ctx, void *buf, size_t *len);
 cmg_status cmg_state_load(cmg_ctx *ctx, const void *buf, size_t len);
 
+/* ---------------------------------------------------------------------------
+ * Decoding without device allocation.  The paper has no counterpart to this
+ * entry point; it serves callers that may not allocate device memory while
+ * they run, e.g. an application that gives all of its device memory to its own
+ * pool at start-up, or a time-critical loop that cannot accept the implicit
+ * device-wide synchronisation of cudaMalloc/cudaFree.
+ *
+ * cmg_decode_compact computes the standard representation u^_L of planes
+ * z0 .. z0+nz-1 (eq. compact-to-standard) from the sections u~_1 .. u~_L of a
+ * compact vector, exactly like cmg_decode_solution, but without a context:
+ * words_dev[l-1], exps_dev[l-1] and widths[l-1] describe section l in the BFP
+ * layout above (device memory of the caller; the pointer arrays and widths are
+ * host arrays), out_dev receives nz * n * n doubles (n = 2^L - 1; 2-D: z0 = 0,
+ * nz = 1).  The decoded coarse levels it needs are kept in one static device
+ * array of CMG_STATIC_SCRATCH_BYTES that every GPU loading this library holds
+ * until the process exits; the call itself allocates nothing.
+ *  - Capacity: returns CMG_ERANGE without launching anything when
+ *    cmg_decode_compact_scratch_bytes(dim, L) exceeds CMG_STATIC_SCRATCH_BYTES
+ *    (3-D up to L = 8, 2-D up to L = 11).
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current); make that first call before any stream capture.
+ *  - All calls on one device share the array, which keeps the previous call's
+ *    contents (the call clears what must start at zero).  Calls whose work may
+ *    overlap on the GPU (different streams, or different host threads) race on
+ *    the array and must be serialised by the caller.
+ *  - Synchronises the stream; CMG_ECORRUPT / CMG_ERANGE / CMG_EINVAL as for
+ *    cmg_decode_solution. */
+#define CMG_STATIC_SCRATCH_BYTES ((size_t)24 << 20)
+size_t cmg_decode_compact_scratch_bytes(int dim, int L);
+cmg_status cmg_decode_compact(int dim, int L, const uint32_t *const *words_dev,
+                              const int8_t *const *exps_dev, const int *widths, int64_t z0,
+                              int64_t nz, double *out_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,8 @@ _SIGS = {
     "cmg_decode_solution": (_i32, [_vp, _i64, _i64, _vp]),
     "cmg_state_save": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
     "cmg_state_load": (_i32, [_vp, _vp, ctypes.c_size_t]),
+    "cmg_decode_compact_scratch_bytes": (ctypes.c_size_t, [_i32, _i32]),
+    "cmg_decode_compact": (_i32, [_i32, _i32, _vp, _vp, _vp, _i64, _i64, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
