@@ -242,6 +242,10 @@ def run_gpu(args, wl):
                 "avg_launch_ms": sw_ms / sw_n if sw_n else None,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
     whole_frac = (reports[0]["alg_bytes"] / (ms_step * 1e-3) / 1e9) / peak
+    # where one solve spends its device time (the last timed step), per kernel kind
+    kernels = {k: {"ms": round(v["ms"], 4), "launches": v["launches"],
+                   "GB_per_s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
+               for k, v in solver.kernel_stats().items() if v["launches"]}
 
     # end to end through the public API: H2D of the step's inputs (the RHS tables,
     # from pinned memory) and D2H of the step's result (the compact solution).
@@ -313,6 +317,7 @@ def run_gpu(args, wl):
         "whole_solve_hbm_frac": whole_frac,
         "nodal_rel_err_sampled": nodal_rel,
         "roofline": roofline,
+        "kernels_last_step": kernels,
         "cpu_baseline": cpu,
         "e2e": {"value": world * dofs / e2e_s, "unit": "DoF/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

@@ -87,6 +87,18 @@ typedef struct {
   double resid_alg_bytes;
 } cmg_report;
 
+/* Kernel kinds for cmg_kernel_stats. */
+enum {
+  CMG_KIND_RESIDUAL = 0,   /* fmgResidual (Algorithm 2), first sweep fused */
+  CMG_KIND_SWEEP = 1,      /* Jacobi sweeps, corrections fused */
+  CMG_KIND_RESTRICT = 2,   /* restriction into the int64 accumulator */
+  CMG_KIND_ACC_ENCODE = 3, /* accumulator to BFP (restricted right-hand side) */
+  CMG_KIND_COARSE = 4,     /* level-1 solve */
+  CMG_KIND_REPACK = 5,     /* FMG level step (widening) */
+  CMG_KIND_OTHER = 6,      /* decode chain and step-wise pieces */
+  CMG_KIND_COUNT = 7
+};
+
 /* Section selectors for cmg_get_section / cmg_set_section. */
 enum { CMG_SEC_U = 0, CMG_SEC_R = 1, CMG_SEC_RC = 2, CMG_SEC_Y = 3 };
 
@@ -126,6 +138,13 @@ cmg_status cmg_set_rhs_separable(cmg_ctx *ctx, int nterms, const int32_t *tables
 /* Algorithm 3 end to end (coarse solve, then L = 2..L_max with N_ir IR
  * iterations each).  Synchronises; fills *report when non-NULL. */
 cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *report);
+
+/* Launch statistics of the last cmg_fmg_solve per kernel kind (CMG_KIND_*),
+ * for launches on level L_max (top = 1) or on coarser levels (top = 0): total
+ * device time (CUDA events on the context's stream; 0 unless cmg_set_timing
+ * was enabled), number of launches and modelled algorithmic bytes. */
+cmg_status cmg_kernel_stats(cmg_ctx *ctx, int kind, int top, double *ms, int64_t *launches,
+                            double *bytes);
 
 /* Individual steps of Algorithm 3 (unfused kernels), for step-wise checking.
  * cmg_start: L = 1, u~_1 = round(f_1 / A_1).  cmg_prolongate: FMG level step

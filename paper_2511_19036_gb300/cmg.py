@@ -84,6 +84,8 @@ _SIGS = {
     "cmg_decode_solution": (_i32, [_vp, _i64, _i64, _vp]),
     "cmg_state_save": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
     "cmg_state_load": (_i32, [_vp, _vp, ctypes.c_size_t]),
+    "cmg_kernel_stats": (_i32, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "cmg_decode_compact_scratch_bytes": (ctypes.c_size_t, [_i32, _i32]),
     "cmg_decode_compact": (_i32, [_i32, _i32, _vp, _vp, _vp, _i64, _i64, _vp, _vp]),
 }
@@ -201,6 +203,20 @@ class Solver:
         rep = Report()
         self._chk(_lib.cmg_fmg_solve(self._h, ctypes.byref(rep)), "cmg_fmg_solve")
         return rep.as_dict()
+
+    KINDS = ("residual", "sweep", "restrict", "acc_encode", "coarse", "repack", "other")
+
+    def kernel_stats(self) -> dict:
+        """Per kernel kind and level class ('top' = L_max): ms, launches, bytes."""
+        out = {}
+        for kind, name in enumerate(self.KINDS):
+            for top in (1, 0):
+                ms, n, by = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+                self._chk(_lib.cmg_kernel_stats(self._h, kind, top, ctypes.byref(ms), ctypes.byref(n),
+                                                ctypes.byref(by)), "cmg_kernel_stats")
+                out["%s_%s" % (name, "top" if top else "lower")] = {
+                    "ms": ms.value, "launches": n.value, "bytes": by.value}
+        return out
 
     def start(self):
         self._chk(_lib.cmg_start(self._h), "cmg_start")

@@ -40,7 +40,7 @@ struct Level {
   bool y_zero = true;
   SecBuf t;                       // t^_l of the restriction chain (no pre-smoothing)
   long long *uh = nullptr, *w = nullptr, *acc = nullptr;
-  short *uhg = nullptr, *wg = nullptr;  // per-block grids of u^_l and w_l
+  int *uhg = nullptr, *wg = nullptr;  // per-block descriptors of u^_l and w_l
   int *accmeta = nullptr;
 };
 
@@ -69,7 +69,7 @@ struct cmg_ctx {
   int c_num2 = 0, c_exp2 = 0;  // omega / (2d) = c_num2 2^c_exp2 (level-free part)
   std::string msg;
   bool timing = false;
-  KStat st_sweep, st_resid;
+  KStat stats[CMG_KIND_COUNT][2];  // per kernel kind; [1] = launches on level L_max
   long long launches = 0;
   double alg_bytes = 0;
 };
@@ -137,10 +137,10 @@ static Sec sec_of(const SecBuf &b) {
   return s;
 }
 
-static Tmp tmp_of(long long *v, short *gr, int *meta) {
+static Tmp tmp_of(long long *v, int *gb, int *meta) {
   Tmp t;
   t.v = v;
-  t.gr = gr;
+  t.gb = gb;
   t.meta = meta;
   return t;
 }
@@ -157,6 +157,7 @@ static double tmp_bytes(const Geo &g) { return 8.0 * (double)g.nz * g.n * g.n; }
 
 static void ev_begin(cmg_ctx *c, KStat &k) {
   if (!c->timing) return;
+  if (k.ev.size() > 100000) return;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -167,9 +168,12 @@ static void ev_begin(cmg_ctx *c, KStat &k) {
 static void ev_end(cmg_ctx *c, KStat &k, double bytes) {
   k.launches++;
   k.bytes += bytes;
-  if (!c->timing) return;
+  if (!c->timing || k.ev.empty() || k.ev.size() > 100000) return;
   cudaEventRecord(k.ev.back().second, c->st);
 }
+
+// statistics slot of a kernel launch on level l
+static KStat &kstat(cmg_ctx *c, int kind, int l) { return c->stats[kind][l == c->P.L_max ? 1 : 0]; }
 
 static void ev_collect(KStat &k) {
   for (auto &p : k.ev) {
@@ -241,8 +245,10 @@ extern "C" void cmg_destroy(cmg_ctx *ctx) {
     cudaFree(v.uhg);
     cudaFree(v.wg);
   }
-  stat_reset(ctx->st_sweep);
-  stat_reset(ctx->st_resid);
+  for (int k = 0; k < CMG_KIND_COUNT; k++) {
+    stat_reset(ctx->stats[k][0]);
+    stat_reset(ctx->stats[k][1]);
+  }
   cudaFree(ctx->meta_pool);
   cudaFree(ctx->err);
   cudaFree(ctx->tables);
@@ -296,8 +302,8 @@ extern "C" cmg_status cmg_create(const cmg_params *p, void *stream, cmg_ctx **ou
       chk(cudaMalloc(&v.uh, nt * 8));
       chk(cudaMalloc(&v.w, nt * 8));
       chk(cudaMalloc(&v.acc, nt * 8));
-      chk(cudaMalloc(&v.uhg, (size_t)g.nblocks * sizeof(short)));
-      chk(cudaMalloc(&v.wg, (size_t)g.nblocks * sizeof(short)));
+      chk(cudaMalloc(&v.uhg, (size_t)g.nblocks * sizeof(int)));
+      chk(cudaMalloc(&v.wg, (size_t)g.nblocks * sizeof(int)));
       if (r == CMG_OK) {
         chk(cudaMemsetAsync(v.acc, 0, nt * 8, ctx->st));
         chk(cudaMemsetAsync(v.uh, 0, nt * 8, ctx->st));
@@ -410,7 +416,9 @@ static cmg_status run_chain(cmg_ctx *ctx, int upto) {
     if (l > 1) a.uhc = tmp_of(ctx->lv[l - 1].uh, ctx->lv[l - 1].uhg, nullptr);
     a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
     a.err = ctx->err;
+    ev_begin(ctx, kstat(ctx, CMG_KIND_OTHER, l));
     launch_chain(ctx->P.dim, a, ctx->st);
+    ev_end(ctx, kstat(ctx, CMG_KIND_OTHER, l), sec_bytes(v.g, v.u.W) + tmp_bytes(v.g));
     cmg_status s = launched(ctx, sec_bytes(v.g, v.u.W) + tmp_bytes(v.g) + (l > 1 ? tmp_bytes(a.gc) : 0));
     if (s) return s;
   }
@@ -472,9 +480,9 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
   a.err = ctx->err;
   double bytes = sec_bytes(v.g, v.u.W) + (L > 1 ? tmp_bytes(a.gc) : 0) + sec_bytes(v.g, v.r.W) +
                  (first_sweep ? sec_bytes(v.g, v.r.W) : 0) + (chain ? sec_bytes(v.g, Wt) : 0);
-  ev_begin(ctx, ctx->st_resid);
+  ev_begin(ctx, kstat(ctx, CMG_KIND_RESIDUAL, L));
   launch_residual(d, a, ctx->st);
-  ev_end(ctx, ctx->st_resid, bytes);
+  ev_end(ctx, kstat(ctx, CMG_KIND_RESIDUAL, L), bytes);
   if ((s = launched(ctx, bytes))) return s;
   if (chain) {  // t^_l = round(R t^_(l+1)), r_l = round(t^_l) (Algorithm 2)
     for (int l = L; l >= 2; l--) {
@@ -487,7 +495,9 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
       if ((s = fresh_tmp_meta(ctx, c.accmeta))) return s;
       ra.acc = tmp_of(c.acc, nullptr, c.accmeta);
       ra.err = ctx->err;
+      ev_begin(ctx, kstat(ctx, CMG_KIND_RESTRICT, l));
       launch_restrict(d, ra, ctx->st);
+      ev_end(ctx, kstat(ctx, CMG_KIND_RESTRICT, l), sec_bytes(f.g, Wt) + 2 * tmp_bytes(c.g));
       if ((s = launched(ctx, sec_bytes(f.g, Wt) + 2 * tmp_bytes(c.g)))) return s;
       AccArgs b{};
       b.g = c.g;
@@ -501,7 +511,9 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
       b.t_out = sec_of(c.t);
       jacobi_factor(ctx, l - 1, b.c_num, b.c_exp, b.cbits);
       b.err = ctx->err;
+      ev_begin(ctx, kstat(ctx, CMG_KIND_ACC_ENCODE, l));
       launch_acc_encode(d, b, ctx->st);
+      ev_end(ctx, kstat(ctx, CMG_KIND_ACC_ENCODE, l), 2 * tmp_bytes(c.g) + sec_bytes(c.g, c.r.W) + sec_bytes(c.g, Wt));
       if ((s = launched(ctx, 2 * tmp_bytes(c.g) + sec_bytes(c.g, c.r.W) + sec_bytes(c.g, Wt)))) return s;
     }
   }
@@ -555,10 +567,9 @@ static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
                  (o.has_z ? tmp_bytes(a.gc) : 0) + (o.write_y ? sec_bytes(v.g, a.Wy) : 0) +
                  (o.corr ? 2 * sec_bytes(v.g, a.u_out.W) : 0) + (o.write_w ? tmp_bytes(v.g) : 0) +
                  (o.write_uh ? tmp_bytes(v.g) + tmp_bytes(a.gc) : 0);
-  const bool finest = (l == L);
-  if (finest) ev_begin(ctx, ctx->st_sweep);
+  ev_begin(ctx, kstat(ctx, CMG_KIND_SWEEP, l));
   launch_sweep(d, a, ctx->st);
-  if (finest) ev_end(ctx, ctx->st_sweep, bytes);
+  ev_end(ctx, kstat(ctx, CMG_KIND_SWEEP, l), bytes);
   if ((s = launched(ctx, bytes))) return s;
   if (o.write_y) {
     v.ycur = 1 - v.ycur;
@@ -582,7 +593,9 @@ static cmg_status do_restrict(cmg_ctx *ctx, int l, bool first_sweep_below) {
   }
   a.acc = tmp_of(c.acc, nullptr, c.accmeta);
   a.err = ctx->err;
+  ev_begin(ctx, kstat(ctx, CMG_KIND_RESTRICT, l));
   launch_restrict(d, a, ctx->st);
+  ev_end(ctx, kstat(ctx, CMG_KIND_RESTRICT, l), sec_bytes(v.g, a.y.W) + sec_bytes(v.g, a.rc.W) + 2 * tmp_bytes(c.g));
   cmg_status s = launched(ctx, sec_bytes(v.g, a.y.W) + sec_bytes(v.g, a.rc.W) + 2 * tmp_bytes(c.g));
   if (s) return s;
   AccArgs b{};
@@ -603,8 +616,11 @@ static cmg_status do_restrict(cmg_ctx *ctx, int l, bool first_sweep_below) {
   b.chain = 0;
   jacobi_factor(ctx, l - 1, b.c_num, b.c_exp, b.cbits);
   b.err = ctx->err;
+  const double bb = 2 * tmp_bytes(c.g) + sec_bytes(c.g, c.rc.W) * (first_sweep_below ? 2 : 1);
+  ev_begin(ctx, kstat(ctx, CMG_KIND_ACC_ENCODE, l));
   launch_acc_encode(d, b, ctx->st);
-  return launched(ctx, 2 * tmp_bytes(c.g) + sec_bytes(c.g, c.rc.W) * (first_sweep_below ? 2 : 1));
+  ev_end(ctx, kstat(ctx, CMG_KIND_ACC_ENCODE, l), bb);
+  return launched(ctx, bb);
 }
 
 static cmg_status do_coarse(cmg_ctx *ctx, bool start, bool corr) {
@@ -640,7 +656,9 @@ static cmg_status do_coarse(cmg_ctx *ctx, bool start, bool corr) {
     a.w_out = tmp_of(v.w, v.wg, nullptr);
     if (corr) a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
   }
+  ev_begin(ctx, kstat(ctx, CMG_KIND_COARSE, 1));
   launch_coarse(a, ctx->st);
+  ev_end(ctx, kstat(ctx, CMG_KIND_COARSE, 1), 64);
   if ((s = launched(ctx, 64))) return s;
   if (!start && corr) std::swap(v.u, v.u_alt);
   return CMG_OK;
@@ -686,7 +704,9 @@ extern "C" cmg_status cmg_prolongate(cmg_ctx *ctx) {
     if ((s = fresh_meta(ctx, v.u_alt))) return s;
     a.out = sec_of(v.u_alt);
     a.nblocks = v.g.nblocks;
+    ev_begin(ctx, kstat(ctx, CMG_KIND_REPACK, l));
     launch_repack(a, ctx->st);
+    ev_end(ctx, kstat(ctx, CMG_KIND_REPACK, l), sec_bytes(v.g, v.u.W) + sec_bytes(v.g, Wn));
     if ((s = launched(ctx, sec_bytes(v.g, v.u.W) + sec_bytes(v.g, Wn)))) return s;
     std::swap(v.u, v.u_alt);
   }
@@ -824,8 +844,10 @@ extern "C" cmg_status cmg_sync(cmg_ctx *ctx) {
 
 extern "C" cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *rep) {
   if (!ctx) return CMG_EINVAL;
-  stat_reset(ctx->st_sweep);
-  stat_reset(ctx->st_resid);
+  for (int k = 0; k < CMG_KIND_COUNT; k++) {
+    stat_reset(ctx->stats[k][0]);
+    stat_reset(ctx->stats[k][1]);
+  }
   ctx->launches = 0;
   ctx->alg_bytes = 0;
   cudaEvent_t e0, e1;
@@ -860,15 +882,29 @@ extern "C" cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *rep) {
     }
     rep->persistent_bits = bits;
     rep->temp_bytes = tb;
-    ev_collect(ctx->st_sweep);
-    ev_collect(ctx->st_resid);
-    rep->sweep_ms_total = ctx->st_sweep.ms;
-    rep->sweep_launches = ctx->st_sweep.launches;
-    rep->sweep_alg_bytes = ctx->st_sweep.bytes;
-    rep->resid_ms_total = ctx->st_resid.ms;
-    rep->resid_launches = ctx->st_resid.launches;
-    rep->resid_alg_bytes = ctx->st_resid.bytes;
+    for (int k = 0; k < CMG_KIND_COUNT; k++) {
+      ev_collect(ctx->stats[k][0]);
+      ev_collect(ctx->stats[k][1]);
+    }
+    const KStat &sw = ctx->stats[CMG_KIND_SWEEP][1], &rs = ctx->stats[CMG_KIND_RESIDUAL][1];
+    rep->sweep_ms_total = sw.ms;
+    rep->sweep_launches = sw.launches;
+    rep->sweep_alg_bytes = sw.bytes;
+    rep->resid_ms_total = rs.ms;
+    rep->resid_launches = rs.launches;
+    rep->resid_alg_bytes = rs.bytes;
   }
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_kernel_stats(cmg_ctx *ctx, int kind, int top, double *ms, int64_t *launches,
+                                       double *bytes) {
+  if (!ctx || kind < 0 || kind >= CMG_KIND_COUNT || top < 0 || top > 1) return CMG_EINVAL;
+  KStat &k = ctx->stats[kind][top];
+  ev_collect(k);
+  if (ms) *ms = k.ms;
+  if (launches) *launches = k.launches;
+  if (bytes) *bytes = k.bytes;
   return CMG_OK;
 }
 

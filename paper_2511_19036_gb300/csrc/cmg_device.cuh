@@ -8,8 +8,9 @@
 // bits, than interior blocks), so one grid per array would need far more than
 // 64 bits:
 //   * BFP sections carry their grid in each block exponent (e - W + 1);
-//   * int64 temporaries (decoded solution chain, w = y~ + z) carry one grid per
-//     32-value block, written by the warp that produced the block;
+//   * int64 temporaries (decoded solution chain, w = y~ + z) carry one
+//     descriptor per 32-value block, written by the warp that produced the
+//     block: its grid and the bit length of its largest magnitude;
 //   * a stencil kernel converts its operand to one grid per CTA tile, the
 //     finest grid found in the tile's footprint;
 //   * each warp chooses the grid of its output block from its own inputs.
@@ -31,7 +32,6 @@ namespace cmg {
 constexpr int META_BIAS = 1000;
 constexpr int GRID_NONE = 1 << 20;    // grid of an all-zero input: no constraint
 constexpr int MAG_NONE = -(1 << 20);  // magnitude exponent of an all-zero input
-constexpr short GR_NONE = 32767;      // per-block grid of an all-zero temporary block
 
 // error flags accumulated in a device word
 constexpr int ERR_EXP = 1;      // block exponent outside [-127, 127]
@@ -61,7 +61,7 @@ struct Sec {
 
 struct Tmp {
   long long *v;     // padded layout ((k*n + j)*R + i)
-  short *gr;        // per 32-value block grid (temporaries); nullptr for accumulators
+  int *gb;          // per 32-value block descriptor (grid << 8 | bits); nullptr for accumulators
   int *meta;        // accumulators: {G, unused}
 };
 
@@ -91,7 +91,10 @@ __device__ inline int sec_msb(const Sec &s) {  // |value| < 2^msb
   return m0 - META_BIAS;
 }
 __device__ __forceinline__ int blk_lsb(int e, int W) { return e == -128 ? GRID_NONE : e - W + 1; }
-__device__ __forceinline__ int gr_of(short g) { return g == GR_NONE ? GRID_NONE : (int)g; }
+// temporary block descriptor: values v of the block stand for v * 2^grid with
+// |v| < 2^bits; bits == 0 marks an all-zero block
+__device__ __forceinline__ int gb_grid(int gb) { return (gb & 0xff) ? (gb >> 8) : GRID_NONE; }
+__device__ __forceinline__ int gb_mag(int gb) { return (gb & 0xff) ? (gb >> 8) + (gb & 0xff) : MAG_NONE; }
 
 // ---------------------------------------------------------------- checked integer ops
 // exact left shift of an int64 (0 stays 0)
@@ -162,7 +165,7 @@ __device__ __forceinline__ long long tmp_raw(const Tmp &t, const Geo &g, int i, 
     G = GRID_NONE;
     return 0;
   }
-  G = gr_of(__ldg(t.gr + blk_index(g, i, j, k)));
+  G = gb_grid(__ldg(t.gb + blk_index(g, i, j, k)));
   return __ldg(t.v + ((long long)k * g.n + j) * g.R + i);
 }
 
@@ -202,9 +205,9 @@ template <int DIM>
 __device__ __forceinline__ int prolong_grid(const Tmp &c, const Geo &gc, int I, int J, int K) {
   Parents<DIM> p(I, J, K);
   int G = GRID_NONE;
-  if (inside(gc, p.ia, p.ja, p.ka)) G = gr_of(__ldg(c.gr + blk_index(gc, p.ia, p.ja, p.ka)));
+  if (inside(gc, p.ia, p.ja, p.ka)) G = gb_grid(__ldg(c.gb + blk_index(gc, p.ia, p.ja, p.ka)));
   if (!p.two) return G;
-  if (inside(gc, p.ib, p.jb, p.kb)) G = imin(G, gr_of(__ldg(c.gr + blk_index(gc, p.ib, p.jb, p.kb))));
+  if (inside(gc, p.ib, p.jb, p.kb)) G = imin(G, gb_grid(__ldg(c.gb + blk_index(gc, p.ib, p.jb, p.kb))));
   return G >= GRID_NONE / 2 ? G : G - 1;
 }
 
@@ -271,22 +274,24 @@ __device__ __forceinline__ void pack_block(int q, int W, uint32_t *scratch, uint
 
 // Warp-collective store of one 32-value block of a temporary: the values v on
 // grid G are renormalised to the coarsest grid that holds them all exactly
-// (common trailing zero bits removed) and written with that block grid.
-__device__ __forceinline__ void store_tmp_block(long long v, int G, long long *dst, short *gr, bool active,
+// (common trailing zero bits removed) and written with the block descriptor.
+__device__ __forceinline__ void store_tmp_block(long long v, int G, long long *dst, int *gb, bool active,
                                                 bool &ovf) {
   unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)(unsigned long long)v);
   unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)((unsigned long long)v >> 32));
   int lane = threadIdx.x & 31;
   if (!(lo | hi)) {  // all-zero block
     if (active) *dst = 0;
-    if (lane == 0) *gr = GR_NONE;
+    if (lane == 0) *gb = 0;
     return;
   }
   int tz = lo ? __ffs(lo) - 1 : 32 + __ffs(hi) - 1;
+  long long vn = v >> tz;
+  int bits = __reduce_max_sync(0xffffffffu, bitlen64(vn));
   int g = G + tz;
-  if (g > 32000 || g < -32000) ovf = true;
-  if (active) *dst = v >> tz;
-  if (lane == 0) *gr = (short)g;
+  if (g > (1 << 22) || g < -(1 << 22)) ovf = true;
+  if (active) *dst = vn;
+  if (lane == 0) *gb = (int)((unsigned)g << 8) | bits;
 }
 
 // CTA-level reduction of written exponents into the section metadata.

@@ -78,7 +78,7 @@ extern "C" size_t cmg_decode_compact_scratch_bytes(int dim, int L) {
   for (int l = 1; l < L; l++) {
     Geo g = geo_of(dim, l);
     need += round256((size_t)g.nz * g.n * g.R * sizeof(long long));
-    need += round256((size_t)g.nblocks * sizeof(short));
+    need += round256((size_t)g.nblocks * sizeof(int));
   }
   return need;
 }
@@ -113,8 +113,8 @@ extern "C" cmg_status cmg_decode_compact(int dim, int L, const uint32_t *const *
     Tmp cur{};
     cur.v = (long long *)p;
     p += round256((size_t)g.nz * g.n * g.R * sizeof(long long));
-    cur.gr = (short *)p;
-    p += round256((size_t)g.nblocks * sizeof(short));
+    cur.gb = (int *)p;
+    p += round256((size_t)g.nblocks * sizeof(int));
     ChainArgs a{};
     a.g = g;
     a.gc = l > 1 ? geo_of(dim, l - 1) : g;
