@@ -30,6 +30,8 @@ WORKLOADS = {
     "poisson3d_2049": ("poisson3d_manufactured", 11,
                        "3-D Poisson 2049^3 grid (2047^3 = 8.58e9 interior DoF), zero Dirichlet, "
                        "RHS matrix-free from u=sin(pi x)sin(pi y)sin(pi z)(1+x^2yz)"),
+    "poisson3d_513": ("poisson3d_manufactured", 9,
+                      "3-D Poisson 513^3 grid (511^3 = 1.33e8 DoF), same RHS as poisson3d_2049"),
     "poisson3d_257": ("poisson3d_fourier", 8,
                       "3-D Poisson 257^3 grid (255^3 DoF), RHS = 8 seeded Fourier modes"),
     "poisson2d_257": ("poisson2d_manufactured", 8,
