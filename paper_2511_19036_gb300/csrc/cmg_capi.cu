@@ -62,7 +62,7 @@ struct cmg_ctx {
   int meta_next = 1;  // slot 0 stays all-zero: the metadata of an all-zero section
   int *err = nullptr;
   int32_t *tables = nullptr;
-  int nterms = 0, scale_exp = 0, fsh = 0;
+  int nterms = 0, scale_exp = 0, fsh = 0, rhs_bits = 0;
   std::vector<int32_t> tables_host;
   bool have_rhs = false;
   int uh_upto = 0;  // u^_1 .. u^_uh_upto agree with the current u~
@@ -364,6 +364,7 @@ extern "C" cmg_status cmg_set_rhs_separable(cmg_ctx *ctx, int nterms, const int3
   ctx->nterms = nterms;
   ctx->scale_exp = scale_exp;
   ctx->fsh = B > 50 ? B - 50 : 0;
+  ctx->rhs_bits = B;
   ctx->have_rhs = true;
   return CMG_OK;
 }
@@ -453,6 +454,7 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
   a.n1max = (1 << ctx->P.L_max) - 1;
   a.Lmax = ctx->P.L_max;
   a.fsh = ctx->fsh;
+  a.rhs_bits = ctx->rhs_bits;
   a.Gf = ctx->scale_exp + ctx->fsh - d * L;
   v.r.W = Wr(ctx, L, L);
   cmg_status s = fresh_meta(ctx, v.r);

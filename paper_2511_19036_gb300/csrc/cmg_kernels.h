@@ -31,6 +31,7 @@ struct ResidArgs {
   Tmp uhc;             // u^_(L-1)
   const int32_t *tables;
   int nterms, n1max, Lmax, fsh;
+  int rhs_bits;        // bit length of the bound sum_t prod_a max|T| on |F_q| before the shift
   int Gf;              // grid of f_L: scale_exp + fsh - d L
   Sec r_out;
   int first_sweep;     // also y~ = round(c r)

@@ -1,0 +1,919 @@
+// Stencil kernels of the compact FMG path for GB300 (sm_103a): the weighted
+// Jacobi sweep, the residual of Algorithm 2 and the restriction R_l = P_l^T.
+//
+// Tiling.  A CTA of TY warps owns a 32 x TY column tile of a level and marches
+// it through up to ZC planes in z.  Thread (lane, ty) owns the column
+// (x0 + lane, j0 + ty): it decodes the stencil operand F of that column once
+// per plane and keeps the planes k-1, k, k+1 in registers, so only the
+// in-plane neighbours go through shared memory (two plane buffers of
+// (TY + 2) x 34 values; warps 0-2 also decode the halo).  One CTA barrier per
+// plane separates writing plane k+1 from reading plane k.
+//
+// Latency.  The compact words and block exponents of plane k+2 (operand) and
+// k+1 (per-kernel inputs such as r~c or u~) are loaded into registers one plane
+// ahead of their use, so that decoding never waits on a global load that was
+// issued in the same plane.
+//
+// Operand F = [BFP section s] + [P_l t] (t an int64 coarse temporary with one
+// descriptor per block).  The coarse values P_l needs are staged once per CTA
+// and coarse plane in a ring of four planes (7 x 19 values around the tile) on
+// one grid, with all-zero planes at both ends of the level, so a fine value of
+// P_l t is two shared-memory reads at offsets fixed per thread.  A second ring
+// serves P_l u^_(l-1) for the fused u^_l = u~_l + P_l u^_(l-1) of the last
+// up-sweep.
+//
+// Exactness (see cmg_device.cuh): F is converted to the finest grid found in
+// the CTA's footprint; each warp picks the grid of its output block; per-value
+// overflow checks run only for blocks whose static bounds do not fit.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cmg_device.cuh"
+#include "cmg_kernels.h"
+
+namespace cmg {
+namespace {
+
+constexpr int CR = 7;               // coarse rows feeding fine rows j0-1 .. j0+TY
+constexpr int CX = 19;              // coarse columns feeding fine columns x0-1 .. x0+32
+constexpr int CRX = CR * CX;        // values of one ring plane
+constexpr int PW = 34;              // plane buffer row: 32 values and one halo value each side
+constexpr int PLANE = (TY + 2) * PW;
+constexpr int NHALO = 2 * 32 + 2 * (TY + 2);  // halo values of one plane
+constexpr int TMAX = 16;            // right-hand-side terms held in shared memory
+
+__device__ inline bool first_cta() { return blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0; }
+
+// ------------------------------------------------------------------ compact reads
+struct Raw {
+  int e;            // block exponent (-128: all-zero block or outside)
+  uint32_t w0, w1;  // the word(s) holding the code
+};
+
+struct CodePos {
+  int woff, boff, two;  // word offset in the block, bit offset, code spans two words
+};
+
+__device__ __forceinline__ CodePos code_pos(int x, int W) {
+  CodePos c;
+  const int pos = x * W;
+  c.woff = pos >> 5;
+  c.boff = pos & 31;
+  c.two = c.boff + W > 32;
+  return c;
+}
+
+// issue the loads of one code and its block exponent (no use of the result yet)
+__device__ __forceinline__ Raw raw_load(const Sec &s, long long blk, CodePos cp, bool ok) {
+  Raw r;
+  r.e = -128;
+  r.w0 = 0u;
+  r.w1 = 0u;
+  if (ok) {
+    r.e = __ldg(s.exps + blk);
+    const uint32_t *w = s.words + blk * s.W + cp.woff;
+    r.w0 = __ldg(w);
+    if (cp.two) r.w1 = __ldg(w + 1);
+  }
+  return r;
+}
+
+__device__ __forceinline__ int raw_code(const Raw &r, int boff, int W) {
+  const uint32_t bits = __funnelshift_r(r.w0, r.w1, boff);
+  return ((int)(bits << (32 - W))) >> (32 - W);
+}
+
+// the value on grid G (G at or below the block's grid e - W + 1)
+__device__ __forceinline__ long long raw_val(const Raw &r, int boff, int W, int G) {
+  if (r.e == -128) return 0;
+  return (long long)((unsigned long long)(long long)raw_code(r, boff, W) << (r.e - W + 1 - G));
+}
+
+// ------------------------------------------------------------------ tile geometry
+struct Tile {
+  int bx, x0, j0, k0, k1;
+  int cr0, cx0;  // coarse row / column of ring entry (0, 0)
+};
+
+__device__ __forceinline__ Tile make_tile(const Geo &g) {
+  Tile T;
+  T.bx = blockIdx.x;
+  T.x0 = T.bx * 32;
+  T.j0 = blockIdx.y * TY;
+  T.k0 = blockIdx.z * ZC;
+  T.k1 = imin(g.nz, T.k0 + ZC);
+  T.cr0 = ((T.j0 - 1) >> 1) - 1;
+  T.cx0 = ((T.x0 - 1) >> 1) - 1;
+  return T;
+}
+
+// One decode slot of a thread: a fixed (i, j) column of the CTA footprint.
+struct Slot {
+  bool ok;     // (i, j) inside the level's plane
+  int bip;     // block index inside a plane
+  int sm;      // index in a plane buffer
+  int oa, ob;  // P_l parents of (i, j) in a ring plane (row * CX + column)
+  CodePos cp;  // code position for the operand section's width
+};
+
+// (i, j) fine 0-based, (r, x) its place in the plane buffer.  The parents of
+// every footprint node fall in ring rows 1..6 and columns 1..18.
+__device__ __forceinline__ Slot make_slot(const Geo &g, int W, int i, int j, int r, int x, const Tile &T) {
+  Slot s;
+  s.ok = (unsigned)i < (unsigned)g.n && (unsigned)j < (unsigned)g.n;
+  s.bip = s.ok ? j * g.nbx + (i >> 5) : 0;
+  s.sm = r * PW + x;
+  const int I = i + 1, J = j + 1, sx = I & 1, sy = J & 1;
+  s.oa = (((J - sy) >> 1) - 1 - T.cr0) * CX + (((I - sx) >> 1) - 1 - T.cx0);
+  s.ob = (((J + sy) >> 1) - 1 - T.cr0) * CX + (((I + sx) >> 1) - 1 - T.cx0);
+  s.cp = code_pos(i & 31, W);
+  return s;
+}
+
+// coarse planes of the P_l parents of fine plane kf (3-D): K = kf + 1 odd has
+// parents in planes kf/2 - 1 and kf/2, K even in (kf - 1)/2 only
+template <int DIM>
+__device__ __forceinline__ void zparents(int kf, int &za, int &zb) {
+  if (DIM == 2) {
+    za = zb = 0;
+  } else if (kf & 1) {
+    za = zb = (kf - 1) >> 1;
+  } else {
+    za = (kf >> 1) - 1;
+    zb = kf >> 1;
+  }
+}
+
+// (P_l t) at a slot from a ring, on the ring's grid minus one
+__device__ __forceinline__ long long ring_p(const long long *ring, const Slot &s, int za, int zb) {
+  return ring[(za & 3) * CRX + s.oa] + ring[(zb & 3) * CRX + s.ob];
+}
+
+// One ring entry per thread (tid < CRX): a fixed coarse (ci, cj) column.
+struct Stager {
+  bool on, ok;
+  int bip;          // block index inside a coarse plane
+  long long vip;    // value index inside a coarse plane
+  long long v;      // loaded value, not yet stored
+  int gb;           // loaded descriptor
+};
+
+__device__ __forceinline__ Stager make_stager(const Geo &gc, const Tile &T, int tid) {
+  Stager s;
+  s.on = tid < CRX;
+  const int r = tid / CX, x = tid - (tid / CX) * CX;
+  const int cj = T.cr0 + r, ci = T.cx0 + x;
+  s.ok = s.on && (unsigned)ci < (unsigned)gc.n && (unsigned)cj < (unsigned)gc.n;
+  s.bip = s.ok ? cj * gc.nbx + (ci >> 5) : 0;
+  s.vip = s.ok ? (long long)cj * gc.R + ci : 0;
+  s.v = 0;
+  s.gb = 0;
+  return s;
+}
+
+__device__ __forceinline__ void stage_load(Stager &s, const Tmp &t, const Geo &gc, int c) {
+  s.v = 0;
+  s.gb = 0;
+  if (s.ok && (unsigned)c < (unsigned)gc.nz) {
+    s.gb = __ldg(t.gb + (long long)c * gc.n * gc.nbx + s.bip);
+    s.v = __ldg(t.v + (long long)c * gc.n * gc.R + s.vip);
+  }
+}
+
+__device__ __forceinline__ void stage_store(const Stager &s, long long *ring, int c, int G1, int tid) {
+  if (s.on) ring[(c & 3) * CRX + tid] = (s.gb & 0xff) ? shl(s.v, (s.gb >> 8) - G1) : 0;
+}
+
+// ------------------------------------------------------------------ footprint bounds
+struct Bounds {
+  int G;  // finest grid (GRID_NONE: all zero)
+  int M;  // |v| < 2^M (MAG_NONE: all zero)
+};
+
+// Scans the CTA footprint: the exponents of section s over planes k0-1..k1,
+// rows j0-1..j0+TY and blocks bx-1..bx+1, and the descriptors of the coarse
+// temporaries t and u over the coarse planes, rows and blocks P_l reads.
+// sm: 6 ints; ends with a CTA barrier.
+template <int DIM>
+__device__ __forceinline__ void footprint_bounds(const Geo &g, const Geo &gc, const Tile &T, const Sec &s,
+                                                 bool has_s, const Tmp &t, bool has_t, const Tmp &u, bool has_u,
+                                                 int *sm, Bounds &bs, Bounds &bt, Bounds &bu) {
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid == 0) {
+    sm[0] = sm[2] = sm[4] = GRID_NONE;
+    sm[1] = sm[3] = sm[5] = MAG_NONE;
+  }
+  __syncthreads();
+  const int klo = DIM == 3 ? T.k0 - 1 : 0, khi = DIM == 3 ? T.k1 : 0;
+  if (has_s) {
+    int G = GRID_NONE, M = MAG_NONE;
+    const int per = (TY + 2) * 3, cnt = (khi - klo + 1) * per;
+    for (int idx = tid; idx < cnt; idx += NT) {
+      const int kk = klo + idx / per, rem = idx - (idx / per) * per;
+      const int jj = T.j0 - 1 + rem / 3, bb = T.bx - 1 + rem % 3;
+      if ((unsigned)kk < (unsigned)g.nz && (unsigned)jj < (unsigned)g.n && (unsigned)bb < (unsigned)g.nbx) {
+        const int e = __ldg(s.exps + ((long long)kk * g.n + jj) * g.nbx + bb);
+        if (e != -128) {
+          G = imin(G, e - s.W + 1);
+          M = imax(M, e);
+        }
+      }
+    }
+    if (G < GRID_NONE / 2) atomicMin(sm, G);
+    if (M > MAG_NONE / 2) atomicMax(sm + 1, M);
+  }
+  if (has_t || has_u) {
+    const int cj0 = imax(0, T.cr0), cj1 = imin(gc.n - 1, T.cr0 + CR - 1);
+    const int ck0 = DIM == 3 ? imax(0, (klo - 1) >> 1) : 0;
+    const int ck1 = DIM == 3 ? imin(gc.nz - 1, khi >> 1) : 0;
+    const int cb0 = imax(0, T.cx0) >> 5, cb1 = imin(gc.n - 1, T.cx0 + CX - 1) >> 5;
+    const int nb = cb1 - cb0 + 1, nr = cj1 - cj0 + 1, np = ck1 - ck0 + 1;
+    if (nb > 0 && nr > 0 && np > 0) {
+      const int cnt = nb * nr * np;
+      for (int which = 0; which < 2; which++) {
+        if (!(which ? has_u : has_t)) continue;
+        const int *xgb = which ? u.gb : t.gb;
+        int G = GRID_NONE, M = MAG_NONE;
+        for (int idx = tid; idx < cnt; idx += NT) {
+          const int kk = ck0 + idx / (nb * nr), rem = idx % (nb * nr);
+          const int jj = cj0 + rem / nb, bb = cb0 + rem % nb;
+          const int gbv = __ldg(xgb + ((long long)kk * gc.n + jj) * gc.nbx + bb);
+          if (gbv & 0xff) {
+            G = imin(G, gb_grid(gbv));
+            M = imax(M, gb_mag(gbv));
+          }
+        }
+        if (G < GRID_NONE / 2) atomicMin(sm + 2 + 2 * which, G);
+        if (M > MAG_NONE / 2) atomicMax(sm + 3 + 2 * which, M);
+      }
+    }
+  }
+  __syncthreads();
+  bs.G = sm[0];
+  bs.M = sm[1];
+  bt.G = sm[2];
+  bt.M = sm[3];
+  bu.G = sm[4];
+  bu.M = sm[5];
+}
+
+// Operand bounds: F = s + P t on grid GF = min(G_s, G_t - 1), |F| < 2^MF.
+__device__ __forceinline__ Bounds operand_of(const Bounds &bs, const Bounds &bt) {
+  Bounds b;
+  b.G = imin(bs.G, bt.G < GRID_NONE / 2 ? bt.G - 1 : GRID_NONE);
+  const int M = imax(bs.M, bt.M);
+  b.M = M > MAG_NONE / 2 ? M + 1 : MAG_NONE;
+  return b;
+}
+
+// ------------------------------------------------------------------ the z-march
+struct SmemTile {
+  long long Fs[2][PLANE];   // in-plane operand, double-buffered
+  long long ring[4 * CRX];  // coarse ring of the operand's P_l t
+  long long ringu[4 * CRX]; // coarse ring of P_l u^_(l-1)
+};
+
+struct MarchIn {
+  Sec s;         // operand section (if has_s)
+  Tmp t;         // operand coarse temporary (if has_t)
+  Tmp u;         // second ring (if has_u)
+  bool has_s, has_t, has_u;
+  int GF;        // operand grid
+  int G1t, G1u;  // staging grids of the rings
+};
+
+// Calls, for every plane k of the tile in order, body.advance() (what
+// body.prefetch(k) loaded becomes current), body.prefetch(k + 1) (loads for
+// the next plane) and body.out(k, S, s0, F0, Pu): S = (2d) F - sum of the 2d
+// neighbours at the thread's node (grid GF), s0 its section part, F0 its
+// operand, Pu the value of P_l u at the node (grid G1u - 1).  Every thread of
+// the CTA calls it.
+template <int DIM, class Body>
+__device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T, const MarchIn &in, SmemTile &sm,
+                                      Body &body) {
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
+  const int Ws = in.has_s ? in.s.W : 1;
+  const Slot own = make_slot(g, Ws, T.x0 + lane, T.j0 + ty, ty + 1, lane + 1, T);
+  // halo: warp 0 row j0-1, warp 1 row j0+TY, warp 2 the columns x0-1 and x0+32
+  const bool has_h = tid < NHALO;
+  Slot hal;
+  {
+    int i, j, r, x;
+    if (tid < 32) {
+      i = T.x0 + tid, j = T.j0 - 1, r = 0, x = tid + 1;
+    } else if (tid < 64) {
+      i = T.x0 + tid - 32, j = T.j0 + TY, r = TY + 1, x = tid - 31;
+    } else {
+      const int c = imin(tid - 64, 2 * (TY + 2) - 1);
+      r = c >> 1, j = T.j0 - 1 + r;
+      x = (c & 1) ? 33 : 0;
+      i = (c & 1) ? T.x0 + 32 : T.x0 - 1;
+    }
+    hal = make_slot(g, Ws, i, j, r, x, T);
+  }
+  const long long pb = (long long)g.n * g.nbx;  // blocks per plane
+  const bool rings = in.has_t || in.has_u;
+  Stager st0 = make_stager(gc, T, tid), st1 = st0;
+  const bool has_s = in.has_s;
+  auto raw_at = [&](const Slot &sl, int kf) -> Raw {
+    return raw_load(in.s, kf * pb + sl.bip, sl.cp, has_s && sl.ok && (unsigned)kf < (unsigned)g.nz);
+  };
+  auto F_at = [&](const Slot &sl, const Raw &r, int kf, long long &sv) -> long long {
+    sv = has_s ? raw_val(r, sl.cp.boff, Ws, in.GF) : 0;
+    if (!in.has_t) return sv;
+    int za, zb;
+    zparents<DIM>(kf, za, zb);
+    return sv + ring_p(sm.ring, sl, za, zb);
+  };
+  auto pu_at = [&](int kf) -> long long {
+    if (!in.has_u) return 0;
+    int za, zb;
+    zparents<DIM>(kf, za, zb);
+    return ring_p(sm.ringu, own, za, zb);
+  };
+
+  if (DIM == 2) {
+    if (rings) {
+      if (in.has_t) stage_load(st0, in.t, gc, 0);
+      if (in.has_u) stage_load(st1, in.u, gc, 0);
+      if (in.has_t) stage_store(st0, sm.ring, 0, in.G1t, tid);
+      if (in.has_u) stage_store(st1, sm.ringu, 0, in.G1u, tid);
+    }
+    body.prefetch(0);
+    const Raw r0 = raw_at(own, 0);
+    Raw h0 = r0;
+    if (has_h) h0 = raw_at(hal, 0);
+    __syncthreads();
+    long long s0, sh;
+    const long long F0 = F_at(own, r0, 0, s0);
+    sm.Fs[0][own.sm] = F0;
+    if (has_h) sm.Fs[0][hal.sm] = F_at(hal, h0, 0, sh);
+    __syncthreads();
+    const long long *P = sm.Fs[0];
+    const long long S = 4 * F0 - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
+    body.advance();
+    body.out(0, S, s0, F0, pu_at(0));
+    return;
+  }
+
+  // 3-D: ring planes (k0 - 2)/2 .. k0/2 before the first decode
+  int staged_hi = -2;
+  if (rings) {
+    for (int c = (T.k0 - 2) >> 1; c <= (T.k0 >> 1); c++) {
+      if (in.has_t) stage_load(st0, in.t, gc, c);
+      if (in.has_u) stage_load(st1, in.u, gc, c);
+      if (in.has_t) stage_store(st0, sm.ring, c, in.G1t, tid);
+      if (in.has_u) stage_store(st1, sm.ringu, c, in.G1u, tid);
+    }
+    staged_hi = T.k0 >> 1;
+  }
+  const Raw rm = raw_at(own, T.k0 - 1);
+  const Raw r0 = raw_at(own, T.k0);
+  Raw h0 = rm, hn = rm;
+  if (has_h) h0 = raw_at(hal, T.k0);
+  Raw rn = raw_at(own, T.k0 + 1);
+  if (has_h) hn = raw_at(hal, T.k0 + 1);
+  body.prefetch(T.k0);
+  __syncthreads();
+  long long sx, s0, Fm, F0;
+  Fm = F_at(own, rm, T.k0 - 1, sx);
+  F0 = F_at(own, r0, T.k0, s0);
+  sm.Fs[T.k0 & 1][own.sm] = F0;
+  if (has_h) sm.Fs[T.k0 & 1][hal.sm] = F_at(hal, h0, T.k0, sx);
+
+  for (int k = T.k0; k < T.k1; k++) {
+    const int cs = (k + 2) >> 1;
+    const bool stage = rings && cs > staged_hi && cs <= gc.nz;
+    if (stage) {
+      if (in.has_t) stage_load(st0, in.t, gc, cs);
+      if (in.has_u) stage_load(st1, in.u, gc, cs);
+    }
+    body.advance();
+    if (k + 1 < T.k1) body.prefetch(k + 1);
+    Raw rn2 = rm, hn2 = rm;
+    if (k + 2 <= T.k1) rn2 = raw_at(own, k + 2);
+    if (has_h && k + 2 < T.k1) hn2 = raw_at(hal, k + 2);
+    __syncthreads();  // plane k complete in Fs[k & 1]; ring planes for k + 1 staged
+    long long sp;
+    const long long Fp = F_at(own, rn, k + 1, sp);
+    if (k + 1 < T.k1) {
+      long long* nxt = sm.Fs[(k + 1) & 1];
+      nxt[own.sm] = Fp;
+      if (has_h) nxt[hal.sm] = F_at(hal, hn, k + 1, sx);
+    }
+    const long long *P = sm.Fs[k & 1];
+    const long long S =
+        6 * F0 - Fm - Fp - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
+    body.out(k, S, s0, F0, pu_at(k));
+    if (stage) {
+      if (in.has_t) stage_store(st0, sm.ring, cs, in.G1t, tid);
+      if (in.has_u) stage_store(st1, sm.ringu, cs, in.G1u, tid);
+      staged_hi = cs;
+    }
+    Fm = F0;
+    F0 = Fp;
+    s0 = sp;
+    rn = rn2;
+    hn = hn2;
+  }
+}
+
+// March without an operand (F = 0): the body still sees every plane.
+template <class Body>
+__device__ __forceinline__ void march_none(const Tile &T, int nplanes_dim2, Body &body) {
+  const int k1 = nplanes_dim2 ? 1 : T.k1;
+  const int k0 = nplanes_dim2 ? 0 : T.k0;
+  body.prefetch(k0);
+  for (int k = k0; k < k1; k++) {
+    body.advance();
+    if (k + 1 < k1) body.prefetch(k + 1);
+    body.out(k, 0, 0, 0, 0);
+  }
+}
+
+// ------------------------------------------------------------------ sweep
+template <int DIM>
+struct SweepBody {
+  const SweepArgs &a;
+  const Geo &g;
+  int GF, MF, GA, MA, G1u;
+  bool ring_u;          // P_l u^_(l-1) from the ring (else per value from global memory)
+  int Mu;               // |P_l u^_(l-1)| < 2^Mu over the footprint
+  int bip, lane, ty, i, j;
+  bool rowok, pt;
+  CodePos cprc, cpu;
+  Raw rc_n, u_n;        // prefetched inputs of the next plane
+  Raw rc_c, u_c;        // inputs of the current plane
+  bool ovf;
+  MetaAcc my, mu;
+  uint32_t *pk;
+
+  __device__ __forceinline__ void prefetch(int k) {
+    if (!rowok) return;
+    const long long blk = (long long)k * g.n * g.nbx + bip;
+    rc_n = raw_load(a.rc, blk, cprc, true);
+    if (a.corr) u_n = raw_load(a.u_in, blk, cpu, true);
+  }
+  __device__ __forceinline__ void advance() {
+    rc_c = rc_n;
+    u_c = u_n;
+  }
+
+  __device__ __forceinline__ void out(int k, long long S, long long own, long long F0, long long Pu) {
+    if (!rowok) return;  // warp-uniform: one warp per row
+    const Raw rc = rc_c, u = u_c;
+    const long long blk = (long long)k * g.n * g.nbx + bip;
+    const int erc = rc.e;
+    const int Gres = imin(blk_lsb(erc, a.rc.W), GA);
+    const int Mres = imax(erc == -128 ? MAG_NONE : erc, MA) + 1;
+    const int Gcr = Gres + a.c_exp;
+    const int Gy = a.has_y ? imin(GF, Gcr) : Gcr;
+    if (!pt) S = 0;
+    long long ynew;
+    // static range of this block (warp-uniform); else per-value checks
+    if (Gres >= GRID_NONE / 2 || (Mres - Gres <= 62 - a.cbits && Mres + a.cbits + a.c_exp - Gy <= 61 &&
+                                  (!a.has_y || MF - Gy <= 61))) {
+      const long long res = raw_val(rc, cprc.boff, a.rc.W, Gres) - shl(S, GA - Gres);
+      ynew = shl(res * a.c_num, Gcr - Gy);
+      if (a.has_y) ynew += shl(own, GF - Gy);
+    } else {
+      if (erc != -128 && erc - Gres > 61) ovf = true;
+      const long long res = raw_val(rc, cprc.boff, a.rc.W, Gres) - shl_ck(S, GA - Gres, ovf);
+      ck62(res, ovf);
+      ynew = shl_ck(mul_ck(res, a.c_num, a.cbits, ovf), Gcr - Gy, ovf);
+      if (a.has_y) ynew += shl_ck(own, GF - Gy, ovf);
+      ck62(ynew, ovf);
+    }
+    int e, sh;
+    const int q = encode_block(ynew, Gy, a.Wy, e, sh, a.err);
+    const long long yr = rounded_value(ynew, q, sh);
+    if (a.write_y) {
+      pack_block(q, a.Wy, pk, a.y_out.words + blk * a.Wy);
+      if (lane == 0) {
+        a.y_out.exps[blk] = (int8_t)e;
+        my.add(e);
+      }
+    }
+    long long ur = 0;
+    int Gu = Gy, eu = -128;
+    if (a.corr) {
+      const int eu0 = u.e;
+      Gu = imin(blk_lsb(eu0, a.u_in.W), Gy);
+      if (e != -128 || eu0 != -128)
+        if (imax(eu0 == -128 ? MAG_NONE : eu0, e) + 1 - Gu > 62) ovf = true;
+      const long long usum = raw_val(u, cpu.boff, a.u_in.W, Gu) + shl(yr, Gy - Gu);
+      int su;
+      const int qu = encode_block(usum, Gu, a.u_out.W, eu, su, a.err);
+      ur = rounded_value(usum, qu, su);
+      pack_block(qu, a.u_out.W, pk, a.u_out.words + blk * a.u_out.W);
+      if (lane == 0) {
+        a.u_out.exps[blk] = (int8_t)eu;
+        mu.add(eu);
+      }
+    }
+    const long long p = ((long long)k * g.n + j) * g.R + i;
+    if (a.write_w) {  // w_l = y~' + P w_(l-1); P w_(l-1) = F - y~ at this node
+      const int Gw = imin(Gy, GF);
+      long long w;
+      if (imax(MF, e == -128 ? MAG_NONE : e) + 1 - Gw <= 62) {
+        w = shl(yr, Gy - Gw);
+        if (a.has_z && pt) w += shl(F0 - (a.has_y ? own : 0), GF - Gw);
+      } else {
+        w = shl_ck(yr, Gy - Gw, ovf);
+        if (a.has_z && pt) w += shl_ck(F0 - (a.has_y ? own : 0), GF - Gw, ovf);
+        ck62(w, ovf);
+      }
+      store_tmp_block(w, Gw, a.w_out.v + p, a.w_out.gb + blk, pt, ovf);
+    }
+    if (a.write_uh) {  // u^_l = u~_l' + P u^_(l-1)
+      if (ring_u || !a.has_uhc) {
+        const int Gp = a.has_uhc ? G1u - 1 : GRID_NONE;
+        const int Guh = imin(Gu, Gp);
+        long long uh;
+        if (imax(eu == -128 ? MAG_NONE : eu, a.has_uhc ? Mu : MAG_NONE) + 1 - Guh <= 62) {
+          uh = shl(ur, Gu - Guh);
+          if (a.has_uhc && pt) uh += shl(Pu, Gp - Guh);
+        } else {
+          uh = shl_ck(ur, Gu - Guh, ovf);
+          if (a.has_uhc && pt) uh += shl_ck(Pu, Gp - Guh, ovf);
+          ck62(uh, ovf);
+        }
+        store_tmp_block(uh, Guh, a.uh_out.v + p, a.uh_out.gb + blk, pt, ovf);
+      } else {
+        const int gu = pt ? prolong_grid<DIM>(a.uhc, a.gc, i + 1, j + 1, k + 1) : GRID_NONE;
+        const int Guh = imin(Gu, __reduce_min_sync(0xffffffffu, gu));
+        long long uh = shl_ck(ur, Gu - Guh, ovf);
+        if (pt) uh += prolong_tmp<DIM>(a.uhc, a.gc, i + 1, j + 1, k + 1, Guh, ovf);
+        ck62(uh, ovf);
+        store_tmp_block(uh, Guh, a.uh_out.v + p, a.uh_out.gb + blk, pt, ovf);
+      }
+    }
+  }
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(NT, 2) k_sweep(SweepArgs a) {
+  __shared__ SmemTile sm;
+  __shared__ uint32_t pk[TY][33];
+  __shared__ int smy[2], smu[2], smb[6];
+  const Geo g = a.g;
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
+  const Tile T = make_tile(g);
+  if (tid == 0) smy[0] = smy[1] = smu[0] = smu[1] = 0;
+  const bool uring_wanted = a.write_uh && a.has_uhc;
+  Bounds bs, bt, bu;
+  footprint_bounds<DIM>(g, a.gc, T, a.y_in, a.has_y, a.wc, a.has_z, a.uhc, uring_wanted, smb, bs, bt, bu);
+  const Bounds bF = operand_of(bs, bt);
+  const int GF = bF.G, MF = bF.M;
+  const int sA = (DIM - 2) * g.l;
+  if (tid == 0 && GF < GRID_NONE / 2 && MF + 4 - GF > 62) flag_range(a.err, 101, MF + 4, GF);
+  SweepBody<DIM> b{a, g};
+  b.GF = GF;
+  b.MF = MF;
+  b.GA = GF - sA;
+  b.MA = MF + 4 - sA;  // |A F| < 2^MA on grid GA
+  // the u^ ring holds the footprint on one grid when its span fits
+  b.ring_u = uring_wanted && (bu.G >= GRID_NONE / 2 || bu.M - bu.G <= 61);
+  b.G1u = bu.G < GRID_NONE / 2 ? bu.G : 0;
+  b.Mu = bu.M;
+  b.lane = lane;
+  b.ty = ty;
+  b.i = T.x0 + lane;
+  b.j = T.j0 + ty;
+  b.rowok = b.j < g.n;
+  b.pt = b.rowok && b.i < g.n;
+  b.bip = b.rowok ? b.j * g.nbx + T.bx : 0;
+  b.cprc = code_pos(lane, a.rc.W);
+  b.cpu = code_pos(lane, a.corr ? a.u_in.W : 1);
+  b.ovf = false;
+  b.my.init();
+  b.mu.init();
+  b.pk = pk[ty];
+  MarchIn in;
+  in.s = a.y_in;
+  in.t = a.wc;
+  in.u = a.uhc;
+  in.has_s = a.has_y;
+  in.has_t = a.has_z;
+  in.has_u = b.ring_u;
+  in.GF = GF;
+  in.G1t = GF + 1;
+  in.G1u = b.G1u;
+  if (in.has_s || in.has_t || in.has_u) march<DIM>(g, a.gc, T, in, sm, b);
+  else march_none(T, DIM == 2, b);
+  ovf_flush(b.ovf, a.err, 102);
+  if (a.write_y) meta_flush(b.my, a.y_out.meta, smy);
+  if (a.corr) meta_flush(b.mu, a.u_out.meta, smu);
+}
+
+// ------------------------------------------------------------------ residual
+__device__ __forceinline__ long long rne_shift128(__int128 v, int s) {
+  if (s <= 0) return (long long)v;
+  __int128 q = v >> s;
+  __int128 rem = v - (q << s);
+  __int128 half = (__int128)1 << (s - 1);
+  if (rem > half || (rem == half && (q & 1))) q += 1;
+  return (long long)q;
+}
+
+// F_q at level-l node (I, J, K): sum_t prod_a T[t][a][I_a * stride - 1], exact
+// in 128 bits, rounded to nearest-even after dropping fsh bits (any number of
+// terms; reads the tables from global memory).
+template <int DIM>
+__device__ __forceinline__ long long rhs_global(const ResidArgs &a, int I, int J, int K) {
+  const int stride = 1 << (a.Lmax - a.g.l);
+  const int n1 = a.n1max;
+  __int128 F = 0;
+  for (int t = 0; t < a.nterms; t++) {
+    const int32_t *T = a.tables + (long long)t * DIM * n1;
+    long long yz = (long long)__ldg(T + n1 + J * stride - 1);
+    if (DIM == 3) yz *= (long long)__ldg(T + 2 * n1 + K * stride - 1);
+    F += (__int128)__ldg(T + I * stride - 1) * (__int128)yz;
+  }
+  return rne_shift128(F, a.fsh);
+}
+
+struct RhsSmem {
+  int tx[TMAX][32];        // x-factors of the tile's columns
+  int ty[TMAX][TY];        // y-factors of its rows
+  int tz[TMAX][ZC];        // z-factors of its planes
+};
+
+template <int DIM>
+struct ResidBody {
+  const ResidArgs &a;
+  const Geo &g;
+  const RhsSmem &rs;
+  int GF, GA, Gt, Gcr, k0;
+  bool fast, rhs_sm;
+  int bip, lane, ty, i, j;
+  bool rowok, pt;
+  bool ovf;
+  MetaAcc mr, my, mt;
+  uint32_t *pk;
+
+  __device__ __forceinline__ void prefetch(int) {}
+  __device__ __forceinline__ void advance() {}
+
+  // F_q at this thread's node of plane k: the products T_x T_y T_z of every term
+  // are formed exactly as T_x (T_y T_z) with T_y T_z split into 32-bit halves;
+  // the high halves accumulate in SA (units of 2^32), the low ones in L
+  __device__ __forceinline__ long long rhs(int k) {
+    if (!rhs_sm) return rhs_global<DIM>(a, i + 1, j + 1, k + 1);
+    long long SA = 0, L = 0;
+    for (int t = 0; t < a.nterms; t++) {
+      long long yz = (long long)rs.ty[t][ty];
+      if (DIM == 3) yz *= (long long)rs.tz[t][k - k0];
+      const long long x = rs.tx[t][lane];
+      const long long hi = yz >> 32;                        // signed, |hi| < 2^28
+      const long long lo = (long long)(unsigned)(yz & 0xffffffffll);  // [0, 2^32)
+      const long long b = x * lo;                           // |b| < 2^62
+      SA += x * hi + (b >> 32);
+      L += b & 0xffffffffll;
+    }
+    const __int128 V = ((__int128)SA << 32) + (__int128)L;
+    return rne_shift128(V, a.fsh);
+  }
+
+  __device__ __forceinline__ void out(int k, long long S, long long, long long, long long) {
+    if (!rowok) return;
+    long long t = 0;
+    if (pt) {
+      const long long fq = rhs(k);
+      if (fast) {
+        t = shl(fq, a.Gf - Gt) - shl(S, GA - Gt);
+      } else {
+        t = shl_ck(fq, a.Gf - Gt, ovf) - shl_ck(S, GA - Gt, ovf);
+        ck62(t, ovf);
+      }
+    }
+    int e, sh;
+    const int q = encode_block(t, Gt, a.r_out.W, e, sh, a.err);
+    const long long blk = (long long)k * g.n * g.nbx + bip;
+    pack_block(q, a.r_out.W, pk, a.r_out.words + blk * a.r_out.W);
+    if (lane == 0) {
+      a.r_out.exps[blk] = (int8_t)e;
+      mr.add(e);
+    }
+    if (a.first_sweep) {  // y~ = round(c r): the first Jacobi sweep from y~ = 0
+      const long long rr = rounded_value(t, q, sh);
+      int ey, sy;
+      const int qy = encode_block(fast ? rr * a.c_num : mul_ck(rr, a.c_num, a.cbits, ovf), Gcr, a.y_out.W, ey,
+                                  sy, a.err);
+      pack_block(qy, a.y_out.W, pk, a.y_out.words + blk * a.y_out.W);
+      if (lane == 0) {
+        a.y_out.exps[blk] = (int8_t)ey;
+        my.add(ey);
+      }
+    }
+    if (a.write_t) {  // t^_L at the width of Table 1, for the restriction chain
+      int et, st;
+      const int qt = encode_block(t, Gt, a.t_out.W, et, st, a.err);
+      pack_block(qt, a.t_out.W, pk, a.t_out.words + blk * a.t_out.W);
+      if (lane == 0) {
+        a.t_out.exps[blk] = (int8_t)et;
+        mt.add(et);
+      }
+    }
+  }
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(NT, 2) k_residual(ResidArgs a) {
+  __shared__ SmemTile sm;
+  __shared__ RhsSmem rs;
+  __shared__ uint32_t pk[TY][33];
+  __shared__ int smr[2], smy[2], smt[2], smb[6];
+  const Geo g = a.g;
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
+  const Tile T = make_tile(g);
+  if (tid == 0) smr[0] = smr[1] = smy[0] = smy[1] = smt[0] = smt[1] = 0;
+  // the tile's slice of the separable right-hand side tables (Sec. 7 problems):
+  // exact products need |sum| < 2^94 for the split accumulation
+  const bool rhs_sm = a.nterms <= TMAX && a.rhs_bits <= 94;
+  if (rhs_sm) {
+    const int stride = 1 << (a.Lmax - g.l), n1 = a.n1max;
+    for (int idx = tid; idx < a.nterms * (32 + TY + ZC); idx += NT) {
+      const int t = idx / (32 + TY + ZC), r = idx - t * (32 + TY + ZC);
+      const int32_t *Tt = a.tables + (long long)t * DIM * n1;
+      if (r < 32) {
+        const int ii = T.x0 + r;
+        rs.tx[t][r] = ii < g.n ? __ldg(Tt + (ii + 1) * stride - 1) : 0;
+      } else if (r < 32 + TY) {
+        const int jj = T.j0 + r - 32;
+        rs.ty[t][r - 32] = jj < g.n ? __ldg(Tt + n1 + (jj + 1) * stride - 1) : 0;
+      } else {
+        const int kk = T.k0 + r - 32 - TY;
+        rs.tz[t][r - 32 - TY] = (DIM == 3 && kk < g.nz) ? __ldg(Tt + 2 * n1 + (kk + 1) * stride - 1) : 1;
+      }
+    }
+  }
+  Bounds bs, bt, bu;
+  footprint_bounds<DIM>(g, a.gc, T, a.u, true, a.uhc, a.has_uhc, a.uhc, false, smb, bs, bt, bu);
+  const Bounds bF = operand_of(bs, bt);
+  const int GF = bF.G, MF = bF.M;
+  const int sA = (DIM - 2) * g.l;
+  const int GA = GF - sA, MA = MF + 4 - sA;
+  const int Gt = imin(a.Gf, GA), Mt = imax(a.Gf + 51, MA) + 1;
+  if (tid == 0 && GF < GRID_NONE / 2 && MF + 4 - GF > 62) flag_range(a.err, 201, MF + 4, GF);
+  ResidBody<DIM> b{a, g, rs};
+  b.GF = GF;
+  b.GA = GA;
+  b.Gt = Gt;
+  b.Gcr = Gt + a.c_exp;
+  b.k0 = T.k0;
+  // the bound |t| < 2^Mt is loose (t is a residual, far below |f| + |A F|): when
+  // it does not fit, every value is checked instead
+  b.fast = Mt - Gt <= 62 && (!a.first_sweep || Mt + 1 + a.cbits - Gt <= 62);
+  b.rhs_sm = rhs_sm;
+  b.lane = lane;
+  b.ty = ty;
+  b.i = T.x0 + lane;
+  b.j = T.j0 + ty;
+  b.rowok = b.j < g.n;
+  b.pt = b.rowok && b.i < g.n;
+  b.bip = b.rowok ? b.j * g.nbx + T.bx : 0;
+  b.ovf = false;
+  b.mr.init();
+  b.my.init();
+  b.mt.init();
+  b.pk = pk[ty];
+  MarchIn in;
+  in.s = a.u;
+  in.t = a.uhc;
+  in.u = a.uhc;
+  in.has_s = true;
+  in.has_t = a.has_uhc;
+  in.has_u = false;
+  in.GF = GF;
+  in.G1t = GF + 1;
+  in.G1u = 0;
+  march<DIM>(g, a.gc, T, in, sm, b);
+  ovf_flush(b.ovf, a.err, 202);
+  meta_flush(b.mr, a.r_out.meta, smr);
+  if (a.first_sweep) meta_flush(b.my, a.y_out.meta, smy);
+  if (a.write_t) meta_flush(b.mt, a.t_out.meta, smt);
+}
+
+// ------------------------------------------------------------------ restriction
+// R_l = P_l^T on grid G-1: an all-even node gives 2d to its coarse node, any
+// other node gives d to each of the two coarse nodes (I -+ e_S)/2.
+template <int DIM>
+__device__ __forceinline__ void scatter_restrict(unsigned long long *acc, const Geo &gc, int I, int J, int K,
+                                                 long long d) {
+  Parents<DIM> p(I, J, K);
+  if (!p.two) {
+    atomicAdd(acc + ((long long)p.ka * gc.n + p.ja) * gc.R + p.ia, (unsigned long long)(2 * d));
+    return;
+  }
+  if (inside(gc, p.ia, p.ja, p.ka))
+    atomicAdd(acc + ((long long)p.ka * gc.n + p.ja) * gc.R + p.ia, (unsigned long long)d);
+  if (inside(gc, p.ib, p.jb, p.kb))
+    atomicAdd(acc + ((long long)p.kb * gc.n + p.jb) * gc.R + p.ib, (unsigned long long)d);
+}
+
+template <int DIM>
+struct RestrictBody {
+  const RestrictArgs &a;
+  const Geo &g;
+  int GA, Gd;
+  bool fast;
+  int bip, i, j;
+  bool rowok, pt;
+  CodePos cprc;
+  Raw rc_n, rc_c;
+  bool ovf;
+
+  __device__ __forceinline__ void prefetch(int k) {
+    if (!rowok) return;
+    rc_n = raw_load(a.rc, (long long)k * g.n * g.nbx + bip, cprc, true);
+  }
+  __device__ __forceinline__ void advance() { rc_c = rc_n; }
+
+  __device__ __forceinline__ void out(int k, long long S, long long, long long, long long) {
+    if (!rowok) return;
+    const Raw rc = rc_c;
+    if (rc.e != -128 && rc.e - Gd > 57) ovf = true;
+    long long d = raw_val(rc, cprc.boff, a.rc.W, Gd);
+    if (a.has_y && pt) {
+      if (fast) {
+        d -= shl(S, GA - Gd);
+      } else {
+        d -= shl_ck(S, GA - Gd, ovf);
+        ck58(d, ovf);
+      }
+    }
+    if (pt && d) scatter_restrict<DIM>((unsigned long long *)a.acc.v, a.gc, i + 1, j + 1, k + 1, d);
+  }
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(NT, 2) k_restrict(RestrictArgs a) {
+  __shared__ SmemTile sm;
+  __shared__ int smb[6];
+  const Geo g = a.g;
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
+  const Tile T = make_tile(g);
+  // one grid for every contribution to the accumulator, from the sections'
+  // global finest grids: the accumulator holds R d on Gd - 1
+  const int sA = (DIM - 2) * g.l;
+  const int Gd = imin(sec_lsb(a.rc), a.has_y ? sec_lsb(a.y) - sA : GRID_NONE);
+  if (tid == 0 && first_cta()) a.acc.meta[0] = Gd - 1;
+  Bounds bs, bt, bu;
+  footprint_bounds<DIM>(g, a.gc, T, a.y, a.has_y, a.acc, false, a.acc, false, smb, bs, bt, bu);
+  const Bounds bF = operand_of(bs, bt);
+  const int GF = bF.G, MF = bF.M;
+  const int GA = GF - sA, MA = MF + 4 - sA;
+  if (tid == 0 && a.has_y && GF < GRID_NONE / 2 && MF + 4 - GF > 62) flag_range(a.err, 301, MF + 4, GF);
+  RestrictBody<DIM> b{a, g};
+  b.GA = GA;
+  b.Gd = Gd;
+  b.fast = !a.has_y || GF >= GRID_NONE / 2 || MA - Gd <= 57;  // else every d is checked
+  b.i = T.x0 + lane;
+  b.j = T.j0 + ty;
+  b.rowok = b.j < g.n;
+  b.pt = b.rowok && b.i < g.n;
+  b.bip = b.rowok ? b.j * g.nbx + T.bx : 0;
+  b.cprc = code_pos(lane, a.rc.W);
+  b.ovf = false;
+  MarchIn in;
+  in.s = a.y;
+  in.t = a.acc;
+  in.u = a.acc;
+  in.has_s = a.has_y;
+  in.has_t = false;
+  in.has_u = false;
+  in.GF = GF;
+  in.G1t = 0;
+  in.G1u = 0;
+  if (in.has_s) march<DIM>(g, a.gc, T, in, sm, b);
+  else march_none(T, DIM == 2, b);
+  ovf_flush(b.ovf, a.err, 302);
+}
+
+dim3 stencil_grid(const Geo &g) {
+  return dim3((unsigned)g.nbx, (unsigned)((g.n + TY - 1) / TY), (unsigned)((g.nz + ZC - 1) / ZC));
+}
+
+}  // namespace
+
+void launch_sweep(int dim, const SweepArgs &a, cudaStream_t st) {
+  dim3 b(32, TY);
+  if (dim == 3) k_sweep<3><<<stencil_grid(a.g), b, 0, st>>>(a);
+  else k_sweep<2><<<stencil_grid(a.g), b, 0, st>>>(a);
+}
+
+void launch_residual(int dim, const ResidArgs &a, cudaStream_t st) {
+  dim3 b(32, TY);
+  if (dim == 3) k_residual<3><<<stencil_grid(a.g), b, 0, st>>>(a);
+  else k_residual<2><<<stencil_grid(a.g), b, 0, st>>>(a);
+}
+
+void launch_restrict(int dim, const RestrictArgs &a, cudaStream_t st) {
+  dim3 b(32, TY);
+  if (dim == 3) k_restrict<3><<<stencil_grid(a.g), b, 0, st>>>(a);
+  else k_restrict<2><<<stencil_grid(a.g), b, 0, st>>>(a);
+}
+
+}  // namespace cmg
