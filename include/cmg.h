@@ -57,7 +57,8 @@ typedef enum {
  * rounded only where they are stored, as the paper's rounding rules prescribe. */
 typedef struct {
   int dim;             /* 2 or 3 */
-  int L_max;           /* finest level, 1 <= L_max <= 14 */
+  int L_max;           /* finest level, 1 <= L_max <= 14 (3-D: <= 12, so that
+                          the finest level has fewer than 2^31 BFP blocks) */
   int b1;              /* finest-level width of u~ (Table 1 b_1), 2..32 */
   int b2;              /* finest-level width of r and y~ (Table 1 b_2), 2..32 */
   int k_u;             /* regressive increment of u~, p + 1 = 2 */

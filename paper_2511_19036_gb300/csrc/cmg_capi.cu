@@ -197,6 +197,10 @@ extern "C" cmg_status cmg_params_check(const cmg_params *p) {
   if (!p) return CMG_EINVAL;
   if (p->dim != 2 && p->dim != 3) return CMG_EINVAL;
   if (p->L_max < 1 || p->L_max > MAXL) return CMG_EINVAL;
+  {  // block and plane indices of the finest level are 32-bit in the kernels
+    const long long n = (1ll << p->L_max) - 1, nbx = (n + 31) / 32;
+    if ((p->dim == 3 ? n : 1) * n * nbx >= (1ll << 31)) return CMG_ERANGE;
+  }
   if (p->b1 < 2 || p->b2 < 2 || p->k_u < 0 || p->k_r < 0) return CMG_EINVAL;
   if (p->k_u * (p->L_max - 1) + p->b1 > 32 || p->k_r * (p->L_max - 1) + p->b2 > 32) return CMG_ERANGE;
   if (p->N_ir < 1 || p->nu1 < 0 || p->nu2 < 1 || p->nu1 > 64 || p->nu2 > 64) return CMG_EINVAL;

@@ -222,9 +222,28 @@ __device__ __forceinline__ long long rne_shift(long long v, int s) {
   return q;
 }
 
+// rne_shift for a warp-uniform s: for s > 0, floor((v + 2^(s-1) - 1 + lsb) /
+// 2^s) with lsb the last bit of floor(v / 2^s) rounds to nearest, ties to even
+// (|v| < 2^62, so the sum cannot overflow)
+__device__ __forceinline__ long long rne_shift_w(long long v, int s) {
+  if (s <= 0) return (long long)((unsigned long long)v << (-s));
+  const long long lsb = (v >> s) & 1;
+  return (v + ((1ll << (s - 1)) - 1) + lsb) >> s;
+}
+
 __device__ __forceinline__ int bitlen64(long long v) {
   unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
   return a ? 64 - __clzll((long long)a) : 0;
+}
+
+// Warp-collective bit length of the largest |v| of a block (0: all zero),
+// from two 32-bit warp reductions.
+__device__ __forceinline__ int block_bitlen(long long v) {
+  const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+  const unsigned hmax = __reduce_max_sync(0xffffffffu, (unsigned)(a >> 32));
+  if (hmax) return 64 - __clz((int)hmax);
+  const unsigned lmax = __reduce_max_sync(0xffffffffu, (unsigned)a);
+  return lmax ? 32 - __clz((int)lmax) : 0;
 }
 
 // Warp-collective BFP rounding of one block: every lane passes its exact value
@@ -232,8 +251,7 @@ __device__ __forceinline__ int bitlen64(long long v) {
 // block exponent (-128 for an all-zero block) and s the drop shift, so that the
 // rounded value on grid G is rne_shift(v, s) << s when s > 0, else v itself.
 __device__ __forceinline__ int encode_block(long long v, int G, int W, int &e, int &s, int *err) {
-  int bl = bitlen64(v);
-  int bmax = __reduce_max_sync(0xffffffffu, bl);
+  const int bmax = block_bitlen(v);
   if (bmax == 0) {
     e = -128;
     s = 0;
@@ -241,12 +259,14 @@ __device__ __forceinline__ int encode_block(long long v, int G, int W, int &e, i
   }
   e = bmax + G;  // 2^(e-1) <= max|v| 2^G < 2^e
   s = bmax - (W - 1);
-  long long q = rne_shift(v, s);
-  long long lim = 1ll << (W - 1);
-  if (__any_sync(0xffffffffu, q == lim || q == -lim)) {
+  long long q = rne_shift_w(v, s);
+  // |q| <= 2^(W-1); |q| == 2^(W-1) (rounding carried into the next power of
+  // two) iff q + 2^(W-1) is 0 mod 2^W, tested on the low 32 bits
+  const unsigned lim = 1u << (W - 1), mask = (lim << 1) - 1u;
+  if (__any_sync(0xffffffffu, (((unsigned)q + lim) & mask) == 0u)) {
     e += 1;
     s += 1;
-    q = rne_shift(v, s);
+    q = rne_shift_w(v, s);
   }
   if ((e > 127 || e < -127) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_EXP);
   return (int)q;
@@ -292,6 +312,18 @@ __device__ __forceinline__ void store_tmp_block(long long v, int G, long long *d
   if (g > (1 << 22) || g < -(1 << 22)) ovf = true;
   if (active) *dst = vn;
   if (lane == 0) *gb = (int)((unsigned)g << 8) | bits;
+}
+
+// Warp-collective store of one 32-value block of a temporary whose values w are
+// already on their block grid g (a grid the caller knows every value to be a
+// multiple of); writes the descriptor with the exact bit length.
+__device__ __forceinline__ void store_tmp_on(long long w, int g, long long *dst, int *gb, bool active, bool &ovf) {
+  const int bits = block_bitlen(w);
+  if (active) *dst = w;
+  if ((threadIdx.x & 31) == 0) {
+    if (bits && (g > (1 << 22) || g < -(1 << 22))) ovf = true;
+    *gb = bits ? (int)((unsigned)g << 8) | bits : 0;
+  }
 }
 
 // CTA-level reduction of written exponents into the section metadata.

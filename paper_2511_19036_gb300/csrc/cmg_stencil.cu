@@ -41,7 +41,17 @@ constexpr int CRX = CR * CX;        // values of one ring plane
 constexpr int PW = 34;              // plane buffer row: 32 values and one halo value each side
 constexpr int PLANE = (TY + 2) * PW;
 constexpr int NHALO = 2 * 32 + 2 * (TY + 2);  // halo values of one plane
-constexpr int TMAX = 16;            // right-hand-side terms held in shared memory
+constexpr int TMAXP = 8;
+// resident CTAs per SM the register allocation is fitted to, per kernel
+#ifndef CMG_SWEEP_MINB
+#define CMG_SWEEP_MINB 3
+#endif
+#ifndef CMG_RESID_MINB
+#define CMG_RESID_MINB 3
+#endif
+#ifndef CMG_RESTRICT_MINB
+#define CMG_RESTRICT_MINB 2
+#endif            // right-hand-side terms with per-thread products in shared memory
 
 __device__ inline bool first_cta() { return blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0; }
 
@@ -65,14 +75,14 @@ __device__ __forceinline__ CodePos code_pos(int x, int W) {
 }
 
 // issue the loads of one code and its block exponent (no use of the result yet)
-__device__ __forceinline__ Raw raw_load(const Sec &s, long long blk, CodePos cp, bool ok) {
+__device__ __forceinline__ Raw raw_load(const Sec &s, int blk, CodePos cp, bool ok) {
   Raw r;
   r.e = -128;
   r.w0 = 0u;
   r.w1 = 0u;
   if (ok) {
     r.e = __ldg(s.exps + blk);
-    const uint32_t *w = s.words + blk * s.W + cp.woff;
+    const uint32_t *w = s.words + (long long)blk * s.W + cp.woff;
     r.w0 = __ldg(w);
     if (cp.two) r.w1 = __ldg(w + 1);
   }
@@ -88,6 +98,21 @@ __device__ __forceinline__ int raw_code(const Raw &r, int boff, int W) {
 __device__ __forceinline__ long long raw_val(const Raw &r, int boff, int W, int G) {
   if (r.e == -128) return 0;
   return (long long)((unsigned long long)(long long)raw_code(r, boff, W) << (r.e - W + 1 - G));
+}
+
+// Left shift for the paths whose static range check passed: there every shift
+// of a nonzero value is below 63, and a shift of 64 or more only meets a zero
+// (an operand whose footprint is all zero), so the count is taken mod 64.
+__device__ __forceinline__ long long shl_fast(long long v, int s) {
+  return (long long)((unsigned long long)v << (s & 63));
+}
+
+// v on grid `from` re-expressed on grid `to`: exact right shift when to >= from
+// (the caller knows v to be a multiple of 2^(to - from)), left shift otherwise
+// (the caller checked the range)
+__device__ __forceinline__ long long regrid(long long v, int from, int to) {
+  const int d = to - from;
+  return d >= 0 ? (v >> (d & 63)) : (long long)((unsigned long long)v << ((-d) & 63));
 }
 
 // ------------------------------------------------------------------ tile geometry
@@ -154,7 +179,7 @@ __device__ __forceinline__ long long ring_p(const long long *ring, const Slot &s
 struct Stager {
   bool on, ok;
   int bip;          // block index inside a coarse plane
-  long long vip;    // value index inside a coarse plane
+  int cj, ci;       // coarse row and column
   long long v;      // loaded value, not yet stored
   int gb;           // loaded descriptor
 };
@@ -166,7 +191,8 @@ __device__ __forceinline__ Stager make_stager(const Geo &gc, const Tile &T, int 
   const int cj = T.cr0 + r, ci = T.cx0 + x;
   s.ok = s.on && (unsigned)ci < (unsigned)gc.n && (unsigned)cj < (unsigned)gc.n;
   s.bip = s.ok ? cj * gc.nbx + (ci >> 5) : 0;
-  s.vip = s.ok ? (long long)cj * gc.R + ci : 0;
+  s.cj = s.ok ? cj : 0;
+  s.ci = s.ok ? ci : 0;
   s.v = 0;
   s.gb = 0;
   return s;
@@ -176,13 +202,13 @@ __device__ __forceinline__ void stage_load(Stager &s, const Tmp &t, const Geo &g
   s.v = 0;
   s.gb = 0;
   if (s.ok && (unsigned)c < (unsigned)gc.nz) {
-    s.gb = __ldg(t.gb + (long long)c * gc.n * gc.nbx + s.bip);
-    s.v = __ldg(t.v + (long long)c * gc.n * gc.R + s.vip);
+    s.gb = __ldg(t.gb + c * gc.n * gc.nbx + s.bip);
+    s.v = __ldg(t.v + (long long)(c * gc.n + s.cj) * gc.R + s.ci);
   }
 }
 
 __device__ __forceinline__ void stage_store(const Stager &s, long long *ring, int c, int G1, int tid) {
-  if (s.on) ring[(c & 3) * CRX + tid] = (s.gb & 0xff) ? shl(s.v, (s.gb >> 8) - G1) : 0;
+  if (s.on) ring[(c & 3) * CRX + tid] = (s.gb & 0xff) ? shl_fast(s.v, (s.gb >> 8) - G1) : 0;
 }
 
 // ------------------------------------------------------------------ footprint bounds
@@ -312,7 +338,7 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
     }
     hal = make_slot(g, Ws, i, j, r, x, T);
   }
-  const long long pb = (long long)g.n * g.nbx;  // blocks per plane
+  const int pb = g.n * g.nbx;  // blocks per plane (block indices fit in int)
   const bool rings = in.has_t || in.has_u;
   Stager st0 = make_stager(gc, T, tid), st1 = st0;
   const bool has_s = in.has_s;
@@ -440,6 +466,7 @@ struct SweepBody {
   int GF, MF, GA, MA, G1u;
   bool ring_u;          // P_l u^_(l-1) from the ring (else per value from global memory)
   int Mu;               // |P_l u^_(l-1)| < 2^Mu over the footprint
+  int GPw, MPw;         // P_l w_(l-1) is exact on grid GPw, |P_l w_(l-1)| < 2^MPw
   int bip, lane, ty, i, j;
   bool rowok, pt;
   CodePos cprc, cpu;
@@ -451,7 +478,7 @@ struct SweepBody {
 
   __device__ __forceinline__ void prefetch(int k) {
     if (!rowok) return;
-    const long long blk = (long long)k * g.n * g.nbx + bip;
+    const int blk = k * g.n * g.nbx + bip;
     rc_n = raw_load(a.rc, blk, cprc, true);
     if (a.corr) u_n = raw_load(a.u_in, blk, cpu, true);
   }
@@ -463,7 +490,7 @@ struct SweepBody {
   __device__ __forceinline__ void out(int k, long long S, long long own, long long F0, long long Pu) {
     if (!rowok) return;  // warp-uniform: one warp per row
     const Raw rc = rc_c, u = u_c;
-    const long long blk = (long long)k * g.n * g.nbx + bip;
+    const int blk = k * g.n * g.nbx + bip;
     const int erc = rc.e;
     const int Gres = imin(blk_lsb(erc, a.rc.W), GA);
     const int Mres = imax(erc == -128 ? MAG_NONE : erc, MA) + 1;
@@ -474,9 +501,9 @@ struct SweepBody {
     // static range of this block (warp-uniform); else per-value checks
     if (Gres >= GRID_NONE / 2 || (Mres - Gres <= 62 - a.cbits && Mres + a.cbits + a.c_exp - Gy <= 61 &&
                                   (!a.has_y || MF - Gy <= 61))) {
-      const long long res = raw_val(rc, cprc.boff, a.rc.W, Gres) - shl(S, GA - Gres);
-      ynew = shl(res * a.c_num, Gcr - Gy);
-      if (a.has_y) ynew += shl(own, GF - Gy);
+      const long long res = raw_val(rc, cprc.boff, a.rc.W, Gres) - shl_fast(S, GA - Gres);
+      ynew = shl_fast(res * a.c_num, Gcr - Gy);
+      if (a.has_y) ynew += shl_fast(own, GF - Gy);
     } else {
       if (erc != -128 && erc - Gres > 61) ovf = true;
       const long long res = raw_val(rc, cprc.boff, a.rc.W, Gres) - shl_ck(S, GA - Gres, ovf);
@@ -489,7 +516,7 @@ struct SweepBody {
     const int q = encode_block(ynew, Gy, a.Wy, e, sh, a.err);
     const long long yr = rounded_value(ynew, q, sh);
     if (a.write_y) {
-      pack_block(q, a.Wy, pk, a.y_out.words + blk * a.Wy);
+      pack_block(q, a.Wy, pk, a.y_out.words + (long long)blk * a.Wy);
       if (lane == 0) {
         a.y_out.exps[blk] = (int8_t)e;
         my.add(e);
@@ -502,44 +529,50 @@ struct SweepBody {
       Gu = imin(blk_lsb(eu0, a.u_in.W), Gy);
       if (e != -128 || eu0 != -128)
         if (imax(eu0 == -128 ? MAG_NONE : eu0, e) + 1 - Gu > 62) ovf = true;
-      const long long usum = raw_val(u, cpu.boff, a.u_in.W, Gu) + shl(yr, Gy - Gu);
+      const long long usum = raw_val(u, cpu.boff, a.u_in.W, Gu) + shl_fast(yr, Gy - Gu);
       int su;
       const int qu = encode_block(usum, Gu, a.u_out.W, eu, su, a.err);
       ur = rounded_value(usum, qu, su);
-      pack_block(qu, a.u_out.W, pk, a.u_out.words + blk * a.u_out.W);
+      pack_block(qu, a.u_out.W, pk, a.u_out.words + (long long)blk * a.u_out.W);
       if (lane == 0) {
         a.u_out.exps[blk] = (int8_t)eu;
         mu.add(eu);
       }
     }
-    const long long p = ((long long)k * g.n + j) * g.R + i;
+    const long long p = (long long)(k * g.n + j) * g.R + i;
     if (a.write_w) {  // w_l = y~' + P w_(l-1); P w_(l-1) = F - y~ at this node
-      const int Gw = imin(Gy, GF);
-      long long w;
-      if (imax(MF, e == -128 ? MAG_NONE : e) + 1 - Gw <= 62) {
-        w = shl(yr, Gy - Gw);
-        if (a.has_z && pt) w += shl(F0 - (a.has_y ? own : 0), GF - Gw);
-      } else {
-        w = shl_ck(yr, Gy - Gw, ovf);
-        if (a.has_z && pt) w += shl_ck(F0 - (a.has_y ? own : 0), GF - Gw, ovf);
-        ck62(w, ovf);
+      // block grid: the coarser of the grids y~' and P w_(l-1) are exact on
+      const int gY = e == -128 ? GRID_NONE : imax(e - a.Wy + 1, Gy);
+      const int gw = imin(gY, a.has_z ? GPw : GRID_NONE);
+      long long w = 0;
+      if (gw < GRID_NONE / 2) {
+        const long long pw = (a.has_z && pt) ? F0 - (a.has_y ? own : 0) : 0;
+        if (imax(a.has_z ? MPw : MAG_NONE, e == -128 ? MAG_NONE : e) + 1 - gw <= 62) {
+          w = regrid(yr, Gy, gw) + regrid(pw, GF, gw);
+        } else {
+          w = regrid(yr, Gy, gw) + (gw >= GF ? regrid(pw, GF, gw) : shl_ck(pw, GF - gw, ovf));
+          ck62(w, ovf);
+        }
       }
-      store_tmp_block(w, Gw, a.w_out.v + p, a.w_out.gb + blk, pt, ovf);
+      store_tmp_on(w, gw, a.w_out.v + p, a.w_out.gb + blk, pt, ovf);
     }
     if (a.write_uh) {  // u^_l = u~_l' + P u^_(l-1)
       if (ring_u || !a.has_uhc) {
-        const int Gp = a.has_uhc ? G1u - 1 : GRID_NONE;
-        const int Guh = imin(Gu, Gp);
-        long long uh;
-        if (imax(eu == -128 ? MAG_NONE : eu, a.has_uhc ? Mu : MAG_NONE) + 1 - Guh <= 62) {
-          uh = shl(ur, Gu - Guh);
-          if (a.has_uhc && pt) uh += shl(Pu, Gp - Guh);
-        } else {
-          uh = shl_ck(ur, Gu - Guh, ovf);
-          if (a.has_uhc && pt) uh += shl_ck(Pu, Gp - Guh, ovf);
-          ck62(uh, ovf);
+        const int gU = eu == -128 ? GRID_NONE : imax(eu - a.u_out.W + 1, Gu);
+        const int gP = a.has_uhc ? G1u - 1 : GRID_NONE;
+        const int gu = imin(gU, gP);
+        long long uh = 0;
+        if (gu < GRID_NONE / 2) {
+          const long long pu = (a.has_uhc && pt) ? Pu : 0;
+          if (imax(eu == -128 ? MAG_NONE : eu, a.has_uhc ? Mu : MAG_NONE) + 1 - gu <= 62) {
+            uh = regrid(ur, Gu, gu) + regrid(pu, gP, gu);
+          } else {
+            uh = (gu >= Gu ? regrid(ur, Gu, gu) : shl_ck(ur, Gu - gu, ovf)) +
+                 (gu >= gP ? regrid(pu, gP, gu) : shl_ck(pu, gP - gu, ovf));
+            ck62(uh, ovf);
+          }
         }
-        store_tmp_block(uh, Guh, a.uh_out.v + p, a.uh_out.gb + blk, pt, ovf);
+        store_tmp_on(uh, gu, a.uh_out.v + p, a.uh_out.gb + blk, pt, ovf);
       } else {
         const int gu = pt ? prolong_grid<DIM>(a.uhc, a.gc, i + 1, j + 1, k + 1) : GRID_NONE;
         const int Guh = imin(Gu, __reduce_min_sync(0xffffffffu, gu));
@@ -553,7 +586,7 @@ struct SweepBody {
 };
 
 template <int DIM>
-__global__ void __launch_bounds__(NT, 2) k_sweep(SweepArgs a) {
+__global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
   __shared__ SmemTile sm;
   __shared__ uint32_t pk[TY][33];
   __shared__ int smy[2], smu[2], smb[6];
@@ -577,6 +610,8 @@ __global__ void __launch_bounds__(NT, 2) k_sweep(SweepArgs a) {
   b.ring_u = uring_wanted && (bu.G >= GRID_NONE / 2 || bu.M - bu.G <= 61);
   b.G1u = bu.G < GRID_NONE / 2 ? bu.G : 0;
   b.Mu = bu.M;
+  b.GPw = bt.G < GRID_NONE / 2 ? bt.G - 1 : GRID_NONE;
+  b.MPw = bt.M;
   b.lane = lane;
   b.ty = ty;
   b.i = T.x0 + lane;
@@ -635,10 +670,23 @@ __device__ __forceinline__ long long rhs_global(const ResidArgs &a, int I, int J
 }
 
 struct RhsSmem {
-  int tx[TMAX][32];        // x-factors of the tile's columns
-  int ty[TMAX][TY];        // y-factors of its rows
-  int tz[TMAX][ZC];        // z-factors of its planes
+  int2 pxy[TMAXP][NT];     // T_x(I) T_y(J) of each thread's column, per term, as
+                           // lo + 2^32 hi with lo in [-2^31, 2^31)
+  int tz[TMAXP][ZC];       // T_z(K) of the tile's planes
 };
+
+// round-to-nearest-even of (hi 2^32 + lo) / 2^fsh, lo in [0, 2^32)
+__device__ __forceinline__ long long rne96(long long hi, unsigned lo, int fsh) {
+  if (fsh >= 33) {
+    const int s = fsh - 32;
+    long long q = hi >> s;
+    const unsigned long long rh = (unsigned long long)hi & ((1ull << s) - 1ull);
+    const unsigned long long hh = 1ull << (s - 1);
+    if (rh > hh || (rh == hh && (lo != 0u || (q & 1)))) q += 1;
+    return q;
+  }
+  return rne_shift128(((__int128)hi << 32) + (__int128)lo, fsh);
+}
 
 template <int DIM>
 struct ResidBody {
@@ -656,24 +704,21 @@ struct ResidBody {
   __device__ __forceinline__ void prefetch(int) {}
   __device__ __forceinline__ void advance() {}
 
-  // F_q at this thread's node of plane k: the products T_x T_y T_z of every term
-  // are formed exactly as T_x (T_y T_z) with T_y T_z split into 32-bit halves;
-  // the high halves accumulate in SA (units of 2^32), the low ones in L
+  // F_q at this thread's node of plane k, exactly: each term (T_x T_y) T_z is
+  // (lo + 2^32 hi) T_z with two 32 x 32-bit products; SA collects floor(term /
+  // 2^32) (|SA| < 2^62 for a bound below 2^94), L the remainders (< 2^35)
   __device__ __forceinline__ long long rhs(int k) {
     if (!rhs_sm) return rhs_global<DIM>(a, i + 1, j + 1, k + 1);
     long long SA = 0, L = 0;
+    const int tid = ty * 32 + lane;
     for (int t = 0; t < a.nterms; t++) {
-      long long yz = (long long)rs.ty[t][ty];
-      if (DIM == 3) yz *= (long long)rs.tz[t][k - k0];
-      const long long x = rs.tx[t][lane];
-      const long long hi = yz >> 32;                        // signed, |hi| < 2^28
-      const long long lo = (long long)(unsigned)(yz & 0xffffffffll);  // [0, 2^32)
-      const long long b = x * lo;                           // |b| < 2^62
-      SA += x * hi + (b >> 32);
+      const int2 p = rs.pxy[t][tid];
+      const int z = DIM == 3 ? rs.tz[t][k - k0] : 1;
+      const long long b = (long long)p.x * z;  // |b| < 2^61
+      SA += (long long)p.y * z + (b >> 32);
       L += b & 0xffffffffll;
     }
-    const __int128 V = ((__int128)SA << 32) + (__int128)L;
-    return rne_shift128(V, a.fsh);
+    return rne96(SA + (L >> 32), (unsigned)(L & 0xffffffffll), a.fsh);
   }
 
   __device__ __forceinline__ void out(int k, long long S, long long, long long, long long) {
@@ -682,7 +727,7 @@ struct ResidBody {
     if (pt) {
       const long long fq = rhs(k);
       if (fast) {
-        t = shl(fq, a.Gf - Gt) - shl(S, GA - Gt);
+        t = shl_fast(fq, a.Gf - Gt) - shl_fast(S, GA - Gt);
       } else {
         t = shl_ck(fq, a.Gf - Gt, ovf) - shl_ck(S, GA - Gt, ovf);
         ck62(t, ovf);
@@ -690,8 +735,8 @@ struct ResidBody {
     }
     int e, sh;
     const int q = encode_block(t, Gt, a.r_out.W, e, sh, a.err);
-    const long long blk = (long long)k * g.n * g.nbx + bip;
-    pack_block(q, a.r_out.W, pk, a.r_out.words + blk * a.r_out.W);
+    const int blk = k * g.n * g.nbx + bip;
+    pack_block(q, a.r_out.W, pk, a.r_out.words + (long long)blk * a.r_out.W);
     if (lane == 0) {
       a.r_out.exps[blk] = (int8_t)e;
       mr.add(e);
@@ -701,7 +746,7 @@ struct ResidBody {
       int ey, sy;
       const int qy = encode_block(fast ? rr * a.c_num : mul_ck(rr, a.c_num, a.cbits, ovf), Gcr, a.y_out.W, ey,
                                   sy, a.err);
-      pack_block(qy, a.y_out.W, pk, a.y_out.words + blk * a.y_out.W);
+      pack_block(qy, a.y_out.W, pk, a.y_out.words + (long long)blk * a.y_out.W);
       if (lane == 0) {
         a.y_out.exps[blk] = (int8_t)ey;
         my.add(ey);
@@ -710,7 +755,7 @@ struct ResidBody {
     if (a.write_t) {  // t^_L at the width of Table 1, for the restriction chain
       int et, st;
       const int qt = encode_block(t, Gt, a.t_out.W, et, st, a.err);
-      pack_block(qt, a.t_out.W, pk, a.t_out.words + blk * a.t_out.W);
+      pack_block(qt, a.t_out.W, pk, a.t_out.words + (long long)blk * a.t_out.W);
       if (lane == 0) {
         a.t_out.exps[blk] = (int8_t)et;
         mt.add(et);
@@ -720,7 +765,7 @@ struct ResidBody {
 };
 
 template <int DIM>
-__global__ void __launch_bounds__(NT, 2) k_residual(ResidArgs a) {
+__global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   __shared__ SmemTile sm;
   __shared__ RhsSmem rs;
   __shared__ uint32_t pk[TY][33];
@@ -731,22 +776,22 @@ __global__ void __launch_bounds__(NT, 2) k_residual(ResidArgs a) {
   if (tid == 0) smr[0] = smr[1] = smy[0] = smy[1] = smt[0] = smt[1] = 0;
   // the tile's slice of the separable right-hand side tables (Sec. 7 problems):
   // exact products need |sum| < 2^94 for the split accumulation
-  const bool rhs_sm = a.nterms <= TMAX && a.rhs_bits <= 94;
+  const bool rhs_sm = a.nterms <= TMAXP && a.rhs_bits <= 94;
   if (rhs_sm) {
     const int stride = 1 << (a.Lmax - g.l), n1 = a.n1max;
-    for (int idx = tid; idx < a.nterms * (32 + TY + ZC); idx += NT) {
-      const int t = idx / (32 + TY + ZC), r = idx - t * (32 + TY + ZC);
+    const int ii = T.x0 + lane, jj = T.j0 + ty;
+    for (int t = 0; t < a.nterms; t++) {
       const int32_t *Tt = a.tables + (long long)t * DIM * n1;
-      if (r < 32) {
-        const int ii = T.x0 + r;
-        rs.tx[t][r] = ii < g.n ? __ldg(Tt + (ii + 1) * stride - 1) : 0;
-      } else if (r < 32 + TY) {
-        const int jj = T.j0 + r - 32;
-        rs.ty[t][r - 32] = jj < g.n ? __ldg(Tt + n1 + (jj + 1) * stride - 1) : 0;
-      } else {
-        const int kk = T.k0 + r - 32 - TY;
-        rs.tz[t][r - 32 - TY] = (DIM == 3 && kk < g.nz) ? __ldg(Tt + 2 * n1 + (kk + 1) * stride - 1) : 1;
-      }
+      const long long p = (ii < g.n && jj < g.n)
+                              ? (long long)__ldg(Tt + (ii + 1) * stride - 1) * __ldg(Tt + n1 + (jj + 1) * stride - 1)
+                              : 0;
+      const int lo = (int)(unsigned)(unsigned long long)p;
+      rs.pxy[t][tid] = make_int2(lo, (int)((p - lo) >> 32));
+    }
+    for (int idx = tid; idx < a.nterms * ZC; idx += NT) {
+      const int t = idx / ZC, r = idx - t * ZC, kk = T.k0 + r;
+      const int32_t *Tt = a.tables + (long long)t * DIM * n1;
+      rs.tz[t][r] = (DIM == 3 && kk < g.nz) ? __ldg(Tt + 2 * n1 + (kk + 1) * stride - 1) : 1;
     }
   }
   Bounds bs, bt, bu;
@@ -827,7 +872,7 @@ struct RestrictBody {
 
   __device__ __forceinline__ void prefetch(int k) {
     if (!rowok) return;
-    rc_n = raw_load(a.rc, (long long)k * g.n * g.nbx + bip, cprc, true);
+    rc_n = raw_load(a.rc, k * g.n * g.nbx + bip, cprc, true);
   }
   __device__ __forceinline__ void advance() { rc_c = rc_n; }
 
@@ -838,7 +883,7 @@ struct RestrictBody {
     long long d = raw_val(rc, cprc.boff, a.rc.W, Gd);
     if (a.has_y && pt) {
       if (fast) {
-        d -= shl(S, GA - Gd);
+        d -= shl_fast(S, GA - Gd);
       } else {
         d -= shl_ck(S, GA - Gd, ovf);
         ck58(d, ovf);
@@ -849,7 +894,7 @@ struct RestrictBody {
 };
 
 template <int DIM>
-__global__ void __launch_bounds__(NT, 2) k_restrict(RestrictArgs a) {
+__global__ void __launch_bounds__(NT, CMG_RESTRICT_MINB) k_restrict(RestrictArgs a) {
   __shared__ SmemTile sm;
   __shared__ int smb[6];
   const Geo g = a.g;
