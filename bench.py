@@ -136,8 +136,9 @@ def oracle_fmg_rate(prob_name: str, L: int, cfg, max_seconds: float = 30.0):
 
 
 def pick_sample_level(prob_name: str, Lmax: int, dim: int) -> int:
-    # bounded oracle sample: about 10-30 s of host work
-    return min(Lmax, 7 if dim == 3 else 10)
+    # bounded oracle sample: a few to about 10 s of host work per solve on the
+    # GPU machine's cores (3-D L = 9 is 1.3e8 DoF)
+    return min(Lmax, 9 if dim == 3 else 12)
 
 
 def run_reference(args, wl):

@@ -347,8 +347,10 @@ __device__ inline void meta_flush(MetaAcc a, int *meta, int *sm2) {
   }
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0 && sm2[0]) {
-    atomicMax(meta, sm2[0]);
-    atomicMax(meta + 1, sm2[1]);
+    // the pair only grows: skip the (same-address, serialising) atomic when
+    // the current value already dominates
+    if (sm2[0] > *(volatile int *)meta) atomicMax(meta, sm2[0]);
+    if (sm2[1] > *(volatile int *)(meta + 1)) atomicMax(meta + 1, sm2[1]);
   }
 }
 

@@ -34,7 +34,7 @@ namespace cmg {
 
 // ------------------------------------------------------------------ accumulator -> BFP
 template <int DIM>
-__global__ void __launch_bounds__(NT) k_acc_encode(AccArgs a) {
+__global__ void __launch_bounds__(NT, 6) k_acc_encode(AccArgs a) {
   __shared__ uint32_t pk[TY][33];
   __shared__ int smr[2], smy[2], smt[2];
   const Geo g = a.g;
@@ -48,23 +48,34 @@ __global__ void __launch_bounds__(NT) k_acc_encode(AccArgs a) {
   mr.init();
   my.init();
   mt.init();
-  const long long blk = (long long)blockIdx.x * TY + ty;
-  if (blk < g.nblocks) {
-    const long long row = blk / g.nbx;
-    const int bx = (int)(blk - row * g.nbx);
+  // each warp rounds a contiguous run of blocks (block indices of a level fit in int)
+  const int nwarps = gridDim.x * TY, w = blockIdx.x * TY + ty;
+  const int nbl = (int)g.nblocks, chunk = (nbl + nwarps - 1) / nwarps;
+  const int b0 = imin(nbl, w * chunk), b1 = imin(nbl, b0 + chunk);
+  int row = b0 / g.nbx, bx = b0 - row * g.nbx;
+  long long vn = 0;  // value of the next block, loaded one block ahead
+  auto load = [&](int r, int x) -> long long {
+    const int i = x * 32 + lane;
+    return i < g.n ? a.acc.v[(long long)r * g.R + i] : 0;
+  };
+  if (b0 < b1) vn = load(row, bx);
+  for (int blk = b0; blk < b1; blk++) {
     const int i = bx * 32 + lane;
-    const long long p = row * g.R + i;
-    long long v = 0;
-    if (i < g.n) {
-      v = a.acc.v[p];
-      a.acc.v[p] = 0;  // ready for the next accumulation
+    const long long p = (long long)row * g.R + i;
+    long long v = vn;
+    if (i < g.n) a.acc.v[p] = 0;  // ready for the next accumulation
+    int nrow = row, nbx = bx + 1;
+    if (nbx == g.nbx) {
+      nbx = 0;
+      nrow++;
     }
+    if (blk + 1 < b1) vn = load(nrow, nbx);
     ck62(v, ovf);
     if (a.chain) {  // t^_l = round(R t^_(l+1)) at the width of Table 1, stored
       int et, st;
       int qt = encode_block(v, G, a.t_out.W, et, st, a.err);
       v = rounded_value(v, qt, st);
-      pack_block(qt, a.t_out.W, pk[ty], a.t_out.words + blk * a.t_out.W);
+      pack_block(qt, a.t_out.W, pk[ty], a.t_out.words + (long long)blk * a.t_out.W);
       if (lane == 0) {
         a.t_out.exps[blk] = (int8_t)et;
         mt.add(et);
@@ -72,7 +83,7 @@ __global__ void __launch_bounds__(NT) k_acc_encode(AccArgs a) {
     }
     int e, sh;
     int q = encode_block(v, G, a.r_out.W, e, sh, a.err);
-    pack_block(q, a.r_out.W, pk[ty], a.r_out.words + blk * a.r_out.W);
+    pack_block(q, a.r_out.W, pk[ty], a.r_out.words + (long long)blk * a.r_out.W);
     if (lane == 0) {
       a.r_out.exps[blk] = (int8_t)e;
       mr.add(e);
@@ -81,12 +92,14 @@ __global__ void __launch_bounds__(NT) k_acc_encode(AccArgs a) {
       long long rr = rounded_value(v, q, sh);
       int ey, sy;
       int qy = encode_block(mul_ck(rr, a.c_num, a.cbits, ovf), Gcr, a.y_out.W, ey, sy, a.err);
-      pack_block(qy, a.y_out.W, pk[ty], a.y_out.words + blk * a.y_out.W);
+      pack_block(qy, a.y_out.W, pk[ty], a.y_out.words + (long long)blk * a.y_out.W);
       if (lane == 0) {
         a.y_out.exps[blk] = (int8_t)ey;
         my.add(ey);
       }
     }
+    row = nrow;
+    bx = nbx;
   }
   ovf_flush(ovf, a.err, 401);
   meta_flush(mr, a.r_out.meta, smr);
@@ -366,9 +379,25 @@ __global__ void k_decode_f64(CodecArgs a) {
 }
 
 // ------------------------------------------------------------------ launchers
+// SMs of the current device (queried once; 152 on GB300)
+static int sm_count() {
+  static int n = 0;
+  if (n <= 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      return 152;
+  }
+  return n;
+}
+
 void launch_acc_encode(int dim, const AccArgs &a, cudaStream_t st) {
   dim3 b(32, TY);
-  unsigned nb = (unsigned)((a.g.nblocks + TY - 1) / TY);
+  // one wave of 6 CTAs of 8 warps per SM, each warp a contiguous run of blocks
+  const long long want = (a.g.nblocks + TY - 1) / TY, cap = 6ll * sm_count();
+  unsigned nb = (unsigned)(want < cap ? want : cap);
   if (dim == 3) k_acc_encode<3><<<nb, b, 0, st>>>(a);
   else k_acc_encode<2><<<nb, b, 0, st>>>(a);
 }
