@@ -459,7 +459,28 @@ __device__ __forceinline__ void march_none(const Tile &T, int nplanes_dim2, Body
 }
 
 // ------------------------------------------------------------------ sweep
-template <int DIM>
+// The sweep shapes the IR iteration launches, compiled separately so that each
+// carries only its own work; SW_GENERIC takes every option at run time (step-wise API).
+enum SweepMode {
+  SW_GENERIC = 0,
+  SW_DOWN,           // y~' = round(y~ + c (rc - A y~))
+  SW_UP,             // operand y~ + P w_(l-1)
+  SW_UP_CORR,        // last up-sweep on the finest level: u~ += y~' (y~' not stored)
+  SW_UP_CORR_UH,     // ... and u^_l for the next FMG level
+  SW_UP_CORR_W_UH,   // last up-sweep below the finest level: u~ += y~', w_l, u^_l
+};
+
+template <int M>
+struct SwF {
+  static constexpr bool fixed = M != SW_GENERIC;
+  static constexpr bool z = M >= SW_UP;
+  static constexpr bool wy = M == SW_DOWN || M == SW_UP;
+  static constexpr bool corr = M >= SW_UP_CORR;
+  static constexpr bool uh = M == SW_UP_CORR_UH || M == SW_UP_CORR_W_UH;
+  static constexpr bool w = M == SW_UP_CORR_W_UH;
+};
+
+template <int DIM, int M>
 struct SweepBody {
   const SweepArgs &a;
   const Geo &g;
@@ -476,11 +497,19 @@ struct SweepBody {
   MetaAcc my, mu;
   uint32_t *pk;
 
+  // options: compile-time for the fixed shapes (y~ present), run-time otherwise
+  __device__ __forceinline__ bool HY() const { return SwF<M>::fixed ? true : (bool)a.has_y; }
+  __device__ __forceinline__ bool HZ() const { return SwF<M>::fixed ? SwF<M>::z : (bool)a.has_z; }
+  __device__ __forceinline__ bool WY() const { return SwF<M>::fixed ? SwF<M>::wy : (bool)a.write_y; }
+  __device__ __forceinline__ bool CORR() const { return SwF<M>::fixed ? SwF<M>::corr : (bool)a.corr; }
+  __device__ __forceinline__ bool WW() const { return SwF<M>::fixed ? SwF<M>::w : (bool)a.write_w; }
+  __device__ __forceinline__ bool WUH() const { return SwF<M>::fixed ? SwF<M>::uh : (bool)a.write_uh; }
+
   __device__ __forceinline__ void prefetch(int k) {
     if (!rowok) return;
     const int blk = k * g.n * g.nbx + bip;
     rc_n = raw_load(a.rc, blk, cprc, true);
-    if (a.corr) u_n = raw_load(a.u_in, blk, cpu, true);
+    if (CORR()) u_n = raw_load(a.u_in, blk, cpu, true);
   }
   __device__ __forceinline__ void advance() {
     rc_c = rc_n;
@@ -495,27 +524,27 @@ struct SweepBody {
     const int Gres = imin(blk_lsb(erc, a.rc.W), GA);
     const int Mres = imax(erc == -128 ? MAG_NONE : erc, MA) + 1;
     const int Gcr = Gres + a.c_exp;
-    const int Gy = a.has_y ? imin(GF, Gcr) : Gcr;
+    const int Gy = HY() ? imin(GF, Gcr) : Gcr;
     if (!pt) S = 0;
     long long ynew;
     // static range of this block (warp-uniform); else per-value checks
     if (Gres >= GRID_NONE / 2 || (Mres - Gres <= 62 - a.cbits && Mres + a.cbits + a.c_exp - Gy <= 61 &&
-                                  (!a.has_y || MF - Gy <= 61))) {
+                                  (!HY() || MF - Gy <= 61))) {
       const long long res = raw_val(rc, cprc.boff, a.rc.W, Gres) - shl_fast(S, GA - Gres);
       ynew = shl_fast(res * a.c_num, Gcr - Gy);
-      if (a.has_y) ynew += shl_fast(own, GF - Gy);
+      if (HY()) ynew += shl_fast(own, GF - Gy);
     } else {
       if (erc != -128 && erc - Gres > 61) ovf = true;
       const long long res = raw_val(rc, cprc.boff, a.rc.W, Gres) - shl_ck(S, GA - Gres, ovf);
       ck62(res, ovf);
       ynew = shl_ck(mul_ck(res, a.c_num, a.cbits, ovf), Gcr - Gy, ovf);
-      if (a.has_y) ynew += shl_ck(own, GF - Gy, ovf);
+      if (HY()) ynew += shl_ck(own, GF - Gy, ovf);
       ck62(ynew, ovf);
     }
     int e, sh;
     const int q = encode_block(ynew, Gy, a.Wy, e, sh, a.err);
     const long long yr = rounded_value(ynew, q, sh);
-    if (a.write_y) {
+    if (WY()) {
       pack_block(q, a.Wy, pk, a.y_out.words + (long long)blk * a.Wy);
       if (lane == 0) {
         a.y_out.exps[blk] = (int8_t)e;
@@ -524,7 +553,7 @@ struct SweepBody {
     }
     long long ur = 0;
     int Gu = Gy, eu = -128;
-    if (a.corr) {
+    if (CORR()) {
       const int eu0 = u.e;
       Gu = imin(blk_lsb(eu0, a.u_in.W), Gy);
       if (e != -128 || eu0 != -128)
@@ -540,14 +569,14 @@ struct SweepBody {
       }
     }
     const long long p = (long long)(k * g.n + j) * g.R + i;
-    if (a.write_w) {  // w_l = y~' + P w_(l-1); P w_(l-1) = F - y~ at this node
+    if (WW()) {  // w_l = y~' + P w_(l-1); P w_(l-1) = F - y~ at this node
       // block grid: the coarser of the grids y~' and P w_(l-1) are exact on
       const int gY = e == -128 ? GRID_NONE : imax(e - a.Wy + 1, Gy);
-      const int gw = imin(gY, a.has_z ? GPw : GRID_NONE);
+      const int gw = imin(gY, HZ() ? GPw : GRID_NONE);
       long long w = 0;
       if (gw < GRID_NONE / 2) {
-        const long long pw = (a.has_z && pt) ? F0 - (a.has_y ? own : 0) : 0;
-        if (imax(a.has_z ? MPw : MAG_NONE, e == -128 ? MAG_NONE : e) + 1 - gw <= 62) {
+        const long long pw = (HZ() && pt) ? F0 - (HY() ? own : 0) : 0;
+        if (imax(HZ() ? MPw : MAG_NONE, e == -128 ? MAG_NONE : e) + 1 - gw <= 62) {
           w = regrid(yr, Gy, gw) + regrid(pw, GF, gw);
         } else {
           w = regrid(yr, Gy, gw) + (gw >= GF ? regrid(pw, GF, gw) : shl_ck(pw, GF - gw, ovf));
@@ -556,7 +585,7 @@ struct SweepBody {
       }
       store_tmp_on(w, gw, a.w_out.v + p, a.w_out.gb + blk, pt, ovf);
     }
-    if (a.write_uh) {  // u^_l = u~_l' + P u^_(l-1)
+    if (WUH()) {  // u^_l = u~_l' + P u^_(l-1)
       if (ring_u || !a.has_uhc) {
         const int gU = eu == -128 ? GRID_NONE : imax(eu - a.u_out.W + 1, Gu);
         const int gP = a.has_uhc ? G1u - 1 : GRID_NONE;
@@ -585,8 +614,12 @@ struct SweepBody {
   }
 };
 
-template <int DIM>
+template <int DIM, int M>
 __global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
+  using F = SwF<M>;
+  const bool has_y = F::fixed ? true : (bool)a.has_y, has_z = F::fixed ? F::z : (bool)a.has_z;
+  const bool write_y = F::fixed ? F::wy : (bool)a.write_y, corr = F::fixed ? F::corr : (bool)a.corr;
+  const bool write_uh = F::fixed ? F::uh : (bool)a.write_uh;
   __shared__ SmemTile sm;
   __shared__ uint32_t pk[TY][33];
   __shared__ int smy[2], smu[2], smb[6];
@@ -594,14 +627,14 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
   const Tile T = make_tile(g);
   if (tid == 0) smy[0] = smy[1] = smu[0] = smu[1] = 0;
-  const bool uring_wanted = a.write_uh && a.has_uhc;
+  const bool uring_wanted = write_uh && a.has_uhc;
   Bounds bs, bt, bu;
-  footprint_bounds<DIM>(g, a.gc, T, a.y_in, a.has_y, a.wc, a.has_z, a.uhc, uring_wanted, smb, bs, bt, bu);
+  footprint_bounds<DIM>(g, a.gc, T, a.y_in, has_y, a.wc, has_z, a.uhc, uring_wanted, smb, bs, bt, bu);
   const Bounds bF = operand_of(bs, bt);
   const int GF = bF.G, MF = bF.M;
   const int sA = (DIM - 2) * g.l;
   if (tid == 0 && GF < GRID_NONE / 2 && MF + 4 - GF > 62) flag_range(a.err, 101, MF + 4, GF);
-  SweepBody<DIM> b{a, g};
+  SweepBody<DIM, M> b{a, g};
   b.GF = GF;
   b.MF = MF;
   b.GA = GF - sA;
@@ -620,7 +653,7 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
   b.pt = b.rowok && b.i < g.n;
   b.bip = b.rowok ? b.j * g.nbx + T.bx : 0;
   b.cprc = code_pos(lane, a.rc.W);
-  b.cpu = code_pos(lane, a.corr ? a.u_in.W : 1);
+  b.cpu = code_pos(lane, corr ? a.u_in.W : 1);
   b.ovf = false;
   b.my.init();
   b.mu.init();
@@ -629,8 +662,8 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
   in.s = a.y_in;
   in.t = a.wc;
   in.u = a.uhc;
-  in.has_s = a.has_y;
-  in.has_t = a.has_z;
+  in.has_s = has_y;
+  in.has_t = has_z;
   in.has_u = b.ring_u;
   in.GF = GF;
   in.G1t = GF + 1;
@@ -638,8 +671,8 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
   if (in.has_s || in.has_t || in.has_u) march<DIM>(g, a.gc, T, in, sm, b);
   else march_none(T, DIM == 2, b);
   ovf_flush(b.ovf, a.err, 102);
-  if (a.write_y) meta_flush(b.my, a.y_out.meta, smy);
-  if (a.corr) meta_flush(b.mu, a.u_out.meta, smu);
+  if (write_y) meta_flush(b.my, a.y_out.meta, smy);
+  if (corr) meta_flush(b.mu, a.u_out.meta, smu);
 }
 
 // ------------------------------------------------------------------ residual
@@ -943,10 +976,28 @@ dim3 stencil_grid(const Geo &g) {
 
 }  // namespace
 
+template <int DIM>
+static void launch_sweep_dim(const SweepArgs &a, cudaStream_t st) {
+  const dim3 grid = stencil_grid(a.g), b(32, TY);
+  int m = SW_GENERIC;
+  if (a.has_y) {
+    if (!a.corr && a.write_y && !a.write_w && !a.write_uh) m = a.has_z ? SW_UP : SW_DOWN;
+    else if (a.corr && a.has_z && !a.write_y && !a.write_w) m = a.write_uh ? SW_UP_CORR_UH : SW_UP_CORR;
+    else if (a.corr && a.has_z && !a.write_y && a.write_w && a.write_uh) m = SW_UP_CORR_W_UH;
+  }
+  switch (m) {
+    case SW_DOWN: k_sweep<DIM, SW_DOWN><<<grid, b, 0, st>>>(a); break;
+    case SW_UP: k_sweep<DIM, SW_UP><<<grid, b, 0, st>>>(a); break;
+    case SW_UP_CORR: k_sweep<DIM, SW_UP_CORR><<<grid, b, 0, st>>>(a); break;
+    case SW_UP_CORR_UH: k_sweep<DIM, SW_UP_CORR_UH><<<grid, b, 0, st>>>(a); break;
+    case SW_UP_CORR_W_UH: k_sweep<DIM, SW_UP_CORR_W_UH><<<grid, b, 0, st>>>(a); break;
+    default: k_sweep<DIM, SW_GENERIC><<<grid, b, 0, st>>>(a); break;
+  }
+}
+
 void launch_sweep(int dim, const SweepArgs &a, cudaStream_t st) {
-  dim3 b(32, TY);
-  if (dim == 3) k_sweep<3><<<stencil_grid(a.g), b, 0, st>>>(a);
-  else k_sweep<2><<<stencil_grid(a.g), b, 0, st>>>(a);
+  if (dim == 3) launch_sweep_dim<3>(a, st);
+  else launch_sweep_dim<2>(a, st);
 }
 
 void launch_residual(int dim, const ResidArgs &a, cudaStream_t st) {
