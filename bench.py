@@ -245,6 +245,13 @@ def run_gpu(args, wl):
                 "avg_launch_ms": sw_ms / sw_n if sw_n else None,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
     whole_frac = (reports[0]["alg_bytes"] / (ms_step * 1e-3) / 1e9) / peak
+    # Sec. 6.2 storage model for this workload (mantissa bits, CMG vs BFPMG) next to
+    # the measured layout (exponents, row padding and the Jacobi ping-pong included)
+    smod = cmg.storage_model(cfg.dim, Lmax, cfg.k_u, cfg.k_r, cfg.b1, cfg.b2)
+    storage = {"cmg_fmg_bits_per_dof": smod["cmg_fmg_bits"] / smod["dofs"],
+               "bfpmg_fmg_bits_per_dof": smod["bfpmg_fmg_bits"] / smod["dofs"],
+               "fmg_saving": smod["fmg_saving"], "vector_saving": smod["vector_saving"],
+               "measured_bits_per_dof": reports[0]["persistent_bits"] / dofs}
     # where one solve spends its device time (the last timed step), per kernel kind
     kernels = {k: {"ms": round(v["ms"], 4), "launches": v["launches"],
                    "GB_per_s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
@@ -321,6 +328,7 @@ def run_gpu(args, wl):
         "nodal_rel_err_sampled": nodal_rel,
         "roofline": roofline,
         "kernels_last_step": kernels,
+        "storage_model": storage,
         "cpu_baseline": cpu,
         "e2e": {"value": world * dofs / e2e_s, "unit": "DoF/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

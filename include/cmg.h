@@ -223,6 +223,36 @@ cmg_status cmg_decode_compact(int dim, int L, const uint32_t *const *words_dev,
                               const int8_t *const *exps_dev, const int *widths, int64_t z0,
                               int64_t nz, double *out_dev, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Analytic storage model (Sec. 6.2 of the paper: mantissas of regressive-
+ * precision vectors, and the comparison with progressive-precision FMG in BFP
+ * arithmetic, "BFPMG").  Host-only arithmetic; no device work.
+ *
+ * Levels are this library's: level l = 1..L has n_l = (2^l - 1)^dim interior
+ * DoF (the paper's level l - 1).  A regressive(+k, b) vector has k (L - l) + b
+ * bits per value on level l (eq. regressive), a progressive(+k, b) one
+ * k (l - 1) + b.  Mantissa bits only (sign included); exponents, padding and
+ * the sublinear temporaries are not counted (the paper calls them negligible or
+ * sublinear).  With k_u = p + 1 and k_r = m:
+ *   cmg_vector  = sum_l n_l (k_u (L - l) + b1)                     (u~)
+ *   cmg_fmg     = cmg_vector + 2 sum_l n_l (k_r (L - l) + b2)      (u~, r, y~)
+ *   bfpmg_vector = n_L (k_u (L - 1) + b1)                          (u_L)
+ *   bfpmg_fmg   = bfpmg_vector + n_L (k_r (L - 1) + b2)            (r_L)
+ *               + n_(L-1) (k_r (L - 2) + b2)                       (r_(L-1))
+ *               + sum_l n_l (k_r (l - 1) + b2)                     (y_1..L)
+ * following the paper's assumptions for BFPMG (memory only for u_L, r_L,
+ * r_(L-1) and y; matrices and right-hand side on the fly; same increments and
+ * constants as CMG).  Savings are the BFPMG / CMG ratios.
+ * Returns CMG_EINVAL for dim outside 1..3, L outside 1..40 or negative /
+ * zero widths. */
+typedef struct {
+  double dofs;               /* n_L */
+  double cmg_vector_bits, cmg_fmg_bits;
+  double bfpmg_vector_bits, bfpmg_fmg_bits;
+  double vector_saving, fmg_saving;
+} cmg_storage;
+cmg_status cmg_storage_model(int dim, int L, int k_u, int k_r, int b1, int b2, cmg_storage *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,13 @@ class Report(ctypes.Structure):
 
 
 _vp, _i64, _i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+class Storage(ctypes.Structure):
+    _fields_ = [("dofs", ctypes.c_double), ("cmg_vector_bits", ctypes.c_double),
+                ("cmg_fmg_bits", ctypes.c_double), ("bfpmg_vector_bits", ctypes.c_double),
+                ("bfpmg_fmg_bits", ctypes.c_double), ("vector_saving", ctypes.c_double),
+                ("fmg_saving", ctypes.c_double)]
+
+
 _SIGS = {
     "cmg_encode": (_i32, [_vp, _i64, _i32, _vp, _vp, _vp]),
     "cmg_decode": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
@@ -84,6 +91,7 @@ _SIGS = {
     "cmg_decode_solution": (_i32, [_vp, _i64, _i64, _vp]),
     "cmg_state_save": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
     "cmg_state_load": (_i32, [_vp, _vp, ctypes.c_size_t]),
+    "cmg_storage_model": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32, ctypes.POINTER(Storage)]),
     "cmg_kernel_stats": (_i32, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "cmg_decode_compact_scratch_bytes": (ctypes.c_size_t, [_i32, _i32]),
@@ -97,6 +105,15 @@ for _name, (_res, _args) in _SIGS.items():
 
 def lib() -> ctypes.CDLL:
     return _lib
+
+
+def storage_model(dim: int, L: int, k_u: int, k_r: int, b1: int, b2: int) -> dict:
+    """Sec. 6.2 mantissa bits of CMG and BFPMG storage (see cmg_storage_model)."""
+    out = Storage()
+    st = _lib.cmg_storage_model(dim, L, k_u, k_r, b1, b2, ctypes.byref(out))
+    if st != OK:
+        raise CmgError(st, "cmg_storage_model", "invalid arguments")
+    return {name: getattr(out, name) for name, _ in Storage._fields_}
 
 
 def exported_symbols():

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -1131,4 +1132,38 @@ extern "C" cmg_status cmg_decode(const uint32_t *words, const int8_t *exps, int6
   a.err = err;
   launch_decode_f64(a, st);
   return codec_finish(err, st);
+}
+
+// ---------------------------------------------------------------- storage model
+// Sec. 6.2 mantissa counts of CMG (regressive) and BFPMG (progressive) storage;
+// see include/cmg.h for the formulas.
+extern "C" cmg_status cmg_storage_model(int dim, int L, int k_u, int k_r, int b1, int b2, cmg_storage *out) {
+  if (!out || dim < 1 || dim > 3 || L < 1 || L > 40 || k_u < 0 || k_r < 0 || b1 < 1 || b2 < 1)
+    return CMG_EINVAL;
+  auto n_of = [dim](int l) {
+    if (l < 1) return 0.0;
+    const double side = std::ldexp(1.0, l) - 1.0;
+    double v = 1.0;
+    for (int a = 0; a < dim; a++) v *= side;
+    return v;
+  };
+  double cu = 0, cr = 0, py = 0;
+  for (int l = 1; l <= L; l++) {
+    const double n = n_of(l);
+    cu += n * (double)(k_u * (L - l) + b1);
+    cr += n * (double)(k_r * (L - l) + b2);
+    py += n * (double)(k_r * (l - 1) + b2);
+  }
+  const double nL = n_of(L);
+  cmg_storage s{};
+  s.dofs = nL;
+  s.cmg_vector_bits = cu;
+  s.cmg_fmg_bits = cu + 2 * cr;
+  s.bfpmg_vector_bits = nL * (double)(k_u * (L - 1) + b1);
+  s.bfpmg_fmg_bits = s.bfpmg_vector_bits + nL * (double)(k_r * (L - 1) + b2) +
+                     n_of(L - 1) * (double)(k_r * (L - 2) + b2) + py;
+  s.vector_saving = s.bfpmg_vector_bits / s.cmg_vector_bits;
+  s.fmg_saving = s.bfpmg_fmg_bits / s.cmg_fmg_bits;
+  *out = s;
+  return CMG_OK;
 }

@@ -721,7 +721,11 @@ __device__ __forceinline__ long long rne96(long long hi, unsigned lo, int fsh) {
   return rne_shift128(((__int128)hi << 32) + (__int128)lo, fsh);
 }
 
-template <int DIM>
+// residual shapes: RS_FIRST (the IR iteration with pre-smoothing: r and the first
+// sweep's y~, u^_(L-1) present) compiled apart from the run-time generic one
+enum ResidMode { RS_GENERIC = 0, RS_FIRST };
+
+template <int DIM, int M>
 struct ResidBody {
   const ResidArgs &a;
   const Geo &g;
@@ -734,6 +738,8 @@ struct ResidBody {
   MetaAcc mr, my, mt;
   uint32_t *pk;
 
+  __device__ __forceinline__ bool FS() const { return M == RS_FIRST ? true : (bool)a.first_sweep; }
+  __device__ __forceinline__ bool WT() const { return M == RS_FIRST ? false : (bool)a.write_t; }
   __device__ __forceinline__ void prefetch(int) {}
   __device__ __forceinline__ void advance() {}
 
@@ -774,7 +780,7 @@ struct ResidBody {
       a.r_out.exps[blk] = (int8_t)e;
       mr.add(e);
     }
-    if (a.first_sweep) {  // y~ = round(c r): the first Jacobi sweep from y~ = 0
+    if (FS()) {  // y~ = round(c r): the first Jacobi sweep from y~ = 0
       const long long rr = rounded_value(t, q, sh);
       int ey, sy;
       const int qy = encode_block(fast ? rr * a.c_num : mul_ck(rr, a.c_num, a.cbits, ovf), Gcr, a.y_out.W, ey,
@@ -785,7 +791,7 @@ struct ResidBody {
         my.add(ey);
       }
     }
-    if (a.write_t) {  // t^_L at the width of Table 1, for the restriction chain
+    if (WT()) {  // t^_L at the width of Table 1, for the restriction chain
       int et, st;
       const int qt = encode_block(t, Gt, a.t_out.W, et, st, a.err);
       pack_block(qt, a.t_out.W, pk, a.t_out.words + (long long)blk * a.t_out.W);
@@ -797,8 +803,11 @@ struct ResidBody {
   }
 };
 
-template <int DIM>
+template <int DIM, int M>
 __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
+  const bool first_sweep = M == RS_FIRST ? true : (bool)a.first_sweep;
+  const bool write_t = M == RS_FIRST ? false : (bool)a.write_t;
+  const bool has_uhc = M == RS_FIRST ? true : (bool)a.has_uhc;
   __shared__ SmemTile sm;
   __shared__ RhsSmem rs;
   __shared__ uint32_t pk[TY][33];
@@ -828,14 +837,14 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
     }
   }
   Bounds bs, bt, bu;
-  footprint_bounds<DIM>(g, a.gc, T, a.u, true, a.uhc, a.has_uhc, a.uhc, false, smb, bs, bt, bu);
+  footprint_bounds<DIM>(g, a.gc, T, a.u, true, a.uhc, has_uhc, a.uhc, false, smb, bs, bt, bu);
   const Bounds bF = operand_of(bs, bt);
   const int GF = bF.G, MF = bF.M;
   const int sA = (DIM - 2) * g.l;
   const int GA = GF - sA, MA = MF + 4 - sA;
   const int Gt = imin(a.Gf, GA), Mt = imax(a.Gf + 51, MA) + 1;
   if (tid == 0 && GF < GRID_NONE / 2 && MF + 4 - GF > 62) flag_range(a.err, 201, MF + 4, GF);
-  ResidBody<DIM> b{a, g, rs};
+  ResidBody<DIM, M> b{a, g, rs};
   b.GF = GF;
   b.GA = GA;
   b.Gt = Gt;
@@ -843,7 +852,7 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   b.k0 = T.k0;
   // the bound |t| < 2^Mt is loose (t is a residual, far below |f| + |A F|): when
   // it does not fit, every value is checked instead
-  b.fast = Mt - Gt <= 62 && (!a.first_sweep || Mt + 1 + a.cbits - Gt <= 62);
+  b.fast = Mt - Gt <= 62 && (!first_sweep || Mt + 1 + a.cbits - Gt <= 62);
   b.rhs_sm = rhs_sm;
   b.lane = lane;
   b.ty = ty;
@@ -862,7 +871,7 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   in.t = a.uhc;
   in.u = a.uhc;
   in.has_s = true;
-  in.has_t = a.has_uhc;
+  in.has_t = has_uhc;
   in.has_u = false;
   in.GF = GF;
   in.G1t = GF + 1;
@@ -870,8 +879,8 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   march<DIM>(g, a.gc, T, in, sm, b);
   ovf_flush(b.ovf, a.err, 202);
   meta_flush(b.mr, a.r_out.meta, smr);
-  if (a.first_sweep) meta_flush(b.my, a.y_out.meta, smy);
-  if (a.write_t) meta_flush(b.mt, a.t_out.meta, smt);
+  if (first_sweep) meta_flush(b.my, a.y_out.meta, smy);
+  if (write_t) meta_flush(b.mt, a.t_out.meta, smt);
 }
 
 // ------------------------------------------------------------------ restriction
@@ -1002,8 +1011,14 @@ void launch_sweep(int dim, const SweepArgs &a, cudaStream_t st) {
 
 void launch_residual(int dim, const ResidArgs &a, cudaStream_t st) {
   dim3 b(32, TY);
-  if (dim == 3) k_residual<3><<<stencil_grid(a.g), b, 0, st>>>(a);
-  else k_residual<2><<<stencil_grid(a.g), b, 0, st>>>(a);
+  const bool first = a.first_sweep && !a.write_t && a.has_uhc;
+  if (dim == 3) {
+    if (first) k_residual<3, RS_FIRST><<<stencil_grid(a.g), b, 0, st>>>(a);
+    else k_residual<3, RS_GENERIC><<<stencil_grid(a.g), b, 0, st>>>(a);
+  } else {
+    if (first) k_residual<2, RS_FIRST><<<stencil_grid(a.g), b, 0, st>>>(a);
+    else k_residual<2, RS_GENERIC><<<stencil_grid(a.g), b, 0, st>>>(a);
+  }
 }
 
 void launch_restrict(int dim, const RestrictArgs &a, cudaStream_t st) {
