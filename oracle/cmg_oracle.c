@@ -15,6 +15,7 @@
 #define _GNU_SOURCE
 #include "cmg_oracle.h"
 
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -176,6 +177,57 @@ void cmgo_restrict(int dim, int level, const double *fine, double *coarse) {
   lev gf = mklev(dim, level), gc = mklev(dim, level - 1);
   long long c = 0;
   restrict_(&gf, &gc, fine, coarse, &c);
+}
+
+/* ------------------------------------------------------------------------- */
+/* FP32 V-cycle (the precision split of Table 1: the cycle works in            */
+/* progressive(+m, b4) precision, the residual of fmgResidual in                */
+/* progressive(+p+m+1, b3); here the cycle runs in IEEE binary32, round to     */
+/* nearest, no fused multiply-add, in the fixed order below, while the outer    */
+/* residual, the level-1 solve and the correction of u~ stay exact)             */
+/* ------------------------------------------------------------------------- */
+
+/* x as binary32; flags *bad when x is not exactly a normal-range float or 0 */
+static inline float to_f32(double x, int *bad) {
+  float f = (float)x;
+  if ((double)f != x || (f != 0.0f && fabsf(f) < FLT_MIN)) *bad = 1;
+  return f;
+}
+
+static inline float get0f(const float *x, const lev *g, int i, int j, int k) {
+  if (i < 0 || i >= g->n || j < 0 || j >= g->n || k < 0 || k >= g->nz) return 0.0f;
+  return x[idx(g, i, j, k)];
+}
+
+/* (A_l x) in binary32: (2d) x_p, then minus the neighbours -x,+x,-y,+y,-z,+z,
+ * each operation rounded, then times h^(d-2) (a power of two) */
+static float A_at_f32(const float *x, const lev *g, int i, int j, int k) {
+  volatile float acc = (float)(2 * g->dim) * x[idx(g, i, j, k)];
+  acc = acc - get0f(x, g, i - 1, j, k);
+  acc = acc - get0f(x, g, i + 1, j, k);
+  acc = acc - get0f(x, g, i, j - 1, k);
+  acc = acc - get0f(x, g, i, j + 1, k);
+  if (g->dim == 3) {
+    acc = acc - get0f(x, g, i, j, k - 1);
+    acc = acc - get0f(x, g, i, j, k + 1);
+  }
+  return acc * ldexpf(1.0f, -(g->dim - 2) * g->l);
+}
+
+/* (P_l xc) in binary32: a copy, or (a + b) rounded, then halved */
+/* value at 1-based node (I, J, K); zero on the boundary.  K ignored in 2-D. */
+static inline float nodef(const float *x, const lev *g, int I, int J, int K) {
+  if (g->dim == 2) K = 1;
+  return get0f(x, g, I - 1, J - 1, K - 1);
+}
+
+static float P_at_f32(const float *xc, const lev *gc, int I, int J, int K) {
+  int sx = I & 1, sy = J & 1, sz = gc->dim == 3 ? (K & 1) : 0;
+  if (!sx && !sy && !sz) return nodef(xc, gc, I / 2, J / 2, K / 2);
+  volatile float a = nodef(xc, gc, (I - sx) / 2, (J - sy) / 2, (K - sz) / 2);
+  volatile float b = nodef(xc, gc, (I + sx) / 2, (J + sy) / 2, (K + sz) / 2);
+  volatile float s = a + b;
+  return s * 0.5f;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -625,6 +677,47 @@ static int jacobi(cmgo_ctx *c, int l, const double *z, long long *cnt) {
   return st;
 }
 
+/* The same sweep with binary32 arithmetic (FP32 V-cycle): F = fl(y + z) (or y),
+ * S = A F as in A_at_f32, res = fl(rc - S), y' = fl(y + fl(c res)); y' is then
+ * rounded into the BFP section like the exact sweep.  Every stored value the
+ * cycle reads must be an exact normal-range binary32 number (else ERANGE). */
+static int jacobi_f32(cmgo_ctx *c, int l, const float *z, long long *cnt) {
+  lev g = mklev(c->P.dim, l);
+  int bad = 0;
+  const float cl = to_f32(cjac(c, l, cnt), &bad);
+  float *F = (float *)malloc((size_t)g.np * sizeof(float));
+  float *yf = (float *)malloc((size_t)g.np * sizeof(float));
+  double *yn = (double *)malloc((size_t)g.np * sizeof(double));
+  if (!F || !yf || !yn) {
+    free(F);
+    free(yf);
+    free(yn);
+    return CMGO_ENOMEM;
+  }
+  for (int64_t p = 0; p < g.np; p++) {
+    yf[p] = to_f32(c->y[l].v[p], &bad);
+    volatile float f = yf[p];
+    if (z) f = f + z[p];
+    F[p] = f;
+  }
+#pragma omp parallel for collapse(2) reduction(| : bad) schedule(static)
+  for (int k = 0; k < g.nz; k++)
+    for (int j = 0; j < g.n; j++)
+      for (int i = 0; i < g.n; i++) {
+        int64_t p = idx(&g, i, j, k);
+        volatile float S = A_at_f32(F, &g, i, j, k);
+        volatile float res = to_f32(c->rc[l].v[p], &bad) - S;
+        volatile float cres = cl * res;
+        volatile float y2 = yf[p] + cres;
+        yn[p] = (double)y2;
+      }
+  int st = round_dense(&g, yn, Wr(c, l), &c->y[l]);
+  free(F);
+  free(yf);
+  free(yn);
+  return bad ? CMGO_ERANGE : st;
+}
+
 /* Down-leg on level l >= 2: y~_l = 0, nu1 sweeps on A y = rc_l (the coarser
  * sections are still zero, so z_l = 0), then the level-(l-1) right-hand side
  * rc_(l-1) = round(R_l (rc_l - A_l y~_l)), which equals r^_(l-1) - s^_(l-1) of
@@ -636,8 +729,38 @@ int cmgo_down(cmgo_ctx *c, int l) {
   int st = CMGO_OK;
   if (l == c->L) sec_copy(&c->rc[l], &c->r[l], &g);
   sec_zero(&c->y[l], &g, Wr(c, l));
-  for (int s = 0; s < c->P.nu1 && st == CMGO_OK; s++) st = jacobi(c, l, NULL, &cnt);
-  if (st == CMGO_OK) {
+  for (int s = 0; s < c->P.nu1 && st == CMGO_OK; s++)
+    st = c->P.arith ? jacobi_f32(c, l, NULL, &cnt) : jacobi(c, l, NULL, &cnt);
+  if (st == CMGO_OK && c->P.arith && c->P.nu1 > 0) {
+    /* FP32 cycle: d = fl(rc - A y) in binary32; R d is then formed exactly
+     * (binary32 rounding never leaves the grid of its inputs, so the exact sum
+     * of these d is what both implementations round into rc_(l-1)) */
+    float *yf = (float *)malloc((size_t)g.np * sizeof(float));
+    double *dd = (double *)malloc((size_t)g.np * sizeof(double));
+    double *rcc = (double *)malloc((size_t)gc.np * sizeof(double));
+    int bad = 0;
+    if (!yf || !dd || !rcc) {
+      free(yf);
+      free(dd);
+      free(rcc);
+      return setst(c, CMGO_ENOMEM);
+    }
+    for (int64_t p = 0; p < g.np; p++) yf[p] = to_f32(c->y[l].v[p], &bad);
+#pragma omp parallel for collapse(2) reduction(| : bad) schedule(static)
+    for (int k = 0; k < g.nz; k++)
+      for (int j = 0; j < g.n; j++)
+        for (int i = 0; i < g.n; i++) {
+          int64_t p = idx(&g, i, j, k);
+          volatile float S = A_at_f32(yf, &g, i, j, k);
+          volatile float d = to_f32(c->rc[l].v[p], &bad) - S;
+          dd[p] = (double)d;
+        }
+    restrict_(&g, &gc, dd, rcc, &cnt);
+    st = bad ? CMGO_ERANGE : round_dense(&gc, rcc, Wr(c, l - 1), &c->rc[l - 1]);
+    free(yf);
+    free(dd);
+    free(rcc);
+  } else if (st == CMGO_OK) {
     if (c->P.nu1 > 0) {
       double *Ay = (double *)malloc((size_t)g.np * sizeof(double));
       double *dd = (double *)malloc((size_t)g.np * sizeof(double));
@@ -684,6 +807,30 @@ int cmgo_up(cmgo_ctx *c, int l) {
   lev g = mklev(c->P.dim, l), gc = mklev(c->P.dim, l - 1);
   long long cnt = 0;
   int st = CMGO_OK;
+  if (c->P.arith) {
+    /* FP32 cycle: z = P w_(l-1) and w_l = fl(y~_l + z) in binary32 */
+    float *wc = (float *)malloc((size_t)gc.np * sizeof(float));
+    float *zf = (float *)malloc((size_t)g.np * sizeof(float));
+    int bad = 0;
+    if (!wc || !zf) {
+      free(wc);
+      free(zf);
+      return setst(c, CMGO_ENOMEM);
+    }
+    for (int64_t p = 0; p < gc.np; p++) wc[p] = to_f32(c->w[l - 1][p], &bad);
+    for (int k = 0; k < g.nz; k++)
+      for (int j = 0; j < g.n; j++)
+        for (int i = 0; i < g.n; i++) zf[idx(&g, i, j, k)] = P_at_f32(wc, &gc, i + 1, j + 1, k + 1);
+    for (int s = 0; s < c->P.nu2 && st == CMGO_OK; s++) st = jacobi_f32(c, l, zf, &cnt);
+    for (int64_t p = 0; p < g.np; p++) {
+      volatile float w = to_f32(c->y[l].v[p], &bad) + zf[p];
+      c->w[l][p] = (double)w;
+    }
+    free(wc);
+    free(zf);
+    c->inexact += cnt;
+    return setst(c, bad ? CMGO_ERANGE : st);
+  }
   double *z = (double *)malloc((size_t)g.np * sizeof(double));
   if (!z) return setst(c, CMGO_ENOMEM);
   prolong(&gc, &g, c->w[l - 1], z, &cnt);

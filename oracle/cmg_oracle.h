@@ -57,6 +57,8 @@ typedef struct {
   int N;        /* IR iterations per FMG level */
   int nu1, nu2; /* pre- and post-smoothing sweeps per level, nu2 >= 1 */
   double omega; /* Jacobi weight */
+  int arith;    /* 0: exact V-cycle; 1: FP32 V-cycle inside exact iterative
+                   refinement (see cmg_oracle.c, "FP32 V-cycle") */
 } cmgo_params;
 
 /* Section selectors. */
