@@ -127,7 +127,7 @@ def oracle_fmg_rate(prob_name: str, L: int, cfg, max_seconds: float = 30.0):
     import oracle
     prob = cmg_problems.make_problem(prob_name, L)
     o = oracle.Oracle.for_problem(prob, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1, nu2=cfg.nu2,
-                                  omega=cfg.omega)
+                                  omega=cfg.omega, arith=cfg.arith)
     t0 = time.perf_counter()
     o.fmg()
     dt = time.perf_counter() - t0
@@ -150,7 +150,7 @@ def run_reference(args, wl):
     import oracle
     oracle.build()
     from paper_2511_19036_gb300.cmg_config import config_for
-    cfg = config_for(prob_name, Lmax)
+    cfg = config_for(prob_name, Lmax, arith=1 if args.arith == "fp32" else 0)
     dim = cfg.dim
     Ls = pick_sample_level(prob_name, Lmax, dim)
     for _ in range(args.warmup):
@@ -198,7 +198,7 @@ def run_gpu(args, wl):
         dist.init_process_group("nccl")
     prob_name, Lmax, desc = WORKLOADS[wl]
     prob = cmg_problems.make_problem(prob_name, Lmax, seed=rank)
-    cfg = cmg.config_for(prob_name, Lmax)
+    cfg = cmg.config_for(prob_name, Lmax, arith=1 if args.arith == "fp32" else 0)
     stream = torch.cuda.Stream()
     solver = cmg.Solver(cfg, stream=stream, timing=True)
     solver.set_rhs(prob.tables, prob.scale_exp)
@@ -298,6 +298,25 @@ def run_gpu(args, wl):
         errs.append(float(np.max(np.abs(u - ue))))
         norms.append(float(np.max(np.abs(ue))))
     nodal_rel = max(errs) / max(norms)
+    # the FP32 cycle: its solution against the exact cycle's on the same planes
+    fp32_vs_exact = None
+    if cfg.arith == 1:
+        cfg64 = cmg.config_for(prob_name, Lmax)
+        ref = cmg.Solver(cfg64, stream=stream)
+        ref.set_rhs(prob.tables, prob.scale_exp)
+        ref.fmg_solve()
+        dmax, umax, err64 = 0.0, 0.0, []
+        for z in planes:
+            a = solver.decode_solution(z, 1).cpu().numpy()[0]
+            b = ref.decode_solution(z, 1).cpu().numpy()[0]
+            Y, X = np.meshgrid(x, x, indexing="ij")
+            ue = prob.exact_u(X, Y, (z + 1) * h) if cfg.dim == 3 else prob.exact_u(X, Y)
+            dmax = max(dmax, float(np.max(np.abs(a - b))))
+            umax = max(umax, float(np.max(np.abs(b))))
+            err64.append(float(np.max(np.abs(b - ue))))
+        fp32_vs_exact = {"max_rel_diff_sampled": dmax / umax,
+                         "nodal_rel_err_exact_cycle": max(err64) / max(norms)}
+        del ref
 
     if rank != 0:
         return 0
@@ -315,10 +334,12 @@ def run_gpu(args, wl):
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "int64" if cfg.arith == 0 else "f32 cycle + int64 refinement",
+        "data": "synthetic",
         "config": {"workload": wl, "description": desc, "dim": cfg.dim, "L_max": Lmax, "dofs": dofs,
                    "b1": cfg.b1, "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": "V(%d,%d)" % (cfg.nu1, cfg.nu2),
-                   "omega": cfg.omega, "l2": "working set larger than L2" if dofs > 1e8 else
+                   "omega": cfg.omega, "arith": "exact" if cfg.arith == 0 else "fp32 cycle",
+                   "l2": "working set larger than L2" if dofs > 1e8 else
                    "working set fits L2 (state per step re-read from L2)",
                    "parallelism": "replicas x%d" % world},
         "bits_per_dof": reports[0]["persistent_bits"] / dofs,
@@ -326,6 +347,7 @@ def run_gpu(args, wl):
         "alg_bytes_per_step": reports[0]["alg_bytes"],
         "whole_solve_hbm_frac": whole_frac,
         "nodal_rel_err_sampled": nodal_rel,
+        "fp32_vs_exact": fp32_vs_exact,
         "roofline": roofline,
         "kernels_last_step": kernels,
         "storage_model": storage,
@@ -349,6 +371,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--arith", default="exact", choices=["exact", "fp32"],
+                    help="exact V-cycle, or the binary32 V-cycle inside exact iterative refinement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)

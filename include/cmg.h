@@ -55,6 +55,8 @@ typedef enum {
 /* Parameters of Algorithm 3 with the precisions of Table 1 (P1: p = 1, m = 1).
  * Intermediate arithmetic is exact (fixed-point integers on the GPU); values are
  * rounded only where they are stored, as the paper's rounding rules prescribe. */
+enum { CMG_ARITH_EXACT = 0, CMG_ARITH_FP32 = 1 };
+
 typedef struct {
   int dim;             /* 2 or 3 */
   int L_max;           /* finest level, 1 <= L_max <= 14 (3-D: <= 12, so that
@@ -67,6 +69,12 @@ typedef struct {
   int nu1, nu2;        /* pre-/post-smoothing Jacobi sweeps, nu1 >= 0, nu2 >= 1 */
   int omega_num;       /* Jacobi weight omega = omega_num / 2^omega_log2den, */
   int omega_log2den;   /* which must make omega / (2d) a dyadic rational */
+  int arith;           /* CMG_ARITH_EXACT (0): exact V-cycle; CMG_ARITH_FP32 (1):
+                          the V-cycle (sweeps, inner residuals, restriction input,
+                          prolongated corrections) in binary32, round to nearest,
+                          in a fixed order, inside the exact iterative refinement
+                          (outer residual, level-1 solve and u~ correction exact);
+                          needs k_r (L_max - 1) + b2 + bitlen(Jacobi numerator) <= 24 */
 } cmg_params;
 
 /* Per-solve report filled by cmg_fmg_solve. */

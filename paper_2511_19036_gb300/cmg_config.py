@@ -17,16 +17,19 @@ class SolverConfig:
     omega_log2den: int = 2
     k_u: int = 2
     k_r: int = 1
+    arith: int = 0  # 0: exact V-cycle; 1: binary32 V-cycle inside exact iterative refinement
 
     @property
     def omega(self) -> float:
         return self.omega_num / float(1 << self.omega_log2den)
 
 
-def config_for(name: str, L_max: int) -> SolverConfig:
+def config_for(name: str, L_max: int, arith: int = 0) -> SolverConfig:
     """Widths and cycle of the standard workloads (2-D: Table 2 Poisson 2D p=1;
     3-D: found by the Sec. 7.1 search on the manufactured 3-D problem)."""
     dim = 2 if name.startswith("poisson2d") else 3
     if dim == 2:
-        return SolverConfig(dim=2, L_max=L_max, b1=4, b2=4, N_ir=3, nu1=2, nu2=2, omega_num=3, omega_log2den=2)
-    return SolverConfig(dim=3, L_max=L_max, b1=5, b2=3, N_ir=3, nu1=2, nu2=2, omega_num=3, omega_log2den=2)
+        return SolverConfig(dim=2, L_max=L_max, b1=4, b2=4, N_ir=3, nu1=2, nu2=2, omega_num=3, omega_log2den=2,
+                            arith=arith)
+    return SolverConfig(dim=3, L_max=L_max, b1=5, b2=3, N_ir=3, nu1=2, nu2=2, omega_num=3, omega_log2den=2,
+                        arith=arith)

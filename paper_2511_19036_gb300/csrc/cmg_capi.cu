@@ -208,11 +208,18 @@ extern "C" cmg_status cmg_params_check(const cmg_params *p) {
   // without pre-smoothing the restriction chain carries t^ at (p+1)L + b1 bits
   if (p->nu1 == 0 && p->k_u * p->L_max + p->b1 > 32) return CMG_ERANGE;
   if (p->omega_num <= 0 || p->omega_log2den < 0 || p->omega_log2den > 30) return CMG_EINVAL;
+  if (p->arith != CMG_ARITH_EXACT && p->arith != CMG_ARITH_FP32) return CMG_EINVAL;
   if (p->dim == 3 && p->omega_num % 3 != 0) return CMG_EINVAL;  // omega/6 must be dyadic
   // keep the Jacobi numerator small (it widens the exact integers by its bit length)
   int num = p->dim == 3 ? p->omega_num / 3 : p->omega_num;
   while (num % 2 == 0) num /= 2;
   if (num >= (1 << 10)) return CMG_EINVAL;
+  if (p->arith == CMG_ARITH_FP32) {
+    // binary32 must hold every r~ / y~ code exactly, and c rc of the fused first sweep
+    int cb = 0;
+    for (int t = num; t; t >>= 1) cb++;
+    if (p->k_r * (p->L_max - 1) + p->b2 + cb > 24) return CMG_ERANGE;
+  }
   return CMG_OK;
 }
 
@@ -565,6 +572,10 @@ static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
     v.u.W = un.W;
   }
   if (o.has_z) a.wc = tmp_of(LV(ctx, l - 1).w, LV(ctx, l - 1).wg, nullptr);
+  if (ctx->P.arith == CMG_ARITH_FP32) {  // binary32 w temporaries in the same buffers
+    if (o.has_z) a.wc_f = (const float *)LV(ctx, l - 1).w;
+    if (o.write_w) a.w_out_f = (float *)v.w;
+  }
   if (l > 1) a.uhc = tmp_of(LV(ctx, l - 1).uh, LV(ctx, l - 1).uhg, nullptr);
   if (o.write_w) a.w_out = tmp_of(v.w, v.wg, nullptr);
   if (o.write_uh) a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
@@ -574,8 +585,11 @@ static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
                  (o.has_z ? tmp_bytes(a.gc) : 0) + (o.write_y ? sec_bytes(v.g, a.Wy) : 0) +
                  (o.corr ? 2 * sec_bytes(v.g, a.u_out.W) : 0) + (o.write_w ? tmp_bytes(v.g) : 0) +
                  (o.write_uh ? tmp_bytes(v.g) + tmp_bytes(a.gc) : 0);
+  if (ctx->P.arith == CMG_ARITH_FP32)  // binary32 w: half the bytes
+    bytes -= 0.5 * ((o.has_z ? tmp_bytes(a.gc) : 0) + (o.write_w ? tmp_bytes(v.g) : 0));
   ev_begin(ctx, kstat(ctx, CMG_KIND_SWEEP, l));
-  launch_sweep(d, a, ctx->st);
+  if (ctx->P.arith == CMG_ARITH_FP32) launch_sweep_f32(d, a, ctx->st);
+  else launch_sweep(d, a, ctx->st);
   ev_end(ctx, kstat(ctx, CMG_KIND_SWEEP, l), bytes);
   if ((s = launched(ctx, bytes))) return s;
   if (o.write_y) {
@@ -601,7 +615,8 @@ static cmg_status do_restrict(cmg_ctx *ctx, int l, bool first_sweep_below) {
   a.acc = tmp_of(c.acc, nullptr, c.accmeta);
   a.err = ctx->err;
   ev_begin(ctx, kstat(ctx, CMG_KIND_RESTRICT, l));
-  launch_restrict(d, a, ctx->st);
+  if (ctx->P.arith == CMG_ARITH_FP32) launch_restrict_f32(d, a, ctx->st);
+  else launch_restrict(d, a, ctx->st);
   ev_end(ctx, kstat(ctx, CMG_KIND_RESTRICT, l), sec_bytes(v.g, a.y.W) + sec_bytes(v.g, a.rc.W) + 2 * tmp_bytes(c.g));
   cmg_status s = launched(ctx, sec_bytes(v.g, a.y.W) + sec_bytes(v.g, a.rc.W) + 2 * tmp_bytes(c.g));
   if (s) return s;
@@ -661,6 +676,7 @@ static cmg_status do_coarse(cmg_ctx *ctx, bool start, bool corr) {
       a.u_out = sec_of(ua);
     }
     a.w_out = tmp_of(v.w, v.wg, nullptr);
+    if (ctx->P.arith == CMG_ARITH_FP32) a.w_out_f = (float *)v.w;
     if (corr) a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
   }
   ev_begin(ctx, kstat(ctx, CMG_KIND_COARSE, 1));

@@ -187,7 +187,11 @@ __global__ void k_coarse(CoarseArgs a) {
     set_tmp1(a.uh_out, q, yG);
     return;
   }
-  set_tmp1(a.w_out, q, yG);  // w_1 = y~_1 (z_1 = 0)
+  if (a.w_out_f) {  // w_1 = y~_1 in binary32 (exact: W <= 24, normal range checked by the cycle)
+    a.w_out_f[0] = e == -128 ? 0.0f : ldexpf((float)q, yG);
+  } else {
+    set_tmp1(a.w_out, q, yG);  // w_1 = y~_1 (z_1 = 0)
+  }
   if (!a.corr) return;
   // u~_1 <- round(u~_1 + y~_1), u^_1 = u~_1
   int eu0 = a.u_in.exps[0];

@@ -21,6 +21,8 @@ struct SweepArgs {
   Sec y_in, rc, y_out, u_in, u_out;
   Tmp wc, w_out, uhc, uh_out;
   int c_num, c_exp, cbits;  // Jacobi factor c_l = c_num 2^c_exp, cbits = bitlen(c_num)
+  const float *wc_f;   // FP32 cycle: w_(l-1) in binary32 (padded level layout)
+  float *w_out_f;      // FP32 cycle: w_l in binary32
   int *err;
 };
 
@@ -70,6 +72,7 @@ struct CoarseArgs {
   Sec rc, y_out, u_in, u_out;
   int corr;            // fused u~_1 += y~_1 (cycle mode)
   Tmp w_out, uh_out;
+  float *w_out_f;      // FP32 cycle: w_1 = y~_1 in binary32 (else w_out)
   int *err;
 };
 
@@ -114,6 +117,8 @@ struct CodecArgs {
 void launch_sweep(int dim, const SweepArgs &a, cudaStream_t st);
 void launch_residual(int dim, const ResidArgs &a, cudaStream_t st);
 void launch_restrict(int dim, const RestrictArgs &a, cudaStream_t st);
+void launch_sweep_f32(int dim, const SweepArgs &a, cudaStream_t st);
+void launch_restrict_f32(int dim, const RestrictArgs &a, cudaStream_t st);
 void launch_acc_encode(int dim, const AccArgs &a, cudaStream_t st);
 void launch_coarse(const CoarseArgs &a, cudaStream_t st);
 void launch_repack(const RepackArgs &a, cudaStream_t st);

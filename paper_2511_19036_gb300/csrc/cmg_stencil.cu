@@ -31,17 +31,12 @@
 
 #include "cmg_device.cuh"
 #include "cmg_kernels.h"
+#include "cmg_stencil_common.cuh"
 
 namespace cmg {
 namespace {
 
-constexpr int CR = 7;               // coarse rows feeding fine rows j0-1 .. j0+TY
-constexpr int CX = 19;              // coarse columns feeding fine columns x0-1 .. x0+32
-constexpr int CRX = CR * CX;        // values of one ring plane
-constexpr int PW = 34;              // plane buffer row: 32 values and one halo value each side
-constexpr int PLANE = (TY + 2) * PW;
-constexpr int NHALO = 2 * 32 + 2 * (TY + 2);  // halo values of one plane
-constexpr int TMAXP = 8;
+constexpr int TMAXP = 8;  // right-hand-side terms with per-thread products in shared memory
 // resident CTAs per SM the register allocation is fitted to, per kernel
 #ifndef CMG_SWEEP_MINB
 #define CMG_SWEEP_MINB 3
@@ -51,247 +46,7 @@ constexpr int TMAXP = 8;
 #endif
 #ifndef CMG_RESTRICT_MINB
 #define CMG_RESTRICT_MINB 2
-#endif            // right-hand-side terms with per-thread products in shared memory
-
-__device__ inline bool first_cta() { return blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0; }
-
-// ------------------------------------------------------------------ compact reads
-struct Raw {
-  int e;            // block exponent (-128: all-zero block or outside)
-  uint32_t w0, w1;  // the word(s) holding the code
-};
-
-struct CodePos {
-  int woff, boff, two;  // word offset in the block, bit offset, code spans two words
-};
-
-__device__ __forceinline__ CodePos code_pos(int x, int W) {
-  CodePos c;
-  const int pos = x * W;
-  c.woff = pos >> 5;
-  c.boff = pos & 31;
-  c.two = c.boff + W > 32;
-  return c;
-}
-
-// issue the loads of one code and its block exponent (no use of the result yet)
-__device__ __forceinline__ Raw raw_load(const Sec &s, int blk, CodePos cp, bool ok) {
-  Raw r;
-  r.e = -128;
-  r.w0 = 0u;
-  r.w1 = 0u;
-  if (ok) {
-    r.e = __ldg(s.exps + blk);
-    const uint32_t *w = s.words + (long long)blk * s.W + cp.woff;
-    r.w0 = __ldg(w);
-    if (cp.two) r.w1 = __ldg(w + 1);
-  }
-  return r;
-}
-
-__device__ __forceinline__ int raw_code(const Raw &r, int boff, int W) {
-  const uint32_t bits = __funnelshift_r(r.w0, r.w1, boff);
-  return ((int)(bits << (32 - W))) >> (32 - W);
-}
-
-// the value on grid G (G at or below the block's grid e - W + 1)
-__device__ __forceinline__ long long raw_val(const Raw &r, int boff, int W, int G) {
-  if (r.e == -128) return 0;
-  return (long long)((unsigned long long)(long long)raw_code(r, boff, W) << (r.e - W + 1 - G));
-}
-
-// Left shift for the paths whose static range check passed: there every shift
-// of a nonzero value is below 63, and a shift of 64 or more only meets a zero
-// (an operand whose footprint is all zero), so the count is taken mod 64.
-__device__ __forceinline__ long long shl_fast(long long v, int s) {
-  return (long long)((unsigned long long)v << (s & 63));
-}
-
-// v on grid `from` re-expressed on grid `to`: exact right shift when to >= from
-// (the caller knows v to be a multiple of 2^(to - from)), left shift otherwise
-// (the caller checked the range)
-__device__ __forceinline__ long long regrid(long long v, int from, int to) {
-  const int d = to - from;
-  return d >= 0 ? (v >> (d & 63)) : (long long)((unsigned long long)v << ((-d) & 63));
-}
-
-// ------------------------------------------------------------------ tile geometry
-struct Tile {
-  int bx, x0, j0, k0, k1;
-  int cr0, cx0;  // coarse row / column of ring entry (0, 0)
-};
-
-__device__ __forceinline__ Tile make_tile(const Geo &g) {
-  Tile T;
-  T.bx = blockIdx.x;
-  T.x0 = T.bx * 32;
-  T.j0 = blockIdx.y * TY;
-  T.k0 = blockIdx.z * ZC;
-  T.k1 = imin(g.nz, T.k0 + ZC);
-  T.cr0 = ((T.j0 - 1) >> 1) - 1;
-  T.cx0 = ((T.x0 - 1) >> 1) - 1;
-  return T;
-}
-
-// One decode slot of a thread: a fixed (i, j) column of the CTA footprint.
-struct Slot {
-  bool ok;     // (i, j) inside the level's plane
-  int bip;     // block index inside a plane
-  int sm;      // index in a plane buffer
-  int oa, ob;  // P_l parents of (i, j) in a ring plane (row * CX + column)
-  CodePos cp;  // code position for the operand section's width
-};
-
-// (i, j) fine 0-based, (r, x) its place in the plane buffer.  The parents of
-// every footprint node fall in ring rows 1..6 and columns 1..18.
-__device__ __forceinline__ Slot make_slot(const Geo &g, int W, int i, int j, int r, int x, const Tile &T) {
-  Slot s;
-  s.ok = (unsigned)i < (unsigned)g.n && (unsigned)j < (unsigned)g.n;
-  s.bip = s.ok ? j * g.nbx + (i >> 5) : 0;
-  s.sm = r * PW + x;
-  const int I = i + 1, J = j + 1, sx = I & 1, sy = J & 1;
-  s.oa = (((J - sy) >> 1) - 1 - T.cr0) * CX + (((I - sx) >> 1) - 1 - T.cx0);
-  s.ob = (((J + sy) >> 1) - 1 - T.cr0) * CX + (((I + sx) >> 1) - 1 - T.cx0);
-  s.cp = code_pos(i & 31, W);
-  return s;
-}
-
-// coarse planes of the P_l parents of fine plane kf (3-D): K = kf + 1 odd has
-// parents in planes kf/2 - 1 and kf/2, K even in (kf - 1)/2 only
-template <int DIM>
-__device__ __forceinline__ void zparents(int kf, int &za, int &zb) {
-  if (DIM == 2) {
-    za = zb = 0;
-  } else if (kf & 1) {
-    za = zb = (kf - 1) >> 1;
-  } else {
-    za = (kf >> 1) - 1;
-    zb = kf >> 1;
-  }
-}
-
-// (P_l t) at a slot from a ring, on the ring's grid minus one
-__device__ __forceinline__ long long ring_p(const long long *ring, const Slot &s, int za, int zb) {
-  return ring[(za & 3) * CRX + s.oa] + ring[(zb & 3) * CRX + s.ob];
-}
-
-// One ring entry per thread (tid < CRX): a fixed coarse (ci, cj) column.
-struct Stager {
-  bool on, ok;
-  int bip;          // block index inside a coarse plane
-  int cj, ci;       // coarse row and column
-  long long v;      // loaded value, not yet stored
-  int gb;           // loaded descriptor
-};
-
-__device__ __forceinline__ Stager make_stager(const Geo &gc, const Tile &T, int tid) {
-  Stager s;
-  s.on = tid < CRX;
-  const int r = tid / CX, x = tid - (tid / CX) * CX;
-  const int cj = T.cr0 + r, ci = T.cx0 + x;
-  s.ok = s.on && (unsigned)ci < (unsigned)gc.n && (unsigned)cj < (unsigned)gc.n;
-  s.bip = s.ok ? cj * gc.nbx + (ci >> 5) : 0;
-  s.cj = s.ok ? cj : 0;
-  s.ci = s.ok ? ci : 0;
-  s.v = 0;
-  s.gb = 0;
-  return s;
-}
-
-__device__ __forceinline__ void stage_load(Stager &s, const Tmp &t, const Geo &gc, int c) {
-  s.v = 0;
-  s.gb = 0;
-  if (s.ok && (unsigned)c < (unsigned)gc.nz) {
-    s.gb = __ldg(t.gb + c * gc.n * gc.nbx + s.bip);
-    s.v = __ldg(t.v + (long long)(c * gc.n + s.cj) * gc.R + s.ci);
-  }
-}
-
-__device__ __forceinline__ void stage_store(const Stager &s, long long *ring, int c, int G1, int tid) {
-  if (s.on) ring[(c & 3) * CRX + tid] = (s.gb & 0xff) ? shl_fast(s.v, (s.gb >> 8) - G1) : 0;
-}
-
-// ------------------------------------------------------------------ footprint bounds
-struct Bounds {
-  int G;  // finest grid (GRID_NONE: all zero)
-  int M;  // |v| < 2^M (MAG_NONE: all zero)
-};
-
-// Scans the CTA footprint: the exponents of section s over planes k0-1..k1,
-// rows j0-1..j0+TY and blocks bx-1..bx+1, and the descriptors of the coarse
-// temporaries t and u over the coarse planes, rows and blocks P_l reads.
-// sm: 6 ints; ends with a CTA barrier.
-template <int DIM>
-__device__ __forceinline__ void footprint_bounds(const Geo &g, const Geo &gc, const Tile &T, const Sec &s,
-                                                 bool has_s, const Tmp &t, bool has_t, const Tmp &u, bool has_u,
-                                                 int *sm, Bounds &bs, Bounds &bt, Bounds &bu) {
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  if (tid == 0) {
-    sm[0] = sm[2] = sm[4] = GRID_NONE;
-    sm[1] = sm[3] = sm[5] = MAG_NONE;
-  }
-  __syncthreads();
-  const int klo = DIM == 3 ? T.k0 - 1 : 0, khi = DIM == 3 ? T.k1 : 0;
-  if (has_s) {
-    int G = GRID_NONE, M = MAG_NONE;
-    const int per = (TY + 2) * 3, cnt = (khi - klo + 1) * per;
-    for (int idx = tid; idx < cnt; idx += NT) {
-      const int kk = klo + idx / per, rem = idx - (idx / per) * per;
-      const int jj = T.j0 - 1 + rem / 3, bb = T.bx - 1 + rem % 3;
-      if ((unsigned)kk < (unsigned)g.nz && (unsigned)jj < (unsigned)g.n && (unsigned)bb < (unsigned)g.nbx) {
-        const int e = __ldg(s.exps + ((long long)kk * g.n + jj) * g.nbx + bb);
-        if (e != -128) {
-          G = imin(G, e - s.W + 1);
-          M = imax(M, e);
-        }
-      }
-    }
-    if (G < GRID_NONE / 2) atomicMin(sm, G);
-    if (M > MAG_NONE / 2) atomicMax(sm + 1, M);
-  }
-  if (has_t || has_u) {
-    const int cj0 = imax(0, T.cr0), cj1 = imin(gc.n - 1, T.cr0 + CR - 1);
-    const int ck0 = DIM == 3 ? imax(0, (klo - 1) >> 1) : 0;
-    const int ck1 = DIM == 3 ? imin(gc.nz - 1, khi >> 1) : 0;
-    const int cb0 = imax(0, T.cx0) >> 5, cb1 = imin(gc.n - 1, T.cx0 + CX - 1) >> 5;
-    const int nb = cb1 - cb0 + 1, nr = cj1 - cj0 + 1, np = ck1 - ck0 + 1;
-    if (nb > 0 && nr > 0 && np > 0) {
-      const int cnt = nb * nr * np;
-      for (int which = 0; which < 2; which++) {
-        if (!(which ? has_u : has_t)) continue;
-        const int *xgb = which ? u.gb : t.gb;
-        int G = GRID_NONE, M = MAG_NONE;
-        for (int idx = tid; idx < cnt; idx += NT) {
-          const int kk = ck0 + idx / (nb * nr), rem = idx % (nb * nr);
-          const int jj = cj0 + rem / nb, bb = cb0 + rem % nb;
-          const int gbv = __ldg(xgb + ((long long)kk * gc.n + jj) * gc.nbx + bb);
-          if (gbv & 0xff) {
-            G = imin(G, gb_grid(gbv));
-            M = imax(M, gb_mag(gbv));
-          }
-        }
-        if (G < GRID_NONE / 2) atomicMin(sm + 2 + 2 * which, G);
-        if (M > MAG_NONE / 2) atomicMax(sm + 3 + 2 * which, M);
-      }
-    }
-  }
-  __syncthreads();
-  bs.G = sm[0];
-  bs.M = sm[1];
-  bt.G = sm[2];
-  bt.M = sm[3];
-  bu.G = sm[4];
-  bu.M = sm[5];
-}
-
-// Operand bounds: F = s + P t on grid GF = min(G_s, G_t - 1), |F| < 2^MF.
-__device__ __forceinline__ Bounds operand_of(const Bounds &bs, const Bounds &bt) {
-  Bounds b;
-  b.G = imin(bs.G, bt.G < GRID_NONE / 2 ? bt.G - 1 : GRID_NONE);
-  const int M = imax(bs.M, bt.M);
-  b.M = M > MAG_NONE / 2 ? M + 1 : MAG_NONE;
-  return b;
-}
+#endif
 
 // ------------------------------------------------------------------ the z-march
 struct SmemTile {
@@ -884,22 +639,6 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
 }
 
 // ------------------------------------------------------------------ restriction
-// R_l = P_l^T on grid G-1: an all-even node gives 2d to its coarse node, any
-// other node gives d to each of the two coarse nodes (I -+ e_S)/2.
-template <int DIM>
-__device__ __forceinline__ void scatter_restrict(unsigned long long *acc, const Geo &gc, int I, int J, int K,
-                                                 long long d) {
-  Parents<DIM> p(I, J, K);
-  if (!p.two) {
-    atomicAdd(acc + ((long long)p.ka * gc.n + p.ja) * gc.R + p.ia, (unsigned long long)(2 * d));
-    return;
-  }
-  if (inside(gc, p.ia, p.ja, p.ka))
-    atomicAdd(acc + ((long long)p.ka * gc.n + p.ja) * gc.R + p.ia, (unsigned long long)d);
-  if (inside(gc, p.ib, p.jb, p.kb))
-    atomicAdd(acc + ((long long)p.kb * gc.n + p.jb) * gc.R + p.ib, (unsigned long long)d);
-}
-
 template <int DIM>
 struct RestrictBody {
   const RestrictArgs &a;
