@@ -269,6 +269,9 @@ def make_problem(name: str, Lmax: int, seed: int = 0) -> SeparableProblem:
         return poisson3d_fourier(Lmax, seed)
     if name == "poisson2d_fourier":
         return poisson2d_fourier(Lmax, seed)
+    if name in ("diffusion3d_grf", "diffusion2d_grf"):
+        from .diffusion import diffusion_grf
+        return diffusion_grf(3 if name.startswith("diffusion3d") else 2, Lmax, seed=seed if seed else 1)
     raise KeyError(name)
 
 

@@ -52,7 +52,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("Lmax", ctypes.c_int), ("b1", ctypes.c_int),
                 ("b2", ctypes.c_int), ("ku", ctypes.c_int), ("kr", ctypes.c_int),
                 ("N", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
-                ("omega", ctypes.c_double), ("arith", ctypes.c_int)]
+                ("omega", ctypes.c_double), ("arith", ctypes.c_int), ("coef", ctypes.c_int)]
 
 
 def lib():
@@ -93,6 +93,8 @@ def lib():
                 "cmgo_rhs": (i32, [vp, i32, vp]),
                 "cmgo_last_t": (i32, [vp, vp]),
                 "cmgo_last_w": (i32, [vp, i32, vp]),
+                "cmgo_set_coefficient": (i32, [vp, vp]),
+                "cmgo_apply_A_diffusion": (i32, [vp, i32, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -165,19 +167,40 @@ class Oracle:
 
     def __init__(self, dim: int, Lmax: int, tables: np.ndarray, scale_exp: int, *,
                  b1: int, b2: int, N: int, nu1: int, nu2: int, omega: float,
-                 ku: int = 2, kr: int = 1, arith: int = 0):
+                 ku: int = 2, kr: int = 1, arith: int = 0, coef: int = 0,
+                 kfield: Optional[np.ndarray] = None):
         self.dim, self.Lmax = dim, Lmax
-        self.params = _Params(dim, Lmax, b1, b2, ku, kr, N, nu1, nu2, omega, arith)
+        self.params = _Params(dim, Lmax, b1, b2, ku, kr, N, nu1, nu2, omega, arith, coef)
         self._tables = np.ascontiguousarray(tables, dtype=np.int32)
         assert self._tables.shape[1:] == (dim, (1 << Lmax) - 1)
         self._ctx = lib().cmgo_create(ctypes.byref(self.params), self._tables.shape[0],
                                       _p(self._tables), scale_exp)
         if not self._ctx:
             raise ValueError("cmgo_create rejected the parameters")
+        if kfield is not None:
+            self.set_coefficient(kfield)
 
     @classmethod
     def for_problem(cls, prob, **kw) -> "Oracle":
+        if getattr(prob, "coef", 0):
+            kw.setdefault("coef", 1)
+            kw.setdefault("arith", 1)
+            kw.setdefault("kfield", prob.kfield())
         return cls(prob.dim, prob.Lmax, prob.tables, prob.scale_exp, **kw)
+
+    def set_coefficient(self, k: np.ndarray):
+        """Nodal binary32 coefficient on the finest grid, boundary included."""
+        k = np.ascontiguousarray(k, dtype=np.float32)
+        n = (1 << self.Lmax) + 1
+        assert k.size == n ** self.dim
+        self._k = k
+        return self._chk(lib().cmgo_set_coefficient(self._ctx, _p(k)), "set_coefficient")
+
+    def apply_A_diffusion(self, level: int, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.zeros_like(x)
+        self._chk(lib().cmgo_apply_A_diffusion(self._ctx, level, _p(x), _p(out)), "apply_A_diffusion")
+        return out
 
     def close(self):
         if self._ctx:

@@ -362,6 +362,7 @@ struct cmgo_ctx {
   sec y[MAXL + 1];  /* correction sections y~_l */
   double *w[MAXL + 1]; /* w_l = y~_l + z_l after the up-leg on level l (exact) */
   double *t;           /* exact t_L of the last residual */
+  float *kfield;       /* diffusion: nodal k on the finest grid, boundary included */
   long long inexact;
   int status;
 };
@@ -394,6 +395,89 @@ static int Wr(const cmgo_ctx *c, int l) { return c->P.b2 == 0 ? 0 : c->P.kr * (c
 /* Table 1: u^ and t^ in fmgResidual carry (p+1)L + b1 bits */
 static int Wt(const cmgo_ctx *c) { return c->P.b1 == 0 ? 0 : c->P.ku * c->L + c->P.b1; }
 
+/* ------------------------------------------------------------------------- */
+/* diffusion -div(k grad u) (the variable-coefficient workload): on level l the */
+/* coefficient is the finest nodal field injected at stride 2^(Lmax - l); the   */
+/* flux between neighbours p, q uses the face value (k_p + k_q) / 2, so         */
+/*   (A_l u)_p = h^(d-2) sum over the 2d neighbours q of (k_p+k_q)/2 (u_p - u_q) */
+/* with u = 0 on the boundary (k = 1 gives the Poisson stencil).  The outer     */
+/* residual evaluates it in FP64 and the cycle in binary32, each in the fixed   */
+/* order below (face sums are exact in FP64; products and sums round).          */
+/* ------------------------------------------------------------------------- */
+
+static const int NBR[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+
+/* k at 1-based node (I, J, K) of level l (boundary nodes 0 and 2^l included) */
+static inline float kcoef(const cmgo_ctx *c, int l, int I, int J, int K) {
+  const int d = c->P.dim, s = 1 << (c->P.Lmax - l), N = (1 << c->P.Lmax) + 1;
+  if (d == 2) K = 0;
+  return c->kfield[((int64_t)(K * s) * N + J * s) * N + I * s];
+}
+
+/* FP64 (A_l x)_p, 0-based interior (i, j, k): acc = 0; for q in -x,+x,-y,+y,-z,+z:
+ * acc = acc + ((k_p + k_q) * 0.5) * (x_p - x_q); times h^(d-2) */
+static double A_at_diff64(const cmgo_ctx *c, const double *x, const lev *g, int i, int j, int k) {
+  const int I = i + 1, J = j + 1, K = k + 1, nn = 2 * g->dim;
+  const double kp = (double)kcoef(c, g->l, I, J, K), xp = x[idx(g, i, j, k)];
+  volatile double acc = 0.0;
+  for (int e = 0; e < nn; e++) {
+    const int Iq = I + NBR[e][0], Jq = J + NBR[e][1], Kq = K + NBR[e][2];
+    volatile double kf = ((double)kcoef(c, g->l, Iq, Jq, Kq) + kp) * 0.5;
+    volatile double du = xp - get0(x, g, Iq - 1, Jq - 1, Kq - 1);
+    volatile double pr = kf * du;
+    acc = acc + pr;
+  }
+  return acc * ldexp(1.0, -(g->dim - 2) * g->l);
+}
+
+/* FP64 diagonal of A_l at the single level-1 node */
+static double diag1_diff64(const cmgo_ctx *c) {
+  const int nn = 2 * c->P.dim;
+  const double kp = (double)kcoef(c, 1, 1, 1, 1);
+  volatile double acc = 0.0;
+  for (int e = 0; e < nn; e++) {
+    volatile double kf = ((double)kcoef(c, 1, 1 + NBR[e][0], 1 + NBR[e][1], 1 + NBR[e][2]) + kp) * 0.5;
+    acc = acc + kf;
+  }
+  return acc * ldexp(1.0, -(c->P.dim - 2));
+}
+
+/* binary32 (A_l F)_p and diagonal D_p: kf = fl(fl(k_q + k_p) * 0.5),
+ * acc = fl(acc + fl(kf * fl(F_p - F_q))), dsum = fl(dsum + kf) in the neighbour
+ * order; S = fl(acc h^(d-2)), D = fl(dsum h^(d-2)) */
+static void A_at_diff32(const cmgo_ctx *c, const float *F, const lev *g, int i, int j, int k, float *S,
+                        float *D) {
+  const int I = i + 1, J = j + 1, K = k + 1, nn = 2 * g->dim;
+  const float kp = kcoef(c, g->l, I, J, K), Fp = F[idx(g, i, j, k)];
+  volatile float acc = 0.0f, dsum = 0.0f;
+  for (int e = 0; e < nn; e++) {
+    const int Iq = I + NBR[e][0], Jq = J + NBR[e][1], Kq = K + NBR[e][2];
+    volatile float ks = kcoef(c, g->l, Iq, Jq, Kq) + kp;
+    volatile float kf = ks * 0.5f;
+    volatile float du = Fp - get0f(F, g, Iq - 1, Jq - 1, Kq - 1);
+    volatile float pr = kf * du;
+    acc = acc + pr;
+    dsum = dsum + kf;
+  }
+  const float hs = ldexpf(1.0f, -(g->dim - 2) * g->l);
+  *S = acc * hs;
+  *D = dsum * hs;
+}
+
+/* binary32 restriction (R_l d) at coarse node (Ic, Jc, Kc) in the order of R_at */
+static float R_at_f32(const float *df, const lev *gf, int Ic, int Jc, int Kc) {
+  int I = 2 * Ic, J = 2 * Jc, K = 2 * Kc;
+  int ns = gf->dim == 3 ? 7 : 3;
+  volatile float sum = 0.0f;
+  for (int s = 0; s < ns; s++) {
+    int ex = ODDSET[s][0], ey = ODDSET[s][1], ez = ODDSET[s][2];
+    sum = sum + nodef(df, gf, I - ex, J - ey, K - ez);
+    sum = sum + nodef(df, gf, I + ex, J + ey, K + ez);
+  }
+  volatile float half = sum * 0.5f;
+  return nodef(df, gf, I, J, K) + half;
+}
+
 int cmgo_width(const cmgo_ctx *c, int which, int level) {
   return which == CMGO_U ? Wu(c, level) : Wr(c, level);
 }
@@ -411,6 +495,7 @@ cmgo_ctx *cmgo_create(const cmgo_params *p, int nterms, const int32_t *tables, i
   if (!p || p->dim < 2 || p->dim > 3 || p->Lmax < 1 || p->Lmax > MAXL || p->N < 1 ||
       p->nu1 < 0 || p->nu2 < 1 || p->b1 < 0 || p->b2 < 0 || nterms < 1 || !tables)
     return NULL;
+  if (p->coef != 0 && (p->coef != 1 || p->arith != 1 || p->nu1 < 1)) return NULL;
   cmgo_ctx *c = (cmgo_ctx *)calloc(1, sizeof(cmgo_ctx));
   if (!c) return NULL;
   c->P = *p;
@@ -470,6 +555,7 @@ void cmgo_destroy(cmgo_ctx *c) {
   }
   free(c->t);
   free(c->tab);
+  free(c->kfield);
   free(c);
 }
 
@@ -477,6 +563,26 @@ int cmgo_status(const cmgo_ctx *c) { return c->status; }
 long long cmgo_inexact(const cmgo_ctx *c) { return c->inexact; }
 int cmgo_level(const cmgo_ctx *c) { return c->L; }
 int cmgo_rhs_shift(const cmgo_ctx *c) { return c->fsh; }
+
+int cmgo_set_coefficient(cmgo_ctx *c, const float *k) {
+  if (!c || !k) return CMGO_EINVAL;
+  const int64_t N = (1 << c->P.Lmax) + 1;
+  const int64_t cnt = c->P.dim == 3 ? N * N * N : N * N;
+  free(c->kfield);
+  c->kfield = (float *)malloc((size_t)cnt * sizeof(float));
+  if (!c->kfield) return CMGO_ENOMEM;
+  memcpy(c->kfield, k, (size_t)cnt * sizeof(float));
+  return CMGO_OK;
+}
+
+int cmgo_apply_A_diffusion(const cmgo_ctx *c, int level, const double *x, double *out) {
+  if (!c || !c->kfield || level < 1 || level > c->P.Lmax) return CMGO_EINVAL;
+  lev g = mklev(c->P.dim, level);
+  for (int k = 0; k < g.nz; k++)
+    for (int j = 0; j < g.n; j++)
+      for (int i = 0; i < g.n; i++) out[idx(&g, i, j, k)] = A_at_diff64(c, x, &g, i, j, k);
+  return CMGO_OK;
+}
 
 static int setst(cmgo_ctx *c, int st) {
   if (st != CMGO_OK && c->status == CMGO_OK) c->status = st;
@@ -533,7 +639,9 @@ int cmgo_start(cmgo_ctx *c) {
   c->inexact = 0;
   c->status = CMGO_OK;
   lev g = mklev(c->P.dim, 1);
-  double x = f_at(c, 1, 1, 1, 1) / A1(c->P.dim); /* coarse-grid solve */
+  if (c->P.coef && !c->kfield) return setst(c, CMGO_EINVAL);
+  /* coarse-grid solve; with diffusion a rounded FP64 division by the diagonal */
+  double x = c->P.coef ? f_at(c, 1, 1, 1, 1) / diag1_diff64(c) : f_at(c, 1, 1, 1, 1) / A1(c->P.dim);
   return setst(c, round_dense(&g, &x, Wu(c, 1), &c->u[1]));
 }
 
@@ -597,15 +705,28 @@ int cmgo_residual(cmgo_ctx *c) {
     free(Au);
     return setst(c, CMGO_ENOMEM);
   }
-  apply_A(&g, uh, Au, &cnt);
   long long cc = 0;
+  if (c->P.coef) {
+    /* diffusion: the outer residual in FP64, t = fl(f - A u^) with A in the
+     * order of A_at_diff64 (u^ itself is exact) */
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < g.nz; k++)
+      for (int j = 0; j < g.n; j++)
+        for (int i = 0; i < g.n; i++) {
+          int64_t p = idx(&g, i, j, k);
+          volatile double a = A_at_diff64(c, uh, &g, i, j, k);
+          c->t[p] = f_at(c, L, i + 1, j + 1, k + 1) - a;
+        }
+  } else {
+    apply_A(&g, uh, Au, &cnt);
 #pragma omp parallel for collapse(2) reduction(+ : cc) schedule(static)
-  for (int k = 0; k < g.nz; k++)
-    for (int j = 0; j < g.n; j++)
-      for (int i = 0; i < g.n; i++) {
-        int64_t p = idx(&g, i, j, k);
-        c->t[p] = xsub(f_at(c, L, i + 1, j + 1, k + 1), Au[p], &cc);
-      }
+    for (int k = 0; k < g.nz; k++)
+      for (int j = 0; j < g.n; j++)
+        for (int i = 0; i < g.n; i++) {
+          int64_t p = idx(&g, i, j, k);
+          c->t[p] = xsub(f_at(c, L, i + 1, j + 1, k + 1), Au[p], &cc);
+        }
+  }
   cnt += cc;
   free(uh);
   free(Au);
@@ -700,14 +821,23 @@ static int jacobi_f32(cmgo_ctx *c, int l, const float *z, long long *cnt) {
     if (z) f = f + z[p];
     F[p] = f;
   }
+  const float omega_f = (float)c->P.omega;
 #pragma omp parallel for collapse(2) reduction(| : bad) schedule(static)
   for (int k = 0; k < g.nz; k++)
     for (int j = 0; j < g.n; j++)
       for (int i = 0; i < g.n; i++) {
         int64_t p = idx(&g, i, j, k);
-        volatile float S = A_at_f32(F, &g, i, j, k);
+        volatile float S, cp = cl;
+        if (c->P.coef) {  /* diffusion: the Jacobi factor omega / D_p per node */
+          float Sd, Dd;
+          A_at_diff32(c, F, &g, i, j, k, &Sd, &Dd);
+          S = Sd;
+          cp = omega_f / Dd;
+        } else {
+          S = A_at_f32(F, &g, i, j, k);
+        }
         volatile float res = to_f32(c->rc[l].v[p], &bad) - S;
-        volatile float cres = cl * res;
+        volatile float cres = cp * res;
         volatile float y2 = yf[p] + cres;
         yn[p] = (double)y2;
       }
@@ -751,11 +881,35 @@ int cmgo_down(cmgo_ctx *c, int l) {
       for (int j = 0; j < g.n; j++)
         for (int i = 0; i < g.n; i++) {
           int64_t p = idx(&g, i, j, k);
-          volatile float S = A_at_f32(yf, &g, i, j, k);
+          volatile float S;
+          if (c->P.coef) {
+            float Sd, Dd;
+            A_at_diff32(c, yf, &g, i, j, k, &Sd, &Dd);
+            S = Sd;
+          } else {
+            S = A_at_f32(yf, &g, i, j, k);
+          }
           volatile float d = to_f32(c->rc[l].v[p], &bad) - S;
           dd[p] = (double)d;
         }
-    restrict_(&g, &gc, dd, rcc, &cnt);
+    if (c->P.coef) {
+      /* diffusion: the products k_f (F_p - F_q) leave d on no common grid, so R d
+       * is formed in binary32 too, in the order of R_at */
+      float *df = (float *)malloc((size_t)g.np * sizeof(float));
+      if (!df) {
+        free(yf);
+        free(dd);
+        free(rcc);
+        return setst(c, CMGO_ENOMEM);
+      }
+      for (int64_t p = 0; p < g.np; p++) df[p] = (float)dd[p];
+      for (int k = 0; k < gc.nz; k++)
+        for (int j = 0; j < gc.n; j++)
+          for (int i = 0; i < gc.n; i++) rcc[idx(&gc, i, j, k)] = (double)R_at_f32(df, &g, i + 1, j + 1, k + 1);
+      free(df);
+    } else {
+      restrict_(&g, &gc, dd, rcc, &cnt);
+    }
     st = bad ? CMGO_ERANGE : round_dense(&gc, rcc, Wr(c, l - 1), &c->rc[l - 1]);
     free(yf);
     free(dd);
@@ -793,7 +947,7 @@ int cmgo_down(cmgo_ctx *c, int l) {
 int cmgo_coarse(cmgo_ctx *c) {
   lev g = mklev(c->P.dim, 1);
   if (c->L == 1) sec_copy(&c->rc[1], &c->r[1], &g);
-  double x = c->rc[1].v[0] / A1(c->P.dim);
+  double x = c->P.coef ? c->rc[1].v[0] / diag1_diff64(c) : c->rc[1].v[0] / A1(c->P.dim);
   int st = round_dense(&g, &x, Wr(c, 1), &c->y[1]);
   c->w[1][0] = c->y[1].v[0];
   return setst(c, st);

@@ -59,6 +59,9 @@ typedef struct {
   double omega; /* Jacobi weight */
   int arith;    /* 0: exact V-cycle; 1: FP32 V-cycle inside exact iterative
                    refinement (see cmg_oracle.c, "FP32 V-cycle") */
+  int coef;     /* 0: Poisson; 1: diffusion -div(k grad u) with a nodal binary32
+                   coefficient field (cmgo_set_coefficient); needs arith = 1 and
+                   nu1 >= 1 (see cmg_oracle.c, "diffusion") */
 } cmgo_params;
 
 /* Section selectors. */
@@ -85,6 +88,13 @@ long long cmgo_inexact(const cmgo_ctx *c);
 int cmgo_level(const cmgo_ctx *c);
 int cmgo_rhs_shift(const cmgo_ctx *c);
 int cmgo_width(const cmgo_ctx *c, int which, int level);
+
+/* Diffusion: the nodal coefficient k at every node of the finest grid,
+ * boundary included: (2^Lmax + 1)^dim binary32 values, x fastest.  Copied. */
+int cmgo_set_coefficient(cmgo_ctx *c, const float *k);
+/* (A_level x) of the diffusion operator with the FP64 order of the outer
+ * residual (dense interior arrays, as cmgo_apply_A) */
+int cmgo_apply_A_diffusion(const cmgo_ctx *c, int level, const double *x, double *out);
 
 int cmgo_start(cmgo_ctx *c);        /* L = 1: u~_1 = round(f_1 / A_1) */
 int cmgo_next_level(cmgo_ctx *c);   /* L += 1: zero new section, widen the others */
