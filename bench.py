@@ -32,6 +32,12 @@ WORKLOADS = {
                        "RHS matrix-free from u=sin(pi x)sin(pi y)sin(pi z)(1+x^2yz)"),
     "poisson3d_513": ("poisson3d_manufactured", 9,
                       "3-D Poisson 513^3 grid (511^3 = 1.33e8 DoF), same RHS as poisson3d_2049"),
+    "diffusion3d_1025": ("diffusion3d_grf", 10,
+                         "3-D -div(k grad u) = 1, 1025^3 grid (1023^3 = 1.07e9 DoF), k = exp(g), g a seeded "
+                         "Gaussian random field (sigma 1, correlation length 0.1, 256 Fourier features), "
+                         "binary32 cycle inside FP64 iterative refinement"),
+    "diffusion3d_257": ("diffusion3d_grf", 8,
+                        "3-D -div(k grad u) = 1, 257^3 grid, k = exp(g) as diffusion3d_1025"),
     "poisson3d_257": ("poisson3d_fourier", 8,
                       "3-D Poisson 257^3 grid (255^3 DoF), RHS = 8 seeded Fourier modes"),
     "poisson2d_257": ("poisson2d_manufactured", 8,
@@ -138,6 +144,8 @@ def oracle_fmg_rate(prob_name: str, L: int, cfg, max_seconds: float = 30.0):
 def pick_sample_level(prob_name: str, Lmax: int, dim: int) -> int:
     # bounded oracle sample: a few to about 10 s of host work per solve on the
     # GPU machine's cores (3-D L = 9 is 1.3e8 DoF)
+    if prob_name.startswith("diffusion"):  # the coefficient field is drawn on the host here
+        return min(Lmax, 7 if dim == 3 else 10)
     return min(Lmax, 9 if dim == 3 else 12)
 
 
@@ -199,9 +207,14 @@ def run_gpu(args, wl):
     prob_name, Lmax, desc = WORKLOADS[wl]
     prob = cmg_problems.make_problem(prob_name, Lmax, seed=rank)
     cfg = cmg.config_for(prob_name, Lmax, arith=1 if args.arith == "fp32" else 0)
+    diffusion = bool(getattr(prob, "coef", 0))
     stream = torch.cuda.Stream()
     solver = cmg.Solver(cfg, stream=stream, timing=True)
     solver.set_rhs(prob.tables, prob.scale_exp)
+    if diffusion:  # the seeded coefficient field, drawn on the device (input data)
+        kfield = prob.kfield(device="cuda").reshape(-1).contiguous()
+        torch.cuda.synchronize()
+        solver.set_coefficient(kfield)
 
     def barrier():
         if dist is not None:
@@ -291,16 +304,37 @@ def run_gpu(args, wl):
     planes = [n // 4, n // 2, (3 * n) // 4] if cfg.dim == 3 else [0]
     errs, norms = [], []
     x = (np.arange(n) + 1.0) * h
-    for z in planes:
-        u = solver.decode_solution(z, 1).cpu().numpy()[0]
-        Y, X = np.meshgrid(x, x, indexing="ij")
-        ue = prob.exact_u(X, Y, (z + 1) * h) if cfg.dim == 3 else prob.exact_u(X, Y)
-        errs.append(float(np.max(np.abs(u - ue))))
-        norms.append(float(np.max(np.abs(ue))))
-    nodal_rel = max(errs) / max(norms)
+    nodal_rel = None
+    if not diffusion:
+        for z in planes:
+            u = solver.decode_solution(z, 1).cpu().numpy()[0]
+            Y, X = np.meshgrid(x, x, indexing="ij")
+            ue = prob.exact_u(X, Y, (z + 1) * h) if cfg.dim == 3 else prob.exact_u(X, Y)
+            errs.append(float(np.max(np.abs(u - ue))))
+            norms.append(float(np.max(np.abs(ue))))
+        nodal_rel = max(errs) / max(norms)
+    # diffusion (no closed form): the solution against a reference solve of the
+    # same discrete problem with wider widths and more IR iterations, on sampled planes
+    diffusion_vs_reference = None
+    if diffusion:
+        import dataclasses
+        rcfg = dataclasses.replace(cfg, b1=14, b2=10, N_ir=16)
+        ref = cmg.Solver(rcfg, stream=stream)
+        ref.set_rhs(prob.tables, prob.scale_exp)
+        ref.set_coefficient(kfield)
+        ref.fmg_solve()
+        dmax, umax = 0.0, 0.0
+        for z in planes:
+            a = solver.decode_solution(z, 1).cpu().numpy()[0]
+            b = ref.decode_solution(z, 1).cpu().numpy()[0]
+            dmax = max(dmax, float(np.max(np.abs(a - b))))
+            umax = max(umax, float(np.max(np.abs(b))))
+        diffusion_vs_reference = {"max_rel_diff_sampled": dmax / umax,
+                                  "reference": "b1=14, b2=10, N_ir=16, same binary32 cycle"}
+        del ref
     # the FP32 cycle: its solution against the exact cycle's on the same planes
     fp32_vs_exact = None
-    if cfg.arith == 1:
+    if cfg.arith == 1 and not diffusion:
         cfg64 = cmg.config_for(prob_name, Lmax)
         ref = cmg.Solver(cfg64, stream=stream)
         ref.set_rhs(prob.tables, prob.scale_exp)
@@ -348,6 +382,7 @@ def run_gpu(args, wl):
         "whole_solve_hbm_frac": whole_frac,
         "nodal_rel_err_sampled": nodal_rel,
         "fp32_vs_exact": fp32_vs_exact,
+        "diffusion_vs_reference": diffusion_vs_reference,
         "roofline": roofline,
         "kernels_last_step": kernels,
         "storage_model": storage,

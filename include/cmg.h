@@ -56,6 +56,7 @@ typedef enum {
  * Intermediate arithmetic is exact (fixed-point integers on the GPU); values are
  * rounded only where they are stored, as the paper's rounding rules prescribe. */
 enum { CMG_ARITH_EXACT = 0, CMG_ARITH_FP32 = 1 };
+enum { CMG_COEF_POISSON = 0, CMG_COEF_DIFFUSION = 1 };
 
 typedef struct {
   int dim;             /* 2 or 3 */
@@ -75,6 +76,11 @@ typedef struct {
                           in a fixed order, inside the exact iterative refinement
                           (outer residual, level-1 solve and u~ correction exact);
                           needs k_r (L_max - 1) + b2 + bitlen(Jacobi numerator) <= 24 */
+  int coef;            /* CMG_COEF_POISSON (0): -Lap u = f; CMG_COEF_DIFFUSION (1):
+                          -div(k grad u) = f with the nodal coefficient set by
+                          cmg_set_coefficient; needs arith = CMG_ARITH_FP32 and
+                          nu1 >= 1 (the outer residual and level-1 solve in FP64,
+                          the cycle in binary32, each in a fixed order) */
 } cmg_params;
 
 /* Per-solve report filled by cmg_fmg_solve. */
@@ -143,6 +149,13 @@ cmg_status cmg_set_timing(cmg_ctx *ctx, int enable); /* per-kernel CUDA events *
  * sum_t prod_a max|T[t][a]|.  |T| must be <= 2^30 and nterms <= 64. */
 cmg_status cmg_set_rhs_separable(cmg_ctx *ctx, int nterms, const int32_t *tables_host,
                                  int scale_exp);
+
+/* Diffusion: the nodal coefficient k on the finest grid, boundary nodes
+ * included, (2^L_max + 1)^dim binary32 values, x fastest, in device memory the
+ * caller keeps alive and unchanged while the context uses it (borrowed; n must
+ * equal that count).  Level l reads it at stride 2^(L_max - l) (injection); the
+ * flux between neighbours uses the face value (k_p + k_q) / 2. */
+cmg_status cmg_set_coefficient(cmg_ctx *ctx, const float *k_dev, int64_t n);
 
 /* Algorithm 3 end to end (coarse solve, then L = 2..L_max with N_ir IR
  * iterations each).  Synchronises; fills *report when non-NULL. */

@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
                 ("b2", ctypes.c_int), ("k_u", ctypes.c_int), ("k_r", ctypes.c_int),
                 ("N_ir", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega_num", ctypes.c_int), ("omega_log2den", ctypes.c_int),
-                ("arith", ctypes.c_int)]
+                ("arith", ctypes.c_int), ("coef", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -92,6 +92,7 @@ _SIGS = {
     "cmg_decode_solution": (_i32, [_vp, _i64, _i64, _vp]),
     "cmg_state_save": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
     "cmg_state_load": (_i32, [_vp, _vp, ctypes.c_size_t]),
+    "cmg_set_coefficient": (_i32, [_vp, _vp, _i64]),
     "cmg_storage_model": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32, ctypes.POINTER(Storage)]),
     "cmg_kernel_stats": (_i32, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
@@ -170,7 +171,7 @@ def decode_raw(words_ptr: int, exps_ptr: int, n: int, W: int, x_ptr: int, stream
 # ---------------------------------------------------------------- solver
 def to_params(cfg: SolverConfig) -> Params:
     return Params(cfg.dim, cfg.L_max, cfg.b1, cfg.b2, cfg.k_u, cfg.k_r, cfg.N_ir,
-                  cfg.nu1, cfg.nu2, cfg.omega_num, cfg.omega_log2den, cfg.arith)
+                  cfg.nu1, cfg.nu2, cfg.omega_num, cfg.omega_log2den, cfg.arith, cfg.coef)
 
 
 def params_check(cfg: SolverConfig) -> int:
@@ -235,6 +236,14 @@ class Solver:
                 out["%s_%s" % (name, "top" if top else "lower")] = {
                     "ms": ms.value, "launches": n.value, "bytes": by.value}
         return out
+
+    def set_coefficient(self, k):
+        """Diffusion: the nodal binary32 coefficient (CUDA tensor, boundary included,
+        (2^L_max + 1)^dim values).  The solver borrows it; it is kept referenced here."""
+        import torch
+        assert k.is_cuda and k.dtype == torch.float32 and k.is_contiguous()
+        self._kfield = k
+        self._chk(_lib.cmg_set_coefficient(self._h, k.data_ptr(), k.numel()), "cmg_set_coefficient")
 
     def start(self):
         self._chk(_lib.cmg_start(self._h), "cmg_start")

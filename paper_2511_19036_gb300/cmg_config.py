@@ -18,6 +18,7 @@ class SolverConfig:
     k_u: int = 2
     k_r: int = 1
     arith: int = 0  # 0: exact V-cycle; 1: binary32 V-cycle inside exact iterative refinement
+    coef: int = 0   # 0: Poisson; 1: diffusion -div(k grad u) (needs arith = 1)
 
     @property
     def omega(self) -> float:
@@ -27,7 +28,12 @@ class SolverConfig:
 def config_for(name: str, L_max: int, arith: int = 0) -> SolverConfig:
     """Widths and cycle of the standard workloads (2-D: Table 2 Poisson 2D p=1;
     3-D: found by the Sec. 7.1 search on the manufactured 3-D problem)."""
-    dim = 2 if name.startswith("poisson2d") else 3
+    dim = 2 if ("2d" in name) else 3
+    if name.startswith("diffusion"):
+        # rough coefficient (k over e^-3..e^3): Jacobi V(2,2) contracts by about
+        # 1/2 per iteration, so more IR iterations than for Poisson
+        return SolverConfig(dim=dim, L_max=L_max, b1=6, b2=4, N_ir=8, nu1=2, nu2=2, omega_num=3,
+                            omega_log2den=2, arith=1, coef=1)
     if dim == 2:
         return SolverConfig(dim=2, L_max=L_max, b1=4, b2=4, N_ir=3, nu1=2, nu2=2, omega_num=3, omega_log2den=2,
                             arith=arith)

@@ -70,6 +70,8 @@ struct cmg_ctx {
   int c_num2 = 0, c_exp2 = 0;  // omega / (2d) = c_num2 2^c_exp2 (level-free part)
   std::string msg;
   bool timing = false;
+  const float *kfield = nullptr;  // diffusion: borrowed nodal coefficient
+  float *dbuf = nullptr;          // diffusion: d = rc - A y~ of the finest level in binary32
   KStat stats[CMG_KIND_COUNT][2];  // per kernel kind; [1] = launches on level L_max
   long long launches = 0;
   double alg_bytes = 0;
@@ -209,6 +211,8 @@ extern "C" cmg_status cmg_params_check(const cmg_params *p) {
   if (p->nu1 == 0 && p->k_u * p->L_max + p->b1 > 32) return CMG_ERANGE;
   if (p->omega_num <= 0 || p->omega_log2den < 0 || p->omega_log2den > 30) return CMG_EINVAL;
   if (p->arith != CMG_ARITH_EXACT && p->arith != CMG_ARITH_FP32) return CMG_EINVAL;
+  if (p->coef != CMG_COEF_POISSON && p->coef != CMG_COEF_DIFFUSION) return CMG_EINVAL;
+  if (p->coef == CMG_COEF_DIFFUSION && (p->arith != CMG_ARITH_FP32 || p->nu1 < 1)) return CMG_EINVAL;
   if (p->dim == 3 && p->omega_num % 3 != 0) return CMG_EINVAL;  // omega/6 must be dyadic
   // keep the Jacobi numerator small (it widens the exact integers by its bit length)
   int num = p->dim == 3 ? p->omega_num / 3 : p->omega_num;
@@ -261,6 +265,7 @@ extern "C" void cmg_destroy(cmg_ctx *ctx) {
     stat_reset(ctx->stats[k][0]);
     stat_reset(ctx->stats[k][1]);
   }
+  cudaFree(ctx->dbuf);
   cudaFree(ctx->meta_pool);
   cudaFree(ctx->err);
   cudaFree(ctx->tables);
@@ -344,6 +349,20 @@ extern "C" int cmg_level(const cmg_ctx *ctx) { return ctx ? ctx->L : -1; }
 extern "C" int64_t cmg_section_blocks(int dim, int level) {
   if ((dim != 2 && dim != 3) || level < 1 || level > MAXL) return -1;
   return make_geo(dim, level).nblocks;
+}
+
+// ---------------------------------------------------------------- coefficient
+extern "C" cmg_status cmg_set_coefficient(cmg_ctx *ctx, const float *k_dev, int64_t n) {
+  if (!ctx || !k_dev) return CMG_EINVAL;
+  if (ctx->P.coef != CMG_COEF_DIFFUSION) return fail(ctx, CMG_EINVAL, "coefficient on a Poisson context");
+  const long long N = (1ll << ctx->P.L_max) + 1;
+  if (n != (ctx->P.dim == 3 ? N * N * N : N * N)) return fail(ctx, CMG_EINVAL, "coefficient size");
+  ctx->kfield = k_dev;
+  if (!ctx->dbuf) {
+    const Geo g = make_geo(ctx->P.dim, ctx->P.L_max);
+    CU(cudaMalloc(&ctx->dbuf, (size_t)g.nz * g.n * g.R * sizeof(float)));
+  }
+  return CMG_OK;
 }
 
 // ---------------------------------------------------------------- right-hand side
@@ -472,6 +491,13 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
   cmg_status s = fresh_meta(ctx, v.r);
   if (s) return s;
   a.r_out = sec_of(v.r);
+  const bool diff = ctx->P.coef == CMG_COEF_DIFFUSION;
+  if (diff) {
+    if (!ctx->kfield) return fail(ctx, CMG_EINVAL, "diffusion without a coefficient (cmg_set_coefficient)");
+    first_sweep = false;  // the first sweep runs as a sweep with per-node factors
+    a.kfield = ctx->kfield;
+    a.kN = (1 << ctx->P.L_max) + 1;
+  }
   a.first_sweep = first_sweep;
   jacobi_factor(ctx, L, a.c_num, a.c_exp, a.cbits);
   if (first_sweep) {
@@ -495,7 +521,8 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
   double bytes = sec_bytes(v.g, v.u.W) + (L > 1 ? tmp_bytes(a.gc) : 0) + sec_bytes(v.g, v.r.W) +
                  (first_sweep ? sec_bytes(v.g, v.r.W) : 0) + (chain ? sec_bytes(v.g, Wt) : 0);
   ev_begin(ctx, kstat(ctx, CMG_KIND_RESIDUAL, L));
-  launch_residual(d, a, ctx->st);
+  if (diff) launch_residual_diffusion(d, a, ctx->st);
+  else launch_residual(d, a, ctx->st);
   ev_end(ctx, kstat(ctx, CMG_KIND_RESIDUAL, L), bytes);
   if ((s = launched(ctx, bytes))) return s;
   if (chain) {  // t^_l = round(R t^_(l+1)), r_l = round(t^_l) (Algorithm 2)
@@ -576,6 +603,12 @@ static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
     if (o.has_z) a.wc_f = (const float *)LV(ctx, l - 1).w;
     if (o.write_w) a.w_out_f = (float *)v.w;
   }
+  if (ctx->P.coef == CMG_COEF_DIFFUSION) {
+    a.kfield = ctx->kfield;
+    a.kN = (1 << ctx->P.L_max) + 1;
+    a.kstride = 1 << (ctx->P.L_max - l);
+    a.omega = (float)ctx->P.omega_num / (float)(1 << ctx->P.omega_log2den);
+  }
   if (l > 1) a.uhc = tmp_of(LV(ctx, l - 1).uh, LV(ctx, l - 1).uhg, nullptr);
   if (o.write_w) a.w_out = tmp_of(v.w, v.wg, nullptr);
   if (o.write_uh) a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
@@ -614,6 +647,29 @@ static cmg_status do_restrict(cmg_ctx *ctx, int l, bool first_sweep_below) {
   }
   a.acc = tmp_of(c.acc, nullptr, c.accmeta);
   a.err = ctx->err;
+  if (ctx->P.coef == CMG_COEF_DIFFUSION) {
+    // d = fl(rc - A y~) in binary32 on level l, then rc_(l-1) = round(R d) in R's order
+    a.d_out = ctx->dbuf;
+    a.kfield = ctx->kfield;
+    a.kN = (1 << ctx->P.L_max) + 1;
+    a.kstride = 1 << (ctx->P.L_max - l);
+    const double bytes = sec_bytes(v.g, a.y.W) + sec_bytes(v.g, a.rc.W) + 8.0 * v.g.nz * v.g.n * v.g.n;
+    ev_begin(ctx, kstat(ctx, CMG_KIND_RESTRICT, l));
+    launch_dvec_diffusion(d, a, ctx->st);
+    GatherArgs ga{};
+    ga.g = v.g;
+    ga.gc = c.g;
+    ga.d = ctx->dbuf;
+    c.rc.W = Wr(ctx, l - 1, L);
+    cmg_status s2 = fresh_meta(ctx, c.rc);
+    if (s2) return s2;
+    ga.rc_out = sec_of(c.rc);
+    ga.err = ctx->err;
+    launch_gather_restrict_f32(d, ga, ctx->st);
+    ev_end(ctx, kstat(ctx, CMG_KIND_RESTRICT, l), bytes + sec_bytes(c.g, c.rc.W));
+    LV(ctx, l - 1).y_zero = true;
+    return launched(ctx, bytes + sec_bytes(c.g, c.rc.W));
+  }
   ev_begin(ctx, kstat(ctx, CMG_KIND_RESTRICT, l));
   if (ctx->P.arith == CMG_ARITH_FP32) launch_restrict_f32(d, a, ctx->st);
   else launch_restrict(d, a, ctx->st);
@@ -678,6 +734,12 @@ static cmg_status do_coarse(cmg_ctx *ctx, bool start, bool corr) {
     a.w_out = tmp_of(v.w, v.wg, nullptr);
     if (ctx->P.arith == CMG_ARITH_FP32) a.w_out_f = (float *)v.w;
     if (corr) a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
+  }
+  if (ctx->P.coef == CMG_COEF_DIFFUSION) {
+    if (!ctx->kfield) return fail(ctx, CMG_EINVAL, "diffusion without a coefficient (cmg_set_coefficient)");
+    a.kfield = ctx->kfield;
+    a.kN = (1 << ctx->P.L_max) + 1;
+    a.kstride = 1 << (ctx->P.L_max - 1);
   }
   ev_begin(ctx, kstat(ctx, CMG_KIND_COARSE, 1));
   launch_coarse(a, ctx->st);
@@ -824,11 +886,13 @@ static cmg_status ir_fused(cmg_ctx *ctx, bool need_uh_top) {
       v.y_zero = true;
       continue;
     }
-    for (int k = 1; k < nu1; k++) {
+    const bool diff = ctx->P.coef == CMG_COEF_DIFFUSION;  // first sweeps not fused
+    if (diff) v.y_zero = true;
+    for (int k = diff ? 0 : 1; k < nu1; k++) {
       SweepOpts o;
       if ((s = do_sweep(ctx, l, o))) return s;
     }
-    if ((s = do_restrict(ctx, l, l - 1 >= 2))) return s;
+    if ((s = do_restrict(ctx, l, !diff && l - 1 >= 2))) return s;
   }
   if ((s = do_coarse(ctx, false, true))) return s;
   for (int l = 2; l <= L; l++) {

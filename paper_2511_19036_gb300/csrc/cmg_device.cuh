@@ -272,6 +272,34 @@ __device__ __forceinline__ int encode_block(long long v, int G, int W, int &e, i
   return (int)q;
 }
 
+// Warp-collective BFP rounding of one block of FP64 values x (padding lanes
+// pass 0), as the oracle rounds doubles: e = the smallest integer with
+// max|x| < 2^e, q = RNE(x 2^(W-1-e)) (the scaling is exact), and a carry into
+// 2^(W-1) raises e by one and re-rounds.  A subnormal block maximum or an
+// exponent outside [-127, 127] sets an error flag.
+__device__ __forceinline__ int encode_block_f64(double x, int W, int &e, int *err) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  const unsigned emx = __reduce_max_sync(0xffffffffu, (unsigned)(bits >> 52));
+  if (emx == 0) {
+    if (__any_sync(0xffffffffu, bits != 0ull) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_RANGE);
+    e = -128;
+    return 0;
+  }
+  e = (int)emx - 1022;  // max|x| in [2^(e-1), 2^e)
+  if (e > 127 || e < -127) {
+    if ((threadIdx.x & 31) == 0) atomicOr(err, ERR_EXP);
+    e = imax(-127, imin(127, e));
+  }
+  const double scale = __longlong_as_double((long long)(W - 1 - e + 1023) << 52);
+  long long q = __double2ll_rn(__dmul_rn(x, scale));
+  const long long lim = 1ll << (W - 1);
+  if (__any_sync(0xffffffffu, q == lim || q == -lim)) {
+    e += 1;
+    q = __double2ll_rn(__dmul_rn(x, __dmul_rn(scale, 0.5)));
+  }
+  return (int)q;
+}
+
 __device__ __forceinline__ long long rounded_value(long long v, int q, int s) {
   return s > 0 ? shl((long long)q, s) : v;
 }

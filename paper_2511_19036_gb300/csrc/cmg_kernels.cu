@@ -170,8 +170,34 @@ __global__ void k_coarse(CoarseArgs a) {
   int div = dim == 2 ? 1 : 3;
   if (dim == 2) G -= 2;
   Sec out = a.mode_start ? a.u_out : a.y_out;
-  if (lane == 0) q = encode_rational(N, G, div, out.W, e);
-  e = __shfl_sync(0xffffffffu, e, 0);
+  if (a.kfield) {
+    // diffusion: x = num / D_1 in FP64 with D_1 = h^(d-2) sum over the
+    // neighbours -x,+x,-y,+y,-z,+z of (k_q + k_p) * 0.5, then rounded as the
+    // oracle rounds doubles
+    double x = 0.0;
+    if (lane == 0) {
+      auto kat = [&](int I, int J, int K) -> double {
+        return (double)__ldg(a.kfield + ((long long)(dim == 3 ? K * a.kstride : 0) * a.kN + J * a.kstride) * a.kN +
+                             I * a.kstride);
+      };
+      const double kp = kat(1, 1, 1);
+      double acc = 0.0;
+      for (int e6 = 0; e6 < 2 * dim; e6++) {
+        const int Iq = 1 + (e6 == 0 ? -1 : e6 == 1 ? 1 : 0), Jq = 1 + (e6 == 2 ? -1 : e6 == 3 ? 1 : 0);
+        const int Kq = 1 + (e6 == 4 ? -1 : e6 == 5 ? 1 : 0);
+        acc = __dadd_rn(acc, __dmul_rn(__dadd_rn(kat(Iq, Jq, Kq), kp), 0.5));
+      }
+      const double D = __dmul_rn(acc, dim == 3 ? 0.5 : 1.0);
+      const int Gn = a.mode_start ? a.Gf1 : G + (dim == 2 ? 2 : 0);  // grid of N as read
+      const double num = __dmul_rn((double)(long long)N, __longlong_as_double((long long)(Gn + 1023) << 52));
+      x = __ddiv_rn(num, D);
+    }
+    q = encode_block_f64(x, out.W, e, a.err);
+    if (lane != 0) q = 0;
+  } else {
+    if (lane == 0) q = encode_rational(N, G, div, out.W, e);
+    e = __shfl_sync(0xffffffffu, e, 0);
+  }
   if ((e > 127 || e < -127) && e != -128 && lane == 0) atomicOr(a.err, ERR_EXP);
   pack_block(lane == 0 ? q : 0, out.W, pk, out.words);
   if (lane == 0) {

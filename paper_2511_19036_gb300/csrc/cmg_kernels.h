@@ -23,6 +23,9 @@ struct SweepArgs {
   int c_num, c_exp, cbits;  // Jacobi factor c_l = c_num 2^c_exp, cbits = bitlen(c_num)
   const float *wc_f;   // FP32 cycle: w_(l-1) in binary32 (padded level layout)
   float *w_out_f;      // FP32 cycle: w_l in binary32
+  const float *kfield; // diffusion (FP32 cycle): nodal k, boundary included
+  int kN, kstride;     // 2^Lmax + 1, and the level's stride 2^(Lmax - l) in it
+  float omega;         // diffusion: Jacobi weight (factor omega / D_p per node)
   int *err;
 };
 
@@ -41,6 +44,8 @@ struct ResidArgs {
   int write_t;         // also store t^_L at the width of Table 1 (no pre-smoothing)
   Sec t_out;
   int c_num, c_exp, cbits;
+  const float *kfield;  // diffusion: nodal k on the finest grid, boundary included
+  int kN;               // 2^Lmax + 1 (the field is kN^dim, x fastest)
   int *err;
 };
 
@@ -49,6 +54,17 @@ struct RestrictArgs {
   int has_y;           // d = rc - A y~ (else d = rc)
   Sec y, rc;
   Tmp acc;             // exact R_l d on one global grid
+  float *d_out;        // diffusion: d = fl(rc - A y~) in binary32 (padded level layout)
+  const float *kfield; // diffusion: nodal k, boundary included
+  int kN, kstride;
+  int *err;
+};
+
+// diffusion: rc_(l-1) = round(R_l d) with R_l d in binary32 in the fixed order
+struct GatherArgs {
+  Geo g, gc;           // fine level l, coarse level l - 1
+  const float *d;      // d on level l (padded layout)
+  Sec rc_out;
   int *err;
 };
 
@@ -73,6 +89,8 @@ struct CoarseArgs {
   int corr;            // fused u~_1 += y~_1 (cycle mode)
   Tmp w_out, uh_out;
   float *w_out_f;      // FP32 cycle: w_1 = y~_1 in binary32 (else w_out)
+  const float *kfield; // diffusion: the level-1 diagonal from k (FP64 division)
+  int kN, kstride;
   int *err;
 };
 
@@ -117,8 +135,11 @@ struct CodecArgs {
 void launch_sweep(int dim, const SweepArgs &a, cudaStream_t st);
 void launch_residual(int dim, const ResidArgs &a, cudaStream_t st);
 void launch_restrict(int dim, const RestrictArgs &a, cudaStream_t st);
+void launch_residual_diffusion(int dim, const ResidArgs &a, cudaStream_t st);
 void launch_sweep_f32(int dim, const SweepArgs &a, cudaStream_t st);
 void launch_restrict_f32(int dim, const RestrictArgs &a, cudaStream_t st);
+void launch_dvec_diffusion(int dim, const RestrictArgs &a, cudaStream_t st);
+void launch_gather_restrict_f32(int dim, const GatherArgs &a, cudaStream_t st);
 void launch_acc_encode(int dim, const AccArgs &a, cudaStream_t st);
 void launch_coarse(const CoarseArgs &a, cudaStream_t st);
 void launch_repack(const RepackArgs &a, cudaStream_t st);

@@ -69,7 +69,9 @@ struct MarchIn {
 // the next plane) and body.out(k, S, s0, F0, Pu): S = (2d) F - sum of the 2d
 // neighbours at the thread's node (grid GF), s0 its section part, F0 its
 // operand, Pu the value of P_l u at the node (grid G1u - 1).  Every thread of
-// the CTA calls it.
+// the CTA calls it.  A body with kRaw = true gets body.out_raw(k, Pc, Fm, F0,
+// Fp, s0) instead: Pc points at the node in the plane buffer (neighbours
+// Pc[-1], Pc[+1], Pc[-PW], Pc[+PW]), Fm / Fp are the z-neighbours.
 template <int DIM, class Body>
 __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T, const MarchIn &in, SmemTile &sm,
                                       Body &body) {
@@ -132,9 +134,13 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
     if (has_h) sm.Fs[0][hal.sm] = F_at(hal, h0, 0, sh);
     __syncthreads();
     const long long *P = sm.Fs[0];
-    const long long S = 4 * F0 - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
     body.advance();
-    body.out(0, S, s0, F0, pu_at(0));
+    if constexpr (Body::kRaw) {
+      body.out_raw(0, P + own.sm, 0, F0, 0, s0);
+    } else {
+      const long long S = 4 * F0 - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
+      body.out(0, S, s0, F0, pu_at(0));
+    }
     return;
   }
 
@@ -184,9 +190,13 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
       if (has_h) nxt[hal.sm] = F_at(hal, hn, k + 1, sx);
     }
     const long long *P = sm.Fs[k & 1];
-    const long long S =
-        6 * F0 - Fm - Fp - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
-    body.out(k, S, s0, F0, pu_at(k));
+    if constexpr (Body::kRaw) {
+      body.out_raw(k, P + own.sm, Fm, F0, Fp, s0);
+    } else {
+      const long long S =
+          6 * F0 - Fm - Fp - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
+      body.out(k, S, s0, F0, pu_at(k));
+    }
     if (stage) {
       if (in.has_t) stage_store(st0, sm.ring, cs, in.G1t, tid);
       if (in.has_u) stage_store(st1, sm.ringu, cs, in.G1u, tid);
@@ -237,6 +247,7 @@ struct SwF {
 
 template <int DIM, int M>
 struct SweepBody {
+  static constexpr bool kRaw = false;
   const SweepArgs &a;
   const Geo &g;
   int GF, MF, GA, MA, G1u;
@@ -482,6 +493,7 @@ enum ResidMode { RS_GENERIC = 0, RS_FIRST };
 
 template <int DIM, int M>
 struct ResidBody {
+  static constexpr bool kRaw = false;
   const ResidArgs &a;
   const Geo &g;
   const RhsSmem &rs;
@@ -638,9 +650,115 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   if (write_t) meta_flush(b.mt, a.t_out.meta, smt);
 }
 
+// ------------------------------------------------------------------ diffusion residual
+// The outer residual of the variable-coefficient problem, t = f - A u^_L in FP64
+// in the oracle's order: for the neighbours -x, +x, -y, +y, -z, +z,
+// acc = acc + ((k_q + k_p) * 0.5) * (u_p - u_q), A u = acc h^(d-2), t = f - A u,
+// rounded into r as the oracle rounds doubles.  u^_L comes exactly from the
+// int64 march (u~_L + P u^_(L-1) on the CTA grid) and converts exactly to FP64
+// while it spans at most 53 bits (else an error flag).
+template <int DIM>
+struct ResidDiffBody {
+  static constexpr bool kRaw = true;
+  const ResidArgs &a;
+  const Geo &g;
+  double scaleF, hs;  // 2^GF and h^(d-2)
+  int kstride;
+  int bip, lane, i, j;
+  bool rowok, pt, bad;
+  MetaAcc mr;
+  uint32_t *pk;
+
+  __device__ __forceinline__ void prefetch(int) {}
+  __device__ __forceinline__ void advance() {}
+  __device__ __forceinline__ float kat(int I, int J, int K) const {
+    return __ldg(a.kfield + ((long long)(DIM == 3 ? K * kstride : 0) * a.kN + J * kstride) * a.kN + I * kstride);
+  }
+  __device__ __forceinline__ double dv(long long v) {
+    if (v >= (1ll << 53) || v <= -(1ll << 53)) bad = true;
+    return __dmul_rn(__ll2double_rn(v), scaleF);
+  }
+  __device__ __forceinline__ void out(int, long long, long long, long long, long long) {}
+
+  __device__ __forceinline__ void out_raw(int k, const long long *Pc, long long Fm, long long F0, long long Fp,
+                                          long long) {
+    if (!rowok) return;
+    double t = 0.0;
+    if (pt) {
+      const int I = i + 1, J = j + 1, K = k + 1;
+      const double up = dv(F0);
+      const double kp = (double)kat(I, J, K);
+      const long long nv[6] = {Pc[-1], Pc[1], Pc[-PW], Pc[PW], Fm, Fp};
+      double acc = 0.0;
+#pragma unroll
+      for (int e = 0; e < 2 * DIM; e++) {
+        const int Iq = I + (e == 0 ? -1 : e == 1 ? 1 : 0), Jq = J + (e == 2 ? -1 : e == 3 ? 1 : 0);
+        const int Kq = K + (e == 4 ? -1 : e == 5 ? 1 : 0);
+        const double kf = __dmul_rn(__dadd_rn((double)kat(Iq, Jq, Kq), kp), 0.5);
+        acc = __dadd_rn(acc, __dmul_rn(kf, __dsub_rn(up, dv(nv[e]))));
+      }
+      const double f = __dmul_rn((double)rhs_global<DIM>(a, I, J, K),
+                                 __longlong_as_double((long long)(a.Gf + 1023) << 52));
+      t = __dsub_rn(f, __dmul_rn(acc, hs));
+    }
+    int e;
+    const int q = encode_block_f64(t, a.r_out.W, e, a.err);
+    const int blk = k * g.n * g.nbx + bip;
+    pack_block(q, a.r_out.W, pk, a.r_out.words + (long long)blk * a.r_out.W);
+    if (lane == 0) {
+      a.r_out.exps[blk] = (int8_t)e;
+      mr.add(e);
+    }
+  }
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(NT, 2) k_residual_diff(ResidArgs a) {
+  __shared__ SmemTile sm;
+  __shared__ uint32_t pk[TY][33];
+  __shared__ int smr[2], smb[6];
+  const Geo g = a.g;
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
+  const Tile T = make_tile(g);
+  if (tid == 0) smr[0] = smr[1] = 0;
+  Bounds bs, bt, bu;
+  footprint_bounds<DIM>(g, a.gc, T, a.u, true, a.uhc, a.has_uhc, a.uhc, false, smb, bs, bt, bu);
+  const Bounds bF = operand_of(bs, bt);
+  const int GF = bF.G, MF = bF.M;
+  if (tid == 0 && GF < GRID_NONE / 2 && MF + 4 - GF > 62) flag_range(a.err, 204, MF + 4, GF);
+  ResidDiffBody<DIM> b{a, g};
+  // 2^GF as a double (GF is at least -1022 for every operand that fits here)
+  b.scaleF = GF < GRID_NONE / 2 ? __longlong_as_double((long long)(imax(GF, -1022) + 1023) << 52) : 0.0;
+  b.hs = __longlong_as_double((long long)(1023 - (DIM - 2) * g.l) << 52);
+  b.kstride = 1 << (a.Lmax - g.l);
+  b.lane = lane;
+  b.i = T.x0 + lane;
+  b.j = T.j0 + ty;
+  b.rowok = b.j < g.n;
+  b.pt = b.rowok && b.i < g.n;
+  b.bip = b.rowok ? b.j * g.nbx + T.bx : 0;
+  b.bad = false;
+  b.mr.init();
+  b.pk = pk[ty];
+  MarchIn in;
+  in.s = a.u;
+  in.t = a.uhc;
+  in.u = a.uhc;
+  in.has_s = true;
+  in.has_t = a.has_uhc;
+  in.has_u = false;
+  in.GF = GF;
+  in.G1t = GF + 1;
+  in.G1u = 0;
+  march<DIM>(g, a.gc, T, in, sm, b);
+  ovf_flush(b.bad, a.err, 205);
+  meta_flush(b.mr, a.r_out.meta, smr);
+}
+
 // ------------------------------------------------------------------ restriction
 template <int DIM>
 struct RestrictBody {
+  static constexpr bool kRaw = false;
   const RestrictArgs &a;
   const Geo &g;
   int GA, Gd;
@@ -758,6 +876,12 @@ void launch_residual(int dim, const ResidArgs &a, cudaStream_t st) {
     if (first) k_residual<2, RS_FIRST><<<stencil_grid(a.g), b, 0, st>>>(a);
     else k_residual<2, RS_GENERIC><<<stencil_grid(a.g), b, 0, st>>>(a);
   }
+}
+
+void launch_residual_diffusion(int dim, const ResidArgs &a, cudaStream_t st) {
+  dim3 b(32, TY);
+  if (dim == 3) k_residual_diff<3><<<stencil_grid(a.g), b, 0, st>>>(a);
+  else k_residual_diff<2><<<stencil_grid(a.g), b, 0, st>>>(a);
 }
 
 void launch_restrict(int dim, const RestrictArgs &a, cudaStream_t st) {

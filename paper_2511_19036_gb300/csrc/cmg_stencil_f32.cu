@@ -150,12 +150,22 @@ struct MarchF {
   bool has_u;
   int G1u;
   float c2d, hscale;  // 2d and h^(d-2)
+  float cjac;         // Poisson: the Jacobi factor c_l
+  // diffusion: nodal k on the finest grid (boundary included, kN^dim), read at
+  // stride 2^(Lmax - l); the Jacobi factor is omega / D_p per node
+  const float *kfield;
+  int kN, kstride;
+  float omega_f;
 };
 
 // The binary32 z-march: as march() in cmg_stencil.cu, with
-// body.out(k, S, y, F, z, Pu) at every plane k (S, y, F, z binary32 at the
-// thread's node; Pu = (P_l u^)(node) exact on grid G1u - 1).
-template <int DIM, class Body>
+// body.out(k, S, y, F, z, Pu, c) at every plane k (S, y, F, z binary32 at the
+// thread's node; Pu = (P_l u^)(node) exact on grid G1u - 1; c the Jacobi
+// factor at the node).  COEF selects the diffusion operator: for the
+// neighbours -x, +x, -y, +y, -z, +z, kf = fl(fl(k_q + k_p) * 0.5),
+// acc = fl(acc + fl(kf fl(F_p - F_q))), dsum = fl(dsum + kf); S = fl(acc h^(d-2)),
+// D = fl(dsum h^(d-2)), c = fl(omega / D) (nodes outside the level get S = c = 0).
+template <int DIM, bool COEF, class Body>
 __device__ __forceinline__ void march_f32(const Geo &g, const Geo &gc, const Tile &T, const MarchF &in, SmemF &sm,
                                           Body &body, bool &bad) {
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
@@ -200,7 +210,30 @@ __device__ __forceinline__ void march_f32(const Geo &g, const Geo &gc, const Til
     zparents<DIM>(kf, za, zb);
     return ring_p(sm.ringu, own, za, zb);
   };
-  auto stencil = [&](const float *P, float Fm, float F0, float Fp) -> float {
+  auto kat = [&](int I, int J, int K) -> float {
+    return __ldg(in.kfield + ((long long)(DIM == 3 ? K * in.kstride : 0) * in.kN + J * in.kstride) * in.kN +
+                 I * in.kstride);
+  };
+  auto stencil = [&](const float *P, float Fm, float F0, float Fp, int k, float &cp) -> float {
+    if constexpr (COEF) {
+      cp = 0.0f;
+      if (!own.ok) return 0.0f;
+      const int I = T.x0 + lane + 1, J = T.j0 + ty + 1, K = k + 1;
+      const float kp = kat(I, J, K);
+      const float nb[6] = {P[own.sm - 1], P[own.sm + 1], P[own.sm - PW], P[own.sm + PW], Fm, Fp};
+      float acc = 0.0f, dsum = 0.0f;
+#pragma unroll
+      for (int e = 0; e < 2 * DIM; e++) {
+        const int Iq = I + (e == 0 ? -1 : e == 1 ? 1 : 0), Jq = J + (e == 2 ? -1 : e == 3 ? 1 : 0);
+        const int Kq = K + (e == 4 ? -1 : e == 5 ? 1 : 0);
+        const float kf = __fmul_rn(__fadd_rn(kat(Iq, Jq, Kq), kp), 0.5f);
+        acc = __fadd_rn(acc, __fmul_rn(kf, __fsub_rn(F0, nb[e])));
+        dsum = __fadd_rn(dsum, kf);
+      }
+      cp = __fdiv_rn(in.omega_f, __fmul_rn(dsum, in.hscale));
+      return __fmul_rn(acc, in.hscale);
+    }
+    cp = in.cjac;
     float acc = __fmul_rn(in.c2d, F0);
     acc = __fsub_rn(acc, P[own.sm - 1]);
     acc = __fsub_rn(acc, P[own.sm + 1]);
@@ -237,9 +270,10 @@ __device__ __forceinline__ void march_f32(const Geo &g, const Geo &gc, const Til
     sm.Fs[0][own.sm] = F0;
     if (has_h) sm.Fs[0][hal.sm] = F_at(hal, h0, 0, yh, zh);
     __syncthreads();
-    const float S = stencil(sm.Fs[0], 0.0f, F0, 0.0f);
+    float cp;
+    const float S = stencil(sm.Fs[0], 0.0f, F0, 0.0f, 0, cp);
     body.advance();
-    body.out(0, S, y0, F0, z0, pu_at(0));
+    body.out(0, S, y0, F0, z0, pu_at(0), cp);
     return;
   }
 
@@ -282,8 +316,9 @@ __device__ __forceinline__ void march_f32(const Geo &g, const Geo &gc, const Til
       nxt[own.sm] = Fp;
       if (has_h) nxt[hal.sm] = F_at(hal, hn, k + 1, yx, zx);
     }
-    const float S = stencil(sm.Fs[k & 1], Fm, F0, Fp);
-    body.out(k, S, y0, F0, z0, pu_at(k));
+    float cp;
+    const float S = stencil(sm.Fs[k & 1], Fm, F0, Fp, k, cp);
+    body.out(k, S, y0, F0, z0, pu_at(k), cp);
     if (stg) {
       stage(cs, false);
       staged_hi = cs;
@@ -350,14 +385,14 @@ struct SweepBodyF {
     u_c = u_n;
   }
 
-  __device__ __forceinline__ void out(int k, float S, float y, float F0, float z, long long Pu) {
+  __device__ __forceinline__ void out(int k, float S, float y, float F0, float z, long long Pu, float cp) {
     if (!rowok) return;  // warp-uniform: one warp per row
     const int blk = k * g.n * g.nbx + bip;
     // y' = fl(y + fl(c fl(rc - S))); padding lanes carry 0
     float ynew = 0.0f;
     if (pt) {
       const float rc = raw_f32(rc_c, cprc.boff, a.rc.W, bad);
-      ynew = __fadd_rn(y, __fmul_rn(c_f, __fsub_rn(rc, S)));
+      ynew = __fadd_rn(y, __fmul_rn(cp, __fsub_rn(rc, S)));
     }
     int Gy;
     const long long vy = f32_block_to_grid(ynew, Gy, bad);
@@ -425,7 +460,7 @@ struct SweepBodyF {
   }
 };
 
-template <int DIM, int M>
+template <int DIM, int M, bool COEF>
 __global__ void __launch_bounds__(NT, CMG_SWEEP_F32_MINB) k_sweep_f32(SweepArgs a) {
   using F = SfF<M>;
   const bool has_y = F::fixed ? true : (bool)a.has_y, has_z = F::fixed ? F::z : (bool)a.has_z;
@@ -469,7 +504,12 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_F32_MINB) k_sweep_f32(SweepArgs 
   in.G1u = b.G1u;
   in.c2d = (float)(2 * DIM);
   in.hscale = __int_as_float((127 - (DIM - 2) * g.l) << 23);
-  march_f32<DIM>(g, a.gc, T, in, sm, b, b.bad);
+  in.cjac = b.c_f;
+  in.kfield = a.kfield;
+  in.kN = a.kN;
+  in.kstride = a.kstride;
+  in.omega_f = a.omega;
+  march_f32<DIM, COEF>(g, a.gc, T, in, sm, b, b.bad);
   ovf_flush(b.ovf, a.err, 111);
   ovf_flush(b.bad, a.err, 112);
   if (write_y) meta_flush(b.my, a.y_out.meta, smy);
@@ -494,7 +534,7 @@ struct RestrictBodyF {
   }
   __device__ __forceinline__ void advance() { rc_c = rc_n; }
 
-  __device__ __forceinline__ void out(int k, float S, float, float, float, long long) {
+  __device__ __forceinline__ void out(int k, float S, float, float, float, long long, float) {
     if (!rowok || !pt) return;
     const float d = __fsub_rn(raw_f32(rc_c, cprc.boff, a.rc.W, bad), S);
     const long long v = f32_on_grid(d, Gd, bad);
@@ -533,15 +573,126 @@ __global__ void __launch_bounds__(NT, 2) k_restrict_f32(RestrictArgs a) {
   in.G1u = 0;
   in.c2d = (float)(2 * DIM);
   in.hscale = __int_as_float((127 - (DIM - 2) * g.l) << 23);
-  march_f32<DIM>(g, a.gc, T, in, sm, b, b.bad);
+  in.cjac = 0.0f;
+  in.kfield = nullptr;
+  march_f32<DIM, false>(g, a.gc, T, in, sm, b, b.bad);
   ovf_flush(b.bad, a.err, 312);
+}
+
+// ------------------------------------------------------------------ diffusion restriction
+// d = fl(rc - A y~) of the diffusion operator, stored in binary32 on level l
+template <int DIM>
+struct DBodyF {
+  const RestrictArgs &a;
+  const Geo &g;
+  int bip, i, j;
+  bool rowok, pt;
+  CodePos cprc;
+  Raw rc_n, rc_c;
+  bool bad;
+
+  __device__ __forceinline__ void prefetch(int k) {
+    if (!rowok) return;
+    rc_n = raw_load(a.rc, k * g.n * g.nbx + bip, cprc, true);
+  }
+  __device__ __forceinline__ void advance() { rc_c = rc_n; }
+  __device__ __forceinline__ void out(int k, float S, float, float, float, long long, float) {
+    if (!rowok || !pt) return;
+    a.d_out[(long long)(k * g.n + j) * g.R + i] = __fsub_rn(raw_f32(rc_c, cprc.boff, a.rc.W, bad), S);
+  }
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(NT, 3) k_dvec_diff(RestrictArgs a) {
+  __shared__ SmemF sm;
+  const Geo g = a.g;
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const Tile T = make_tile(g);
+  DBodyF<DIM> b{a, g};
+  b.i = T.x0 + lane;
+  b.j = T.j0 + ty;
+  b.rowok = b.j < g.n;
+  b.pt = b.rowok && b.i < g.n;
+  b.bip = b.rowok ? b.j * g.nbx + T.bx : 0;
+  b.cprc = code_pos(lane, a.rc.W);
+  b.bad = false;
+  MarchF in;
+  in.s = a.y;
+  in.has_s = a.has_y;
+  in.w = nullptr;
+  in.has_z = false;
+  in.u = a.acc;
+  in.has_u = false;
+  in.G1u = 0;
+  in.c2d = (float)(2 * DIM);
+  in.hscale = __int_as_float((127 - (DIM - 2) * g.l) << 23);
+  in.cjac = 0.0f;
+  in.kfield = a.kfield;
+  in.kN = a.kN;
+  in.kstride = a.kstride;
+  in.omega_f = 1.0f;
+  march_f32<DIM, true>(g, a.gc, T, in, sm, b, b.bad);
+  ovf_flush(b.bad, a.err, 313);
+}
+
+// rc_(l-1) = round(R_l d): per coarse node, in binary32, the fine node 2J plus
+// half the sum over the odd sets {x},{y},{x,y},{z},{x,z},{y,z},{x,y,z} of
+// d(2J - e_S) then d(2J + e_S); one warp per coarse block row
+template <int DIM>
+__global__ void __launch_bounds__(NT) k_gather_restrict_f32(GatherArgs a) {
+  __shared__ uint32_t pk[TY][33];
+  __shared__ int smr[2];
+  const Geo gc = a.gc, g = a.g;
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
+  if (tid == 0) smr[0] = smr[1] = 0;
+  __syncthreads();
+  bool bad = false;
+  MetaAcc mr;
+  mr.init();
+  const long long blk = (long long)blockIdx.x * TY + ty;
+  if (blk < gc.nblocks) {
+    const long long row = blk / gc.nbx;
+    const int bx = (int)(blk - row * gc.nbx);
+    const int ci = bx * 32 + lane;
+    const int cj = (int)(row % gc.n), ck = (int)(row / gc.n);
+    float r = 0.0f;
+    if (ci < gc.n) {
+      const int I = 2 * (ci + 1), J = 2 * (cj + 1), K = DIM == 3 ? 2 * (ck + 1) : 0;
+      auto at = [&](int Ii, int Jj, int Kk) -> float {  // 1-based fine node, zero outside
+        if (Ii < 1 || Ii > g.n || Jj < 1 || Jj > g.n) return 0.0f;
+        if (DIM == 3 && (Kk < 1 || Kk > g.nz)) return 0.0f;
+        const int kk = DIM == 3 ? Kk - 1 : 0;
+        return __ldg(a.d + (long long)(kk * g.n + Jj - 1) * g.R + Ii - 1);
+      };
+      const int ns = DIM == 3 ? 7 : 3;
+      const int ox[7] = {1, 0, 1, 0, 1, 0, 1}, oy[7] = {0, 1, 1, 0, 0, 1, 1}, oz[7] = {0, 0, 0, 1, 1, 1, 1};
+      float sum = 0.0f;
+#pragma unroll
+      for (int s = 0; s < ns; s++) {
+        sum = __fadd_rn(sum, at(I - ox[s], J - oy[s], K - oz[s]));
+        sum = __fadd_rn(sum, at(I + ox[s], J + oy[s], K + oz[s]));
+      }
+      r = __fadd_rn(at(I, J, K), __fmul_rn(sum, 0.5f));
+    }
+    int G;
+    const long long v = f32_block_to_grid(r, G, bad);
+    int e, sh;
+    const int q = encode_block(v, G, a.rc_out.W, e, sh, a.err);
+    pack_block(q, a.rc_out.W, pk[ty], a.rc_out.words + blk * a.rc_out.W);
+    if (lane == 0) {
+      a.rc_out.exps[blk] = (int8_t)e;
+      mr.add(e);
+    }
+  }
+  ovf_flush(bad, a.err, 314);
+  meta_flush(mr, a.rc_out.meta, smr);
 }
 
 dim3 stencil_grid_f(const Geo &g) {
   return dim3((unsigned)g.nbx, (unsigned)((g.n + TY - 1) / TY), (unsigned)((g.nz + ZC - 1) / ZC));
 }
 
-template <int DIM>
+template <int DIM, bool COEF>
 void launch_sweep_f32_dim(const SweepArgs &a, cudaStream_t st) {
   const dim3 grid = stencil_grid_f(a.g), b(32, TY);
   int m = SF_GENERIC;
@@ -551,20 +702,38 @@ void launch_sweep_f32_dim(const SweepArgs &a, cudaStream_t st) {
     else if (a.corr && a.has_z && !a.write_y && a.write_w && a.write_uh) m = SF_UP_CORR_W_UH;
   }
   switch (m) {
-    case SF_DOWN: k_sweep_f32<DIM, SF_DOWN><<<grid, b, 0, st>>>(a); break;
-    case SF_UP: k_sweep_f32<DIM, SF_UP><<<grid, b, 0, st>>>(a); break;
-    case SF_UP_CORR: k_sweep_f32<DIM, SF_UP_CORR><<<grid, b, 0, st>>>(a); break;
-    case SF_UP_CORR_UH: k_sweep_f32<DIM, SF_UP_CORR_UH><<<grid, b, 0, st>>>(a); break;
-    case SF_UP_CORR_W_UH: k_sweep_f32<DIM, SF_UP_CORR_W_UH><<<grid, b, 0, st>>>(a); break;
-    default: k_sweep_f32<DIM, SF_GENERIC><<<grid, b, 0, st>>>(a); break;
+    case SF_DOWN: k_sweep_f32<DIM, SF_DOWN, COEF><<<grid, b, 0, st>>>(a); break;
+    case SF_UP: k_sweep_f32<DIM, SF_UP, COEF><<<grid, b, 0, st>>>(a); break;
+    case SF_UP_CORR: k_sweep_f32<DIM, SF_UP_CORR, COEF><<<grid, b, 0, st>>>(a); break;
+    case SF_UP_CORR_UH: k_sweep_f32<DIM, SF_UP_CORR_UH, COEF><<<grid, b, 0, st>>>(a); break;
+    case SF_UP_CORR_W_UH: k_sweep_f32<DIM, SF_UP_CORR_W_UH, COEF><<<grid, b, 0, st>>>(a); break;
+    default: k_sweep_f32<DIM, SF_GENERIC, COEF><<<grid, b, 0, st>>>(a); break;
   }
 }
 
 }  // namespace
 
 void launch_sweep_f32(int dim, const SweepArgs &a, cudaStream_t st) {
-  if (dim == 3) launch_sweep_f32_dim<3>(a, st);
-  else launch_sweep_f32_dim<2>(a, st);
+  if (a.kfield) {
+    if (dim == 3) launch_sweep_f32_dim<3, true>(a, st);
+    else launch_sweep_f32_dim<2, true>(a, st);
+  } else {
+    if (dim == 3) launch_sweep_f32_dim<3, false>(a, st);
+    else launch_sweep_f32_dim<2, false>(a, st);
+  }
+}
+
+void launch_dvec_diffusion(int dim, const RestrictArgs &a, cudaStream_t st) {
+  const dim3 grid = stencil_grid_f(a.g), b(32, TY);
+  if (dim == 3) k_dvec_diff<3><<<grid, b, 0, st>>>(a);
+  else k_dvec_diff<2><<<grid, b, 0, st>>>(a);
+}
+
+void launch_gather_restrict_f32(int dim, const GatherArgs &a, cudaStream_t st) {
+  const dim3 b(32, TY);
+  const unsigned nb = (unsigned)((a.gc.nblocks + TY - 1) / TY);
+  if (dim == 3) k_gather_restrict_f32<3><<<nb, b, 0, st>>>(a);
+  else k_gather_restrict_f32<2><<<nb, b, 0, st>>>(a);
 }
 
 void launch_restrict_f32(int dim, const RestrictArgs &a, cudaStream_t st) {
