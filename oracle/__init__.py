@@ -95,6 +95,8 @@ def lib():
                 "cmgo_last_w": (i32, [vp, i32, vp]),
                 "cmgo_set_coefficient": (i32, [vp, vp]),
                 "cmgo_apply_A_diffusion": (i32, [vp, i32, vp, vp]),
+                "cmgo_set_rhs_nodal": (i32, [vp, vp]),
+                "cmgo_gradient_k": (i32, [vp, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -195,6 +197,22 @@ class Oracle:
         assert k.size == n ** self.dim
         self._k = k
         return self._chk(lib().cmgo_set_coefficient(self._ctx, _p(k)), "set_coefficient")
+
+    def set_rhs_nodal(self, g: np.ndarray):
+        """Diffusion: nodal right-hand side values at the interior finest nodes."""
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        assert g.size == ((1 << self.Lmax) - 1) ** self.dim
+        self._g = g
+        return self._chk(lib().cmgo_set_rhs_nodal(self._ctx, _p(g)), "set_rhs_nodal")
+
+    def gradient_k(self, u: np.ndarray, lam: np.ndarray) -> np.ndarray:
+        """dJ/dk at every node (boundary included) for the adjoint state lam."""
+        u = np.ascontiguousarray(u, dtype=np.float64).ravel()
+        lam = np.ascontiguousarray(lam, dtype=np.float64).ravel()
+        N = (1 << self.Lmax) + 1
+        out = np.zeros(N ** self.dim)
+        self._chk(lib().cmgo_gradient_k(self._ctx, _p(u), _p(lam), _p(out)), "gradient_k")
+        return out
 
     def apply_A_diffusion(self, level: int, x: np.ndarray) -> np.ndarray:
         x = np.ascontiguousarray(x, dtype=np.float64)

@@ -363,6 +363,7 @@ struct cmgo_ctx {
   double *w[MAXL + 1]; /* w_l = y~_l + z_l after the up-leg on level l (exact) */
   double *t;           /* exact t_L of the last residual */
   float *kfield;       /* diffusion: nodal k on the finest grid, boundary included */
+  double *grhs;        /* diffusion: nodal right-hand side g (interior of the finest grid), or NULL */
   long long inexact;
   int status;
 };
@@ -556,6 +557,7 @@ void cmgo_destroy(cmgo_ctx *c) {
   free(c->t);
   free(c->tab);
   free(c->kfield);
+  free(c->grhs);
   free(c);
 }
 
@@ -572,6 +574,46 @@ int cmgo_set_coefficient(cmgo_ctx *c, const float *k) {
   c->kfield = (float *)malloc((size_t)cnt * sizeof(float));
   if (!c->kfield) return CMGO_ENOMEM;
   memcpy(c->kfield, k, (size_t)cnt * sizeof(float));
+  return CMGO_OK;
+}
+
+int cmgo_set_rhs_nodal(cmgo_ctx *c, const double *g) {
+  if (!c || !g || !c->P.coef) return CMGO_EINVAL;
+  const int64_t n1 = c->n1max, cnt = c->P.dim == 3 ? n1 * n1 * n1 : n1 * n1;
+  free(c->grhs);
+  c->grhs = (double *)malloc((size_t)cnt * sizeof(double));
+  if (!c->grhs) return CMGO_ENOMEM;
+  memcpy(c->grhs, g, (size_t)cnt * sizeof(double));
+  return CMGO_OK;
+}
+
+/* adjoint gradient dJ/dk_i = -lam^T (dA/dk_i) u for
+ * (A u)_p = h^(d-2) sum_q (k_p + k_q)/2 (u_p - u_q): node i enters the faces to
+ * its neighbours q with weight 1/2, so the derivative is
+ * -(1/2) h^(d-2) sum_q (u_i - u_q)(lam_i - lam_q)  (dJ/dm_i = k_i dJ/dk_i for k = exp(m)) */
+int cmgo_gradient_k(const cmgo_ctx *c, const double *u, const double *lam, double *out) {
+  if (!c || !c->kfield || !u || !lam || !out) return CMGO_EINVAL;
+  const int d = c->P.dim, L = c->P.Lmax, N = (1 << L) + 1;
+  lev g = mklev(d, L);
+  const int nz = d == 3 ? N : 1;
+  for (int K = 0; K < nz; K++)
+    for (int J = 0; J < N; J++)
+      for (int I = 0; I < N; I++) {
+        const int Kn = d == 3 ? K : 1;
+        const double ui = get0(u, &g, I - 1, J - 1, Kn - 1), li = get0(lam, &g, I - 1, J - 1, Kn - 1);
+        volatile double acc = 0.0;
+        for (int e = 0; e < 2 * d; e++) {
+          const int Iq = I + NBR[e][0], Jq = J + NBR[e][1], Kq = (d == 3 ? K : 1) + NBR[e][2];
+          if (Iq < 0 || Iq >= N || Jq < 0 || Jq >= N || (d == 3 && (Kq < 0 || Kq >= N))) continue;
+          volatile double du = ui - get0(u, &g, Iq - 1, Jq - 1, Kq - 1);
+          volatile double dl = li - get0(lam, &g, Iq - 1, Jq - 1, Kq - 1);
+          volatile double pr = du * dl;
+          acc = acc + pr;
+        }
+        volatile double t = acc * 0.5;
+        t = t * ldexp(1.0, -(d - 2) * L);
+        out[((int64_t)(d == 3 ? K : 0) * N + J) * N + I] = -t;
+      }
   return CMGO_OK;
 }
 
@@ -604,6 +646,11 @@ static __int128 rne_shift(__int128 v, int sh) {
 static double f_at(const cmgo_ctx *c, int L, int I, int J, int K) {
   int d = c->P.dim, stride = 1 << (c->P.Lmax - L);
   int ia[3] = {I * stride - 1, J * stride - 1, K * stride - 1};
+  if (c->grhs) {  /* nodal right-hand side: f_L = h_L^d g, injected */
+    const int64_t n1 = c->n1max;
+    const int64_t p = d == 3 ? ((int64_t)ia[2] * n1 + ia[1]) * n1 + ia[0] : (int64_t)ia[1] * n1 + ia[0];
+    return ldexp(c->grhs[p], -d * L);
+  }
   __int128 F = 0;
   for (int t = 0; t < c->nterms; t++) {
     __int128 prod = 1;

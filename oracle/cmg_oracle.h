@@ -96,6 +96,18 @@ int cmgo_set_coefficient(cmgo_ctx *c, const float *k);
  * residual (dense interior arrays, as cmgo_apply_A) */
 int cmgo_apply_A_diffusion(const cmgo_ctx *c, int level, const double *x, double *out);
 
+/* Diffusion: a right-hand side given by its nodal values g at the interior
+ * nodes of the finest grid ((2^Lmax - 1)^dim doubles, copied), replacing the
+ * separable one: f_L = h_L^d g, injected at stride 2^(Lmax - L) on coarser
+ * FMG levels. */
+int cmgo_set_rhs_nodal(cmgo_ctx *c, const double *g);
+/* Adjoint gradient of J with respect to the nodal coefficient k at every node
+ * of the finest grid, boundary included ((2^Lmax + 1)^dim doubles):
+ *   G_i = -((sum_q (u_i - u_q)(lam_i - lam_q)) * 0.5) * h^(d-2)
+ * over the neighbours q of i inside the closed grid in the order -x,+x,-y,+y,
+ * -z,+z, with u = lam = 0 on the boundary; u and lam are interior arrays. */
+int cmgo_gradient_k(const cmgo_ctx *c, const double *u, const double *lam, double *out);
+
 int cmgo_start(cmgo_ctx *c);        /* L = 1: u~_1 = round(f_1 / A_1) */
 int cmgo_next_level(cmgo_ctx *c);   /* L += 1: zero new section, widen the others */
 int cmgo_residual(cmgo_ctx *c);     /* Algorithm 2 */
