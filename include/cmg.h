@@ -157,6 +157,25 @@ cmg_status cmg_set_rhs_separable(cmg_ctx *ctx, int nterms, const int32_t *tables
  * flux between neighbours uses the face value (k_p + k_q) / 2. */
 cmg_status cmg_set_coefficient(cmg_ctx *ctx, const float *k_dev, int64_t n);
 
+/* Diffusion: a right-hand side given by nodal values g at the interior nodes
+ * of the finest grid ((2^L_max - 1)^dim doubles in device memory, borrowed
+ * like the coefficient): f_L = h_L^d g, injected at stride 2^(L_max - L) on
+ * coarser FMG levels.  Replaces cmg_set_rhs_separable (used by adjoint solves,
+ * whose right-hand side du J is not separable). */
+cmg_status cmg_set_rhs_nodal(cmg_ctx *ctx, const double *g_dev, int64_t n);
+
+/* Adjoint gradients of J(u) for -div(k grad u) = g with A u = h^d g and the
+ * adjoint state lam solving A lam = dJ/du (A is symmetric), on device arrays:
+ *   dk_dev[i] = dJ/dk_i = -(1/2) h^(d-2) sum over the neighbours q of node i in
+ *               the closed finest grid (order -x,+x,-y,+y,-z,+z) of
+ *               (u_i - u_q)(lam_i - lam_q), every node, boundary included
+ *               ((2^L_max + 1)^dim doubles; u = lam = 0 on the boundary);
+ *   dg_dev[p] = dJ/dg_p = h^d lam_p on the interior (may be NULL).
+ * u and lam are interior arrays ((2^L_max - 1)^dim doubles), x fastest.  FP64 in
+ * that fixed order.  Enqueued on the context's stream. */
+cmg_status cmg_gradient(cmg_ctx *ctx, const double *u_dev, const double *lam_dev, double *dk_dev,
+                        double *dg_dev);
+
 /* Algorithm 3 end to end (coarse solve, then L = 2..L_max with N_ir IR
  * iterations each).  Synchronises; fills *report when non-NULL. */
 cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *report);

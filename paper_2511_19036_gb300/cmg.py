@@ -93,6 +93,8 @@ _SIGS = {
     "cmg_state_save": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
     "cmg_state_load": (_i32, [_vp, _vp, ctypes.c_size_t]),
     "cmg_set_coefficient": (_i32, [_vp, _vp, _i64]),
+    "cmg_set_rhs_nodal": (_i32, [_vp, _vp, _i64]),
+    "cmg_gradient": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "cmg_storage_model": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32, ctypes.POINTER(Storage)]),
     "cmg_kernel_stats": (_i32, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
@@ -244,6 +246,25 @@ class Solver:
         assert k.is_cuda and k.dtype == torch.float32 and k.is_contiguous()
         self._kfield = k
         self._chk(_lib.cmg_set_coefficient(self._h, k.data_ptr(), k.numel()), "cmg_set_coefficient")
+
+    def set_rhs_nodal(self, g):
+        """Diffusion: nodal right-hand side g (CUDA float64 tensor, interior finest nodes);
+        borrowed, kept referenced here."""
+        import torch
+        assert g.is_cuda and g.dtype == torch.float64 and g.is_contiguous()
+        self._grhs = g
+        self._chk(_lib.cmg_set_rhs_nodal(self._h, g.data_ptr(), g.numel()), "cmg_set_rhs_nodal")
+
+    def gradient(self, u, lam, want_dg: bool = True):
+        """Adjoint gradients (dJ/dk on every node, dJ/dg on the interior) from the
+        state u and the adjoint state lam (CUDA float64, interior)."""
+        import torch
+        N = (1 << self.cfg.L_max) + 1
+        dk = torch.empty(N ** self.cfg.dim, dtype=torch.float64, device=u.device)
+        dg = torch.empty_like(lam) if want_dg else None
+        self._chk(_lib.cmg_gradient(self._h, u.contiguous().data_ptr(), lam.contiguous().data_ptr(),
+                                    dk.data_ptr(), dg.data_ptr() if dg is not None else None), "cmg_gradient")
+        return dk, dg
 
     def start(self):
         self._chk(_lib.cmg_start(self._h), "cmg_start")

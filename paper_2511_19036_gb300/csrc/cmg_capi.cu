@@ -71,6 +71,7 @@ struct cmg_ctx {
   std::string msg;
   bool timing = false;
   const float *kfield = nullptr;  // diffusion: borrowed nodal coefficient
+  const double *grhs = nullptr;   // diffusion: borrowed nodal right-hand side, or null
   float *dbuf = nullptr;          // diffusion: d = rc - A y~ of the finest level in binary32
   KStat stats[CMG_KIND_COUNT][2];  // per kernel kind; [1] = launches on level L_max
   long long launches = 0;
@@ -365,6 +366,34 @@ extern "C" cmg_status cmg_set_coefficient(cmg_ctx *ctx, const float *k_dev, int6
   return CMG_OK;
 }
 
+extern "C" cmg_status cmg_set_rhs_nodal(cmg_ctx *ctx, const double *g_dev, int64_t n) {
+  if (!ctx || !g_dev) return CMG_EINVAL;
+  if (ctx->P.coef != CMG_COEF_DIFFUSION) return fail(ctx, CMG_EINVAL, "nodal right-hand side on a Poisson context");
+  const long long n1 = (1ll << ctx->P.L_max) - 1;
+  if (n != (ctx->P.dim == 3 ? n1 * n1 * n1 : n1 * n1)) return fail(ctx, CMG_EINVAL, "right-hand side size");
+  ctx->grhs = g_dev;
+  ctx->have_rhs = true;
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_gradient(cmg_ctx *ctx, const double *u_dev, const double *lam_dev, double *dk_dev,
+                                   double *dg_dev) {
+  if (!ctx || !u_dev || !lam_dev || !dk_dev) return CMG_EINVAL;
+  if (ctx->P.coef != CMG_COEF_DIFFUSION) return fail(ctx, CMG_EINVAL, "gradient needs the diffusion problem");
+  GradArgs a{};
+  a.dim = ctx->P.dim;
+  a.L = ctx->P.L_max;
+  a.u = u_dev;
+  a.lam = lam_dev;
+  a.kfield = ctx->kfield;
+  a.kN = (1 << ctx->P.L_max) + 1;
+  a.dk = dk_dev;
+  a.dg = dg_dev;
+  launch_gradient(a, ctx->st);
+  CU(cudaGetLastError());
+  return CMG_OK;
+}
+
 // ---------------------------------------------------------------- right-hand side
 extern "C" cmg_status cmg_set_rhs_separable(cmg_ctx *ctx, int nterms, const int32_t *tab, int scale_exp) {
   if (!ctx || !tab || nterms < 1 || nterms > 64) return CMG_EINVAL;
@@ -497,6 +526,7 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
     first_sweep = false;  // the first sweep runs as a sweep with per-node factors
     a.kfield = ctx->kfield;
     a.kN = (1 << ctx->P.L_max) + 1;
+    a.grhs = ctx->grhs;
   }
   a.first_sweep = first_sweep;
   jacobi_factor(ctx, L, a.c_num, a.c_exp, a.cbits);
@@ -740,6 +770,11 @@ static cmg_status do_coarse(cmg_ctx *ctx, bool start, bool corr) {
     a.kfield = ctx->kfield;
     a.kN = (1 << ctx->P.L_max) + 1;
     a.kstride = 1 << (ctx->P.L_max - 1);
+    if (ctx->grhs) {  // the level-1 node is the centre of the finest grid
+      const long long n1 = (1ll << ctx->P.L_max) - 1, c = n1 / 2;
+      a.grhs = ctx->grhs;
+      a.gidx = ctx->P.dim == 3 ? (c * n1 + c) * n1 + c : c * n1 + c;
+    }
   }
   ev_begin(ctx, kstat(ctx, CMG_KIND_COARSE, 1));
   launch_coarse(a, ctx->st);

@@ -189,7 +189,9 @@ __global__ void k_coarse(CoarseArgs a) {
       }
       const double D = __dmul_rn(acc, dim == 3 ? 0.5 : 1.0);
       const int Gn = a.mode_start ? a.Gf1 : G + (dim == 2 ? 2 : 0);  // grid of N as read
-      const double num = __dmul_rn((double)(long long)N, __longlong_as_double((long long)(Gn + 1023) << 52));
+      double num = __dmul_rn((double)(long long)N, __longlong_as_double((long long)(Gn + 1023) << 52));
+      if (a.mode_start && a.grhs)  // nodal right-hand side: f_1 = 2^-d g at the centre node
+        num = __dmul_rn(__ldg(a.grhs + a.gidx), __longlong_as_double((long long)(1023 - dim) << 52));
       x = __ddiv_rn(num, D);
     }
     q = encode_block_f64(x, out.W, e, a.err);

@@ -46,6 +46,7 @@ struct ResidArgs {
   int c_num, c_exp, cbits;
   const float *kfield;  // diffusion: nodal k on the finest grid, boundary included
   int kN;               // 2^Lmax + 1 (the field is kN^dim, x fastest)
+  const double *grhs;   // diffusion: nodal right-hand side g on the finest interior, or null
   int *err;
 };
 
@@ -91,6 +92,8 @@ struct CoarseArgs {
   float *w_out_f;      // FP32 cycle: w_1 = y~_1 in binary32 (else w_out)
   const float *kfield; // diffusion: the level-1 diagonal from k (FP64 division)
   int kN, kstride;
+  const double *grhs;  // diffusion start mode: f_1 = 2^-d g[gidx] (else f1 on Gf1)
+  long long gidx;
   int *err;
 };
 
@@ -136,6 +139,17 @@ void launch_sweep(int dim, const SweepArgs &a, cudaStream_t st);
 void launch_residual(int dim, const ResidArgs &a, cudaStream_t st);
 void launch_restrict(int dim, const RestrictArgs &a, cudaStream_t st);
 void launch_residual_diffusion(int dim, const ResidArgs &a, cudaStream_t st);
+
+// adjoint gradients of J for the diffusion problem (FP64, fixed order)
+struct GradArgs {
+  int dim, L;          // finest level
+  const double *u, *lam;  // interior arrays (2^L - 1)^dim
+  const float *kfield; // unused by the formula; kept for the layout size kN
+  int kN;
+  double *dk;          // dJ/dk at every node, boundary included, kN^dim
+  double *dg;          // dJ/dg = h^d lam on the interior, or null
+};
+void launch_gradient(const GradArgs &a, cudaStream_t st);
 void launch_sweep_f32(int dim, const SweepArgs &a, cudaStream_t st);
 void launch_restrict_f32(int dim, const RestrictArgs &a, cudaStream_t st);
 void launch_dvec_diffusion(int dim, const RestrictArgs &a, cudaStream_t st);

@@ -671,6 +671,7 @@ struct ResidDiffBody {
 
   __device__ __forceinline__ void prefetch(int) {}
   __device__ __forceinline__ void advance() {}
+  __device__ __forceinline__ int b_stride() const { return kstride; }
   __device__ __forceinline__ float kat(int I, int J, int K) const {
     return __ldg(a.kfield + ((long long)(DIM == 3 ? K * kstride : 0) * a.kN + J * kstride) * a.kN + I * kstride);
   }
@@ -697,8 +698,15 @@ struct ResidDiffBody {
         const double kf = __dmul_rn(__dadd_rn((double)kat(Iq, Jq, Kq), kp), 0.5);
         acc = __dadd_rn(acc, __dmul_rn(kf, __dsub_rn(up, dv(nv[e]))));
       }
-      const double f = __dmul_rn((double)rhs_global<DIM>(a, I, J, K),
-                                 __longlong_as_double((long long)(a.Gf + 1023) << 52));
+      double f;
+      if (a.grhs) {  // nodal right-hand side, injected: f_L = h_L^d g
+        const int s = b_stride(), n1 = a.n1max;
+        const long long gi = DIM == 3 ? ((long long)(K * s - 1) * n1 + (J * s - 1)) * n1 + (I * s - 1)
+                                      : (long long)(J * s - 1) * n1 + (I * s - 1);
+        f = __dmul_rn(__ldg(a.grhs + gi), __longlong_as_double((long long)(1023 - DIM * g.l) << 52));
+      } else {
+        f = __dmul_rn((double)rhs_global<DIM>(a, I, J, K), __longlong_as_double((long long)(a.Gf + 1023) << 52));
+      }
       t = __dsub_rn(f, __dmul_rn(acc, hs));
     }
     int e;
@@ -876,6 +884,43 @@ void launch_residual(int dim, const ResidArgs &a, cudaStream_t st) {
     if (first) k_residual<2, RS_FIRST><<<stencil_grid(a.g), b, 0, st>>>(a);
     else k_residual<2, RS_GENERIC><<<stencil_grid(a.g), b, 0, st>>>(a);
   }
+}
+
+// dJ/dk_i = -(1/2) h^(d-2) sum over the neighbours q of i inside the closed grid
+// (order -x,+x,-y,+y,-z,+z) of (u_i - u_q)(lam_i - lam_q), u = lam = 0 on the
+// boundary; one thread per node of the closed grid.  dg = h^d lam.
+__global__ void __launch_bounds__(256) k_gradient(GradArgs a) {
+  const long long N = a.kN, total = a.dim == 3 ? N * N * N : N * N;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int I = (int)(t % N), J = (int)((t / N) % N), K = a.dim == 3 ? (int)(t / (N * N)) : 0;
+  const int n = (int)N - 2;
+  auto at = [&](const double *x, int Ii, int Jj, int Kk) -> double {  // zero on the boundary
+    if (Ii < 1 || Ii > n || Jj < 1 || Jj > n) return 0.0;
+    if (a.dim == 3 && (Kk < 1 || Kk > n)) return 0.0;
+    const long long p = a.dim == 3 ? ((long long)(Kk - 1) * n + (Jj - 1)) * n + (Ii - 1)
+                                   : (long long)(Jj - 1) * n + (Ii - 1);
+    return __ldg(x + p);
+  };
+  const double ui = at(a.u, I, J, K), li = at(a.lam, I, J, K);
+  double acc = 0.0;
+  for (int e = 0; e < 2 * a.dim; e++) {
+    const int Iq = I + (e == 0 ? -1 : e == 1 ? 1 : 0), Jq = J + (e == 2 ? -1 : e == 3 ? 1 : 0);
+    const int Kq = K + (e == 4 ? -1 : e == 5 ? 1 : 0);
+    if (Iq < 0 || Iq >= N || Jq < 0 || Jq >= N || (a.dim == 3 && (Kq < 0 || Kq >= N))) continue;
+    acc = __dadd_rn(acc, __dmul_rn(__dsub_rn(ui, at(a.u, Iq, Jq, Kq)), __dsub_rn(li, at(a.lam, Iq, Jq, Kq))));
+  }
+  const double hs = __longlong_as_double((long long)(1023 - (a.dim - 2) * a.L) << 52);
+  a.dk[t] = -__dmul_rn(__dmul_rn(acc, 0.5), hs);
+  if (a.dg && I >= 1 && I <= n && J >= 1 && J <= n && (a.dim == 2 || (K >= 1 && K <= n))) {
+    const long long p = a.dim == 3 ? ((long long)(K - 1) * n + (J - 1)) * n + (I - 1) : (long long)(J - 1) * n + (I - 1);
+    a.dg[p] = __dmul_rn(li, __longlong_as_double((long long)(1023 - a.dim * a.L) << 52));
+  }
+}
+
+void launch_gradient(const GradArgs &a, cudaStream_t st) {
+  const long long N = a.kN, total = a.dim == 3 ? N * N * N : N * N;
+  k_gradient<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
 }
 
 void launch_residual_diffusion(int dim, const ResidArgs &a, cudaStream_t st) {
