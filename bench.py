@@ -36,6 +36,11 @@ WORKLOADS = {
                          "3-D -div(k grad u) = 1, 1025^3 grid (1023^3 = 1.07e9 DoF), k = exp(g), g a seeded "
                          "Gaussian random field (sigma 1, correlation length 0.1, 256 Fourier features), "
                          "binary32 cycle inside FP64 iterative refinement"),
+    "adjoint3d_257": ("diffusion3d_grf", 8,
+                      "3-D adjoint: J = |u - u_obs|^2 / 2 for -div(exp(m) grad u) = 1 on 257^3, m a seeded "
+                      "GRF (sigma 0.5, seed 2), u_obs from m + GRF (sigma 0.1, seed 3); a step is the forward "
+                      "compact FMG, J, and the backward (adjoint compact FMG + gradient kernel) through "
+                      "torch.autograd"),
     "diffusion3d_257": ("diffusion3d_grf", 8,
                         "3-D -div(k grad u) = 1, 257^3 grid, k = exp(g) as diffusion3d_1025"),
     "poisson3d_257": ("poisson3d_fourier", 8,
@@ -398,6 +403,139 @@ def run_gpu(args, wl):
     return 0
 
 
+def run_adjoint(args, wl):
+    """The adjoint workload: DoF/s of one gradient evaluation (forward + backward)."""
+    import numpy as np
+    import torch
+
+    from cmg_problems.diffusion import diffusion_grf
+    from paper_2511_19036_gb300 import _build
+    _build.build()
+    from paper_2511_19036_gb300 import cmg
+    from paper_2511_19036_gb300.adjoint import diffusion_solve
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    _, Lmax, desc = WORKLOADS[wl]
+    dim = 3
+    prob = diffusion_grf(dim, Lmax, seed=2 + 10 * rank, sigma=0.5)
+    pert = diffusion_grf(dim, Lmax, seed=3 + 10 * rank, sigma=0.1)
+    m = prob.g_field("cuda")
+    k = torch.exp(m).to(torch.float32).reshape(-1).contiguous()
+    k_obs = torch.exp(m + pert.g_field("cuda")).to(torch.float32).reshape(-1).contiguous()
+    n = (1 << Lmax) - 1
+    dofs = n ** dim
+    cfg = cmg.config_for("diffusion3d_grf", Lmax)
+    g_host = torch.ones(dofs, dtype=torch.float64).pin_memory()
+    g = g_host.cuda()
+    with torch.no_grad():
+        u_obs = diffusion_solve(k_obs, g, cfg).reshape(-1)
+
+    def step():
+        kt = k.clone().requires_grad_(True)
+        gt = g.clone().requires_grad_(True)
+        u = diffusion_solve(kt, gt, cfg).reshape(-1)
+        J = 0.5 * torch.sum((u - u_obs) ** 2)
+        dk, dg = torch.autograd.grad(J, (kt, gt))
+        return J, dk * kt.detach(), dg  # dJ/dm = k dJ/dk for k = exp(m)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        J, dm, dg = step()
+    ev1.record()
+    barrier()
+    clocks = clk.stop()
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    # end to end: H2D of g, gradient D2H, inside the timed region
+    dm_host = torch.empty(dm.numel(), dtype=torch.float32).pin_memory()
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        barrier()
+        t0 = time.perf_counter()
+        g.copy_(g_host, non_blocking=True)
+        J, dm, dg = step()
+        dm_host.copy_(dm.reshape(-1), non_blocking=True)
+        barrier()
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e)
+    # the dominant kernel, from one timed forward solve of the same problem
+    solver = cmg.Solver(cfg, timing=True)
+    solver.set_coefficient(k)
+    solver.set_rhs_nodal(g)
+    rep = solver.fmg_solve()
+    peak, peak_kind = measured_peak_hbm()
+    ks = solver.kernel_stats()["sweep_top"]
+    achieved = ks["bytes"] / (ks["ms"] * 1e-3) / 1e9 if ks["ms"] > 0 else None
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        Ls = 6
+        o_p = diffusion_grf(dim, Ls, seed=2, sigma=0.5)
+        ko = o_p.kfield().ravel()
+        t0 = time.perf_counter()
+        o = oracle.Oracle(dim, Ls, o_p.tables, o_p.scale_exp, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1,
+                          nu2=cfg.nu2, omega=cfg.omega, arith=1, coef=1, kfield=ko)
+        o.set_rhs_nodal(np.ones(((1 << Ls) - 1) ** dim))
+        o.fmg()
+        uo = np.asarray(o.decode_solution()).ravel()
+        oa = oracle.Oracle(dim, Ls, o_p.tables, o_p.scale_exp, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1,
+                           nu2=cfg.nu2, omega=cfg.omega, arith=1, coef=1, kfield=ko)
+        oa.set_rhs_nodal(np.ldexp(uo, dim * Ls))
+        oa.fmg()
+        o.gradient_k(uo, np.asarray(oa.decode_solution()).ravel())
+        dt = time.perf_counter() - t0
+        sd = ((1 << Ls) - 1) ** dim
+        cpu = {"value": sd / dt, "unit": "DoF/s", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
+               "kind": "oracle", "sample": "oracle forward + adjoint compact FMG + gradient at L_max=%d (%d DoF), %.1f s"
+               % (Ls, sd, dt)}
+    line = {
+        "metric": "adjoint gradient (forward + adjoint compact FMG + gradient) DoF/s", "value": world * dofs / (ms_step * 1e-3),
+        "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 cycle + f64 refinement", "data": "synthetic",
+        "config": {"workload": wl, "description": desc, "dim": dim, "L_max": Lmax, "dofs": dofs, "b1": cfg.b1,
+                   "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": "V(%d,%d)" % (cfg.nu1, cfg.nu2),
+                   "l2": "working set larger than L2", "parallelism": "replicas x%d" % world},
+        "J": float(J.detach()),
+        "roofline": {"kernel": "k_sweep_f32<3> finest level (forward solve)", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": None,
+                     "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * dofs / e2e_s, "unit": "DoF/s", "h2d_bytes_per_step": dofs * 8,
+                "d2h_bytes_per_step": dm.numel() * 4},
+        "gpu_launches": int(2 * rep["launches"] + 1),
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,6 +549,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
+    if args.workload.startswith("adjoint"):
+        return run_adjoint(args, args.workload)
     return run_gpu(args, args.workload)
 
 
