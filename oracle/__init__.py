@@ -52,7 +52,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("Lmax", ctypes.c_int), ("b1", ctypes.c_int),
                 ("b2", ctypes.c_int), ("ku", ctypes.c_int), ("kr", ctypes.c_int),
                 ("N", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
-                ("omega", ctypes.c_double), ("arith", ctypes.c_int), ("coef", ctypes.c_int)]
+                ("omega", ctypes.c_double), ("arith", ctypes.c_int), ("coef", ctypes.c_int),
+                ("smoother", ctypes.c_int)]
 
 
 def lib():
@@ -170,9 +171,9 @@ class Oracle:
     def __init__(self, dim: int, Lmax: int, tables: np.ndarray, scale_exp: int, *,
                  b1: int, b2: int, N: int, nu1: int, nu2: int, omega: float,
                  ku: int = 2, kr: int = 1, arith: int = 0, coef: int = 0,
-                 kfield: Optional[np.ndarray] = None):
+                 kfield: Optional[np.ndarray] = None, smoother: int = 0):
         self.dim, self.Lmax = dim, Lmax
-        self.params = _Params(dim, Lmax, b1, b2, ku, kr, N, nu1, nu2, omega, arith, coef)
+        self.params = _Params(dim, Lmax, b1, b2, ku, kr, N, nu1, nu2, omega, arith, coef, smoother)
         self._tables = np.ascontiguousarray(tables, dtype=np.int32)
         assert self._tables.shape[1:] == (dim, (1 << Lmax) - 1)
         self._ctx = lib().cmgo_create(ctypes.byref(self.params), self._tables.shape[0],

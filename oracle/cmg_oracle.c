@@ -497,6 +497,7 @@ cmgo_ctx *cmgo_create(const cmgo_params *p, int nterms, const int32_t *tables, i
       p->nu1 < 0 || p->nu2 < 1 || p->b1 < 0 || p->b2 < 0 || nterms < 1 || !tables)
     return NULL;
   if (p->coef != 0 && (p->coef != 1 || p->arith != 1 || p->nu1 < 1)) return NULL;
+  if (p->smoother != 0 && (p->smoother != 1 || p->nu1 != 0)) return NULL;
   cmgo_ctx *c = (cmgo_ctx *)calloc(1, sizeof(cmgo_ctx));
   if (!c) return NULL;
   c->P = *p;
@@ -813,9 +814,18 @@ static double cjac(cmgo_ctx *c, int l, long long *cnt) {
   return ldexp(cw, (c->P.dim - 2) * l);
 }
 
+/* colour of 0-based node (i, j, k): red (0) when (i+1)+(j+1)+(k+1) is even */
+static inline int node_colour(int dim, int i, int j, int k) {
+  return ((i + 1) + (j + 1) + (dim == 3 ? (k + 1) : 0)) & 1;
+}
+
 /* one weighted-Jacobi sweep y <- round(y + c (rhs - A z - A y)) on level l
- * (eq. smoother on the compact equation eq. cfas, with s = 0); z may be NULL. */
-static int jacobi(cmgo_ctx *c, int l, const double *z, long long *cnt) {
+ * (eq. smoother on the compact equation eq. cfas, with s = 0); z may be NULL.
+ * colour >= 0 restricts the update to the nodes of that colour (the others keep
+ * their value): a red half-sweep followed by a black one is one red-black
+ * Gauss-Seidel sweep, since nodes of one colour couple only to the other. */
+
+static int jacobi(cmgo_ctx *c, int l, const double *z, long long *cnt, int colour) {
   lev g = mklev(c->P.dim, l);
   double cl = cjac(c, l, cnt);
   double *Ay = (double *)malloc((size_t)g.np * sizeof(double));
@@ -832,6 +842,11 @@ static int jacobi(cmgo_ctx *c, int l, const double *z, long long *cnt) {
   long long cc = 0;
 #pragma omp parallel for reduction(+ : cc) schedule(static)
   for (int64_t p = 0; p < g.np; p++) {
+    const int i = (int)(p % g.n), j = (int)((p / g.n) % g.n), k = (int)(p / ((int64_t)g.n * g.n));
+    if (colour >= 0 && node_colour(g.dim, i, j, k) != colour) {  /* other colour: kept */
+      yn[p] = c->y[l].v[p];
+      continue;
+    }
     double res = c->rc[l].v[p];
     if (z) res = xsub(res, Az[p], &cc);
     res = xsub(res, Ay[p], &cc);
@@ -849,7 +864,7 @@ static int jacobi(cmgo_ctx *c, int l, const double *z, long long *cnt) {
  * S = A F as in A_at_f32, res = fl(rc - S), y' = fl(y + fl(c res)); y' is then
  * rounded into the BFP section like the exact sweep.  Every stored value the
  * cycle reads must be an exact normal-range binary32 number (else ERANGE). */
-static int jacobi_f32(cmgo_ctx *c, int l, const float *z, long long *cnt) {
+static int jacobi_f32(cmgo_ctx *c, int l, const float *z, long long *cnt, int colour) {
   lev g = mklev(c->P.dim, l);
   int bad = 0;
   const float cl = to_f32(cjac(c, l, cnt), &bad);
@@ -874,6 +889,10 @@ static int jacobi_f32(cmgo_ctx *c, int l, const float *z, long long *cnt) {
     for (int j = 0; j < g.n; j++)
       for (int i = 0; i < g.n; i++) {
         int64_t p = idx(&g, i, j, k);
+        if (colour >= 0 && node_colour(g.dim, i, j, k) != colour) {  /* other colour: kept */
+          yn[p] = c->y[l].v[p];
+          continue;
+        }
         volatile float S, cp = cl;
         if (c->P.coef) {  /* diffusion: the Jacobi factor omega / D_p per node */
           float Sd, Dd;
@@ -907,7 +926,7 @@ int cmgo_down(cmgo_ctx *c, int l) {
   if (l == c->L) sec_copy(&c->rc[l], &c->r[l], &g);
   sec_zero(&c->y[l], &g, Wr(c, l));
   for (int s = 0; s < c->P.nu1 && st == CMGO_OK; s++)
-    st = c->P.arith ? jacobi_f32(c, l, NULL, &cnt) : jacobi(c, l, NULL, &cnt);
+    st = c->P.arith ? jacobi_f32(c, l, NULL, &cnt, -1) : jacobi(c, l, NULL, &cnt, -1);
   if (st == CMGO_OK && c->P.arith && c->P.nu1 > 0) {
     /* FP32 cycle: d = fl(rc - A y) in binary32; R d is then formed exactly
      * (binary32 rounding never leaves the grid of its inputs, so the exact sum
@@ -1022,7 +1041,14 @@ int cmgo_up(cmgo_ctx *c, int l) {
     for (int k = 0; k < g.nz; k++)
       for (int j = 0; j < g.n; j++)
         for (int i = 0; i < g.n; i++) zf[idx(&g, i, j, k)] = P_at_f32(wc, &gc, i + 1, j + 1, k + 1);
-    for (int s = 0; s < c->P.nu2 && st == CMGO_OK; s++) st = jacobi_f32(c, l, zf, &cnt);
+    for (int s = 0; s < c->P.nu2 && st == CMGO_OK; s++) {
+      if (c->P.smoother) { /* red-black Gauss-Seidel: red, then black */
+        st = jacobi_f32(c, l, zf, &cnt, 0);
+        if (st == CMGO_OK) st = jacobi_f32(c, l, zf, &cnt, 1);
+      } else {
+        st = jacobi_f32(c, l, zf, &cnt, -1);
+      }
+    }
     for (int64_t p = 0; p < g.np; p++) {
       volatile float w = to_f32(c->y[l].v[p], &bad) + zf[p];
       c->w[l][p] = (double)w;
@@ -1035,7 +1061,14 @@ int cmgo_up(cmgo_ctx *c, int l) {
   double *z = (double *)malloc((size_t)g.np * sizeof(double));
   if (!z) return setst(c, CMGO_ENOMEM);
   prolong(&gc, &g, c->w[l - 1], z, &cnt);
-  for (int s = 0; s < c->P.nu2 && st == CMGO_OK; s++) st = jacobi(c, l, z, &cnt);
+  for (int s = 0; s < c->P.nu2 && st == CMGO_OK; s++) {
+    if (c->P.smoother) { /* red-black Gauss-Seidel: red, then black */
+      st = jacobi(c, l, z, &cnt, 0);
+      if (st == CMGO_OK) st = jacobi(c, l, z, &cnt, 1);
+    } else {
+      st = jacobi(c, l, z, &cnt, -1);
+    }
+  }
   long long cc = 0;
 #pragma omp parallel for reduction(+ : cc) schedule(static)
   for (int64_t p = 0; p < g.np; p++) c->w[l][p] = xadd(c->y[l].v[p], z[p], &cc);

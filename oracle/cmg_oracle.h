@@ -62,6 +62,8 @@ typedef struct {
   int coef;     /* 0: Poisson; 1: diffusion -div(k grad u) with a nodal binary32
                    coefficient field (cmgo_set_coefficient); needs arith = 1 and
                    nu1 >= 1 (see cmg_oracle.c, "diffusion") */
+  int smoother; /* 0: weighted Jacobi; 1: red-black Gauss-Seidel (each sweep a red
+                   then a black half-sweep; needs nu1 = 0, the paper's V(0,1)) */
 } cmgo_params;
 
 /* Section selectors. */
