@@ -57,6 +57,7 @@ typedef enum {
  * rounded only where they are stored, as the paper's rounding rules prescribe. */
 enum { CMG_ARITH_EXACT = 0, CMG_ARITH_FP32 = 1 };
 enum { CMG_COEF_POISSON = 0, CMG_COEF_DIFFUSION = 1 };
+enum { CMG_SMOOTHER_JACOBI = 0, CMG_SMOOTHER_RBGS = 1 };
 
 typedef struct {
   int dim;             /* 2 or 3 */
@@ -67,7 +68,7 @@ typedef struct {
   int k_u;             /* regressive increment of u~, p + 1 = 2 */
   int k_r;             /* regressive increment of r and y~, m = 1 */
   int N_ir;            /* IR iterations per FMG level (Algorithm 3 N) */
-  int nu1, nu2;        /* pre-/post-smoothing Jacobi sweeps, nu1 >= 0, nu2 >= 1 */
+  int nu1, nu2;        /* pre-/post-smoothing sweeps, nu1 >= 0, nu2 >= 1 */
   int omega_num;       /* Jacobi weight omega = omega_num / 2^omega_log2den, */
   int omega_log2den;   /* which must make omega / (2d) a dyadic rational */
   int arith;           /* CMG_ARITH_EXACT (0): exact V-cycle; CMG_ARITH_FP32 (1):
@@ -81,6 +82,14 @@ typedef struct {
                           cmg_set_coefficient; needs arith = CMG_ARITH_FP32 and
                           nu1 >= 1 (the outer residual and level-1 solve in FP64,
                           the cycle in binary32, each in a fixed order) */
+  int smoother;        /* CMG_SMOOTHER_JACOBI (0): weighted Jacobi sweeps;
+                          CMG_SMOOTHER_RBGS (1): red-black Gauss-Seidel post-
+                          smoothing (Algorithm 1 as the V(0,1) cycle of Sec. 7):
+                          each of the nu2 sweeps updates the red nodes (the sum
+                          of the 1-based node numbers even), then the black ones,
+                          each half-sweep with the damped point update
+                          y <- y + omega/(2d) h^(2-d) (rc - A(y + z)) and rounded
+                          into the BFP section; needs nu1 = 0 and coef = 0 */
 } cmg_params;
 
 /* Per-solve report filled by cmg_fmg_solve. */

@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
                 ("b2", ctypes.c_int), ("k_u", ctypes.c_int), ("k_r", ctypes.c_int),
                 ("N_ir", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega_num", ctypes.c_int), ("omega_log2den", ctypes.c_int),
-                ("arith", ctypes.c_int), ("coef", ctypes.c_int)]
+                ("arith", ctypes.c_int), ("coef", ctypes.c_int), ("smoother", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -173,7 +173,7 @@ def decode_raw(words_ptr: int, exps_ptr: int, n: int, W: int, x_ptr: int, stream
 # ---------------------------------------------------------------- solver
 def to_params(cfg: SolverConfig) -> Params:
     return Params(cfg.dim, cfg.L_max, cfg.b1, cfg.b2, cfg.k_u, cfg.k_r, cfg.N_ir,
-                  cfg.nu1, cfg.nu2, cfg.omega_num, cfg.omega_log2den, cfg.arith, cfg.coef)
+                  cfg.nu1, cfg.nu2, cfg.omega_num, cfg.omega_log2den, cfg.arith, cfg.coef, cfg.smoother)
 
 
 def params_check(cfg: SolverConfig) -> int:

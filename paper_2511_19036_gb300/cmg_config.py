@@ -19,6 +19,7 @@ class SolverConfig:
     k_r: int = 1
     arith: int = 0  # 0: exact V-cycle; 1: binary32 V-cycle inside exact iterative refinement
     coef: int = 0   # 0: Poisson; 1: diffusion -div(k grad u) (needs arith = 1)
+    smoother: int = 0  # 0: weighted Jacobi; 1: red-black Gauss-Seidel (needs nu1 = 0)
 
     @property
     def omega(self) -> float:

@@ -214,6 +214,9 @@ extern "C" cmg_status cmg_params_check(const cmg_params *p) {
   if (p->arith != CMG_ARITH_EXACT && p->arith != CMG_ARITH_FP32) return CMG_EINVAL;
   if (p->coef != CMG_COEF_POISSON && p->coef != CMG_COEF_DIFFUSION) return CMG_EINVAL;
   if (p->coef == CMG_COEF_DIFFUSION && (p->arith != CMG_ARITH_FP32 || p->nu1 < 1)) return CMG_EINVAL;
+  if (p->smoother != CMG_SMOOTHER_JACOBI &&
+      (p->smoother != CMG_SMOOTHER_RBGS || p->nu1 != 0 || p->coef != CMG_COEF_POISSON))
+    return CMG_EINVAL;
   if (p->dim == 3 && p->omega_num % 3 != 0) return CMG_EINVAL;  // omega/6 must be dyadic
   // keep the Jacobi numerator small (it widens the exact integers by its bit length)
   int num = p->dim == 3 ? p->omega_num / 3 : p->omega_num;
@@ -594,6 +597,7 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
 // one Jacobi sweep on level l reading y[ycur] (unless y_zero), writing y[1-ycur]
 struct SweepOpts {
   bool has_z = false, write_y = true, corr = false, write_w = false, write_uh = false;
+  int rb = 0;  // red-black half-sweep: 1 red nodes only, 2 black nodes only
 };
 
 static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
@@ -608,6 +612,7 @@ static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
   a.corr = o.corr;
   a.write_w = o.write_w;
   a.write_uh = o.write_uh;
+  a.rb = o.rb;
   a.has_uhc = l > 1;
   a.Wy = Wr(ctx, l, L);
   if (a.has_y) a.y_in = sec_of(v.y[v.ycur]);
@@ -863,6 +868,19 @@ extern "C" cmg_status cmg_coarse(cmg_ctx *ctx) {
   return do_coarse(ctx, false, false);
 }
 
+// one post-smoothing sweep with the options o of its last launch: a Jacobi sweep,
+// or a red half-sweep (y~ stored) followed by a black half-sweep carrying o
+static cmg_status post_sweep(cmg_ctx *ctx, int l, SweepOpts o) {
+  if (ctx->P.smoother != CMG_SMOOTHER_RBGS) return do_sweep(ctx, l, o);
+  SweepOpts red;
+  red.has_z = o.has_z;
+  red.rb = 1;
+  cmg_status s = do_sweep(ctx, l, red);
+  if (s) return s;
+  o.rb = 2;
+  return do_sweep(ctx, l, o);
+}
+
 extern "C" cmg_status cmg_up(cmg_ctx *ctx, int l) {
   if (!ctx) return CMG_EINVAL;
   cmg_status s = need(ctx, l >= 2 && l <= ctx->L, "bad level");
@@ -871,7 +889,7 @@ extern "C" cmg_status cmg_up(cmg_ctx *ctx, int l) {
     SweepOpts o;
     o.has_z = true;
     o.write_w = (k == ctx->P.nu2 - 1) && l < ctx->P.L_max;
-    if ((s = do_sweep(ctx, l, o))) return s;
+    if ((s = post_sweep(ctx, l, o))) return s;
   }
   return CMG_OK;
 }
@@ -939,7 +957,7 @@ static cmg_status ir_fused(cmg_ctx *ctx, bool need_uh_top) {
       o.corr = last;
       o.write_w = last && l < L;
       o.write_uh = last && (l < L || need_uh_top) && l < ctx->P.L_max;
-      if ((s = do_sweep(ctx, l, o))) return s;
+      if ((s = post_sweep(ctx, l, o))) return s;
     }
   }
   ctx->uh_upto = (need_uh_top && L < ctx->P.L_max) ? L : L - 1;

@@ -26,6 +26,8 @@ struct SweepArgs {
   const float *kfield; // diffusion (FP32 cycle): nodal k, boundary included
   int kN, kstride;     // 2^Lmax + 1, and the level's stride 2^(Lmax - l) in it
   float omega;         // diffusion: Jacobi weight (factor omega / D_p per node)
+  int rb;              // 0: every node; 1 / 2: only the red / black nodes (red: the
+                       // 1-based node numbers I + J [+ K] even), the others keep y~
   int *err;
 };
 

@@ -270,6 +270,10 @@ struct SweepBody {
   __device__ __forceinline__ bool CORR() const { return SwF<M>::fixed ? SwF<M>::corr : (bool)a.corr; }
   __device__ __forceinline__ bool WW() const { return SwF<M>::fixed ? SwF<M>::w : (bool)a.write_w; }
   __device__ __forceinline__ bool WUH() const { return SwF<M>::fixed ? SwF<M>::uh : (bool)a.write_uh; }
+  // red-black half-sweep: is node (i, j, k) updated?  red: 1-based I + J [+ K] even
+  __device__ __forceinline__ bool upd(int k) const {
+    return a.rb == 0 || (((i + j + (DIM == 3 ? k + 1 : 0)) ^ (a.rb - 1)) & 1) == 0;
+  }
 
   __device__ __forceinline__ void prefetch(int k) {
     if (!rowok) return;
@@ -292,18 +296,19 @@ struct SweepBody {
     const int Gcr = Gres + a.c_exp;
     const int Gy = HY() ? imin(GF, Gcr) : Gcr;
     if (!pt) S = 0;
+    const bool up = upd(k);  // a node left out by a half-sweep keeps y~
     long long ynew;
     // static range of this block (warp-uniform); else per-value checks
     if (Gres >= GRID_NONE / 2 || (Mres - Gres <= 62 - a.cbits && Mres + a.cbits + a.c_exp - Gy <= 61 &&
                                   (!HY() || MF - Gy <= 61))) {
       const long long res = raw_val(rc, cprc.boff, a.rc.W, Gres) - shl_fast(S, GA - Gres);
-      ynew = shl_fast(res * a.c_num, Gcr - Gy);
+      ynew = up ? shl_fast(res * a.c_num, Gcr - Gy) : 0;
       if (HY()) ynew += shl_fast(own, GF - Gy);
     } else {
       if (erc != -128 && erc - Gres > 61) ovf = true;
-      const long long res = raw_val(rc, cprc.boff, a.rc.W, Gres) - shl_ck(S, GA - Gres, ovf);
+      const long long res = raw_val(rc, cprc.boff, a.rc.W, Gres) - (up ? shl_ck(S, GA - Gres, ovf) : 0);
       ck62(res, ovf);
-      ynew = shl_ck(mul_ck(res, a.c_num, a.cbits, ovf), Gcr - Gy, ovf);
+      ynew = up ? shl_ck(mul_ck(res, a.c_num, a.cbits, ovf), Gcr - Gy, ovf) : 0;
       if (HY()) ynew += shl_ck(own, GF - Gy, ovf);
       ck62(ynew, ovf);
     }

@@ -373,6 +373,10 @@ struct SweepBodyF {
   __device__ __forceinline__ bool CORR() const { return SfF<M>::fixed ? SfF<M>::corr : (bool)a.corr; }
   __device__ __forceinline__ bool WW() const { return SfF<M>::fixed ? SfF<M>::w : (bool)a.write_w; }
   __device__ __forceinline__ bool WUH() const { return SfF<M>::fixed ? SfF<M>::uh : (bool)a.write_uh; }
+  // red-black half-sweep: is node (i, j, k) updated?  red: 1-based I + J [+ K] even
+  __device__ __forceinline__ bool upd(int k) const {
+    return a.rb == 0 || (((i + j + (DIM == 3 ? k + 1 : 0)) ^ (a.rb - 1)) & 1) == 0;
+  }
 
   __device__ __forceinline__ void prefetch(int k) {
     if (!rowok) return;
@@ -388,11 +392,16 @@ struct SweepBodyF {
   __device__ __forceinline__ void out(int k, float S, float y, float F0, float z, long long Pu, float cp) {
     if (!rowok) return;  // warp-uniform: one warp per row
     const int blk = k * g.n * g.nbx + bip;
-    // y' = fl(y + fl(c fl(rc - S))); padding lanes carry 0
+    // y' = fl(y + fl(c fl(rc - S))); padding lanes carry 0; a node left out by a
+    // half-sweep keeps y
     float ynew = 0.0f;
     if (pt) {
-      const float rc = raw_f32(rc_c, cprc.boff, a.rc.W, bad);
-      ynew = __fadd_rn(y, __fmul_rn(cp, __fsub_rn(rc, S)));
+      if (upd(k)) {
+        const float rc = raw_f32(rc_c, cprc.boff, a.rc.W, bad);
+        ynew = __fadd_rn(y, __fmul_rn(cp, __fsub_rn(rc, S)));
+      } else {
+        ynew = y;
+      }
     }
     int Gy;
     const long long vy = f32_block_to_grid(ynew, Gy, bad);

@@ -59,6 +59,18 @@ def test_host_side_parameter_validation(libpath):
         bad = cmg.config_for("poisson3d_fourier", 8)
         setattr(bad, k, v)
         assert cmg.params_check(bad) == cmg.EINVAL, k
+    # red-black Gauss-Seidel: only as V(0, nu2) post-smoothing of the Poisson problem
+    rb = cmg.config_for("poisson3d_fourier", 8)
+    rb.smoother, rb.nu1, rb.nu2 = 1, 0, 1
+    assert cmg.params_check(rb) == cmg.OK
+    for k, v in [("nu1", 1), ("smoother", 2), ("smoother", -1)]:
+        bad = cmg.config_for("poisson3d_fourier", 8)
+        bad.smoother, bad.nu1, bad.nu2 = 1, 0, 1
+        setattr(bad, k, v)
+        assert cmg.params_check(bad) == cmg.EINVAL, k
+    diff = cmg.config_for("diffusion3d_grf", 8)
+    diff.smoother = 1
+    assert cmg.params_check(diff) == cmg.EINVAL
     wide = cmg.config_for("poisson3d_fourier", 14)
     wide.b1 = 12
     assert cmg.params_check(wide) == cmg.ERANGE
