@@ -138,12 +138,20 @@ def oracle_fmg_rate(prob_name: str, L: int, cfg, max_seconds: float = 30.0):
     import oracle
     prob = cmg_problems.make_problem(prob_name, L)
     o = oracle.Oracle.for_problem(prob, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1, nu2=cfg.nu2,
-                                  omega=cfg.omega, arith=cfg.arith)
+                                  omega=cfg.omega, arith=cfg.arith, smoother=cfg.smoother)
     t0 = time.perf_counter()
     o.fmg()
     dt = time.perf_counter() - t0
     dofs = ((1 << L) - 1) ** prob.dim
     return dofs / dt, dt, dofs
+
+
+def smoother_of(args) -> int:
+    return 1 if args.smoother == "rbgs" else 0
+
+
+def cycle_name(cfg) -> str:
+    return "V(%d,%d) %s" % (cfg.nu1, cfg.nu2, "red-black Gauss-Seidel" if cfg.smoother else "weighted Jacobi")
 
 
 def pick_sample_level(prob_name: str, Lmax: int, dim: int) -> int:
@@ -163,7 +171,7 @@ def run_reference(args, wl):
     import oracle
     oracle.build()
     from paper_2511_19036_gb300.cmg_config import config_for
-    cfg = config_for(prob_name, Lmax, arith=1 if args.arith == "fp32" else 0)
+    cfg = config_for(prob_name, Lmax, arith=1 if args.arith == "fp32" else 0, smoother=smoother_of(args))
     dim = cfg.dim
     Ls = pick_sample_level(prob_name, Lmax, dim)
     for _ in range(args.warmup):
@@ -182,8 +190,7 @@ def run_reference(args, wl):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": wl, "description": desc, "dim": dim, "L_max": Lmax, "b1": cfg.b1,
-                   "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": "V(%d,%d)" % (cfg.nu1, cfg.nu2),
-                   "omega": cfg.omega},
+                   "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": cycle_name(cfg), "omega": cfg.omega},
         "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -211,7 +218,7 @@ def run_gpu(args, wl):
         dist.init_process_group("nccl")
     prob_name, Lmax, desc = WORKLOADS[wl]
     prob = cmg_problems.make_problem(prob_name, Lmax, seed=rank)
-    cfg = cmg.config_for(prob_name, Lmax, arith=1 if args.arith == "fp32" else 0)
+    cfg = cmg.config_for(prob_name, Lmax, arith=1 if args.arith == "fp32" else 0, smoother=smoother_of(args))
     diffusion = bool(getattr(prob, "coef", 0))
     stream = torch.cuda.Stream()
     solver = cmg.Solver(cfg, stream=stream, timing=True)
@@ -254,7 +261,7 @@ def run_gpu(args, wl):
     sw_bytes = sum(r["sweep_alg_bytes"] for r in reports)
     peak, peak_kind = measured_peak_hbm()
     achieved = (sw_bytes / sw_n) / (sw_ms / sw_n * 1e-3) / 1e9 if sw_n and sw_ms > 0 else None
-    traffic_per_dof = read_traffic("k_sweep", wl)
+    traffic_per_dof = read_traffic("k_sweep", wl + ("_rbgs" if cfg.smoother else ""))
     roofline = {"kernel": "k_sweep<3> finest level" if cfg.dim == 3 else "k_sweep<2> finest level",
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
@@ -340,7 +347,7 @@ def run_gpu(args, wl):
     # the FP32 cycle: its solution against the exact cycle's on the same planes
     fp32_vs_exact = None
     if cfg.arith == 1 and not diffusion:
-        cfg64 = cmg.config_for(prob_name, Lmax)
+        cfg64 = cmg.config_for(prob_name, Lmax, smoother=cfg.smoother)
         ref = cmg.Solver(cfg64, stream=stream)
         ref.set_rhs(prob.tables, prob.scale_exp)
         ref.fmg_solve()
@@ -376,7 +383,7 @@ def run_gpu(args, wl):
         "vs_baseline": None, "dtype": "int64" if cfg.arith == 0 else "f32 cycle + int64 refinement",
         "data": "synthetic",
         "config": {"workload": wl, "description": desc, "dim": cfg.dim, "L_max": Lmax, "dofs": dofs,
-                   "b1": cfg.b1, "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": "V(%d,%d)" % (cfg.nu1, cfg.nu2),
+                   "b1": cfg.b1, "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": cycle_name(cfg),
                    "omega": cfg.omega, "arith": "exact" if cfg.arith == 0 else "fp32 cycle",
                    "l2": "working set larger than L2" if dofs > 1e8 else
                    "working set fits L2 (state per step re-read from L2)",
@@ -518,7 +525,7 @@ def run_adjoint(args, wl):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 cycle + f64 refinement", "data": "synthetic",
         "config": {"workload": wl, "description": desc, "dim": dim, "L_max": Lmax, "dofs": dofs, "b1": cfg.b1,
-                   "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": "V(%d,%d)" % (cfg.nu1, cfg.nu2),
+                   "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": cycle_name(cfg),
                    "l2": "working set larger than L2", "parallelism": "replicas x%d" % world},
         "J": float(J.detach()),
         "roofline": {"kernel": "k_sweep_f32<3> finest level (forward solve)", "bound": "hbm", "achieved": achieved,
@@ -546,6 +553,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arith", default="exact", choices=["exact", "fp32"],
                     help="exact V-cycle, or the binary32 V-cycle inside exact iterative refinement")
+    ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "rbgs"],
+                    help="V(2,2) weighted Jacobi, or V(0,1) red-black Gauss-Seidel (Algorithm 1's cycle)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)

@@ -26,10 +26,23 @@ class SolverConfig:
         return self.omega_num / float(1 << self.omega_log2den)
 
 
-def config_for(name: str, L_max: int, arith: int = 0) -> SolverConfig:
+def config_for(name: str, L_max: int, arith: int = 0, smoother: int = 0) -> SolverConfig:
     """Widths and cycle of the standard workloads (2-D: Table 2 Poisson 2D p=1;
-    3-D: found by the Sec. 7.1 search on the manufactured 3-D problem)."""
+    3-D: found by the Sec. 7.1 search on the manufactured 3-D problem).
+
+    smoother = 1 gives the V(0,1) cycle with one red-black Gauss-Seidel sweep
+    (Algorithm 1's cycle) at the same widths and N: omega = 1 in 2-D (plain
+    Gauss-Seidel); in 3-D omega = 3/4, so that the point factor omega/6 is
+    dyadic and the exact cycle stays exact."""
     dim = 2 if ("2d" in name) else 3
+    if smoother:
+        if name.startswith("diffusion"):
+            raise ValueError("red-black Gauss-Seidel is built for the Poisson problem")
+        cfg = config_for(name, L_max, arith)
+        cfg.smoother, cfg.nu1, cfg.nu2 = 1, 0, 1
+        if dim == 2:
+            cfg.omega_num, cfg.omega_log2den = 1, 0
+        return cfg
     if name.startswith("diffusion"):
         # rough coefficient (k over e^-3..e^3): Jacobi V(2,2) contracts by about
         # 1/2 per iteration, so more IR iterations than for Poisson

@@ -233,14 +233,16 @@ enum SweepMode {
   SW_UP_CORR,        // last up-sweep on the finest level: u~ += y~' (y~' not stored)
   SW_UP_CORR_UH,     // ... and u^_l for the next FMG level
   SW_UP_CORR_W_UH,   // last up-sweep below the finest level: u~ += y~', w_l, u^_l
+  SW_UP0,            // first up-sweep from y~ = 0 (red half-sweep of V(0,1)): operand P w_(l-1)
 };
 
 template <int M>
 struct SwF {
   static constexpr bool fixed = M != SW_GENERIC;
+  static constexpr bool y = M != SW_UP0;
   static constexpr bool z = M >= SW_UP;
-  static constexpr bool wy = M == SW_DOWN || M == SW_UP;
-  static constexpr bool corr = M >= SW_UP_CORR;
+  static constexpr bool wy = M == SW_DOWN || M == SW_UP || M == SW_UP0;
+  static constexpr bool corr = M >= SW_UP_CORR && M <= SW_UP_CORR_W_UH;
   static constexpr bool uh = M == SW_UP_CORR_UH || M == SW_UP_CORR_W_UH;
   static constexpr bool w = M == SW_UP_CORR_W_UH;
 };
@@ -264,7 +266,7 @@ struct SweepBody {
   uint32_t *pk;
 
   // options: compile-time for the fixed shapes (y~ present), run-time otherwise
-  __device__ __forceinline__ bool HY() const { return SwF<M>::fixed ? true : (bool)a.has_y; }
+  __device__ __forceinline__ bool HY() const { return SwF<M>::fixed ? SwF<M>::y : (bool)a.has_y; }
   __device__ __forceinline__ bool HZ() const { return SwF<M>::fixed ? SwF<M>::z : (bool)a.has_z; }
   __device__ __forceinline__ bool WY() const { return SwF<M>::fixed ? SwF<M>::wy : (bool)a.write_y; }
   __device__ __forceinline__ bool CORR() const { return SwF<M>::fixed ? SwF<M>::corr : (bool)a.corr; }
@@ -388,7 +390,7 @@ struct SweepBody {
 template <int DIM, int M>
 __global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
   using F = SwF<M>;
-  const bool has_y = F::fixed ? true : (bool)a.has_y, has_z = F::fixed ? F::z : (bool)a.has_z;
+  const bool has_y = F::fixed ? F::y : (bool)a.has_y, has_z = F::fixed ? F::z : (bool)a.has_z;
   const bool write_y = F::fixed ? F::wy : (bool)a.write_y, corr = F::fixed ? F::corr : (bool)a.corr;
   const bool write_uh = F::fixed ? F::uh : (bool)a.write_uh;
   __shared__ SmemTile sm;
@@ -863,6 +865,8 @@ static void launch_sweep_dim(const SweepArgs &a, cudaStream_t st) {
     if (!a.corr && a.write_y && !a.write_w && !a.write_uh) m = a.has_z ? SW_UP : SW_DOWN;
     else if (a.corr && a.has_z && !a.write_y && !a.write_w) m = a.write_uh ? SW_UP_CORR_UH : SW_UP_CORR;
     else if (a.corr && a.has_z && !a.write_y && a.write_w && a.write_uh) m = SW_UP_CORR_W_UH;
+  } else if (a.has_z && a.write_y && !a.corr && !a.write_w && !a.write_uh) {
+    m = SW_UP0;
   }
   switch (m) {
     case SW_DOWN: k_sweep<DIM, SW_DOWN><<<grid, b, 0, st>>>(a); break;
@@ -870,6 +874,7 @@ static void launch_sweep_dim(const SweepArgs &a, cudaStream_t st) {
     case SW_UP_CORR: k_sweep<DIM, SW_UP_CORR><<<grid, b, 0, st>>>(a); break;
     case SW_UP_CORR_UH: k_sweep<DIM, SW_UP_CORR_UH><<<grid, b, 0, st>>>(a); break;
     case SW_UP_CORR_W_UH: k_sweep<DIM, SW_UP_CORR_W_UH><<<grid, b, 0, st>>>(a); break;
+    case SW_UP0: k_sweep<DIM, SW_UP0><<<grid, b, 0, st>>>(a); break;
     default: k_sweep<DIM, SW_GENERIC><<<grid, b, 0, st>>>(a); break;
   }
 }

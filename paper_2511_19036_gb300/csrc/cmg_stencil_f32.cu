@@ -340,14 +340,16 @@ enum SweepModeF {
   SF_UP_CORR,       // last up-sweep on the finest level: u~ += y~'
   SF_UP_CORR_UH,    // ... and u^_l
   SF_UP_CORR_W_UH,  // below the finest level: u~ += y~', w_l, u^_l
+  SF_UP0,           // first up-sweep from y~ = 0 (red half-sweep of V(0,1)): operand z
 };
 
 template <int M>
 struct SfF {
   static constexpr bool fixed = M != SF_GENERIC;
+  static constexpr bool y = M != SF_UP0;
   static constexpr bool z = M >= SF_UP;
-  static constexpr bool wy = M == SF_DOWN || M == SF_UP;
-  static constexpr bool corr = M >= SF_UP_CORR;
+  static constexpr bool wy = M == SF_DOWN || M == SF_UP || M == SF_UP0;
+  static constexpr bool corr = M >= SF_UP_CORR && M <= SF_UP_CORR_W_UH;
   static constexpr bool uh = M == SF_UP_CORR_UH || M == SF_UP_CORR_W_UH;
   static constexpr bool w = M == SF_UP_CORR_W_UH;
 };
@@ -367,7 +369,7 @@ struct SweepBodyF {
   MetaAcc my, mu;
   uint32_t *pk;
 
-  __device__ __forceinline__ bool HY() const { return SfF<M>::fixed ? true : (bool)a.has_y; }
+  __device__ __forceinline__ bool HY() const { return SfF<M>::fixed ? SfF<M>::y : (bool)a.has_y; }
   __device__ __forceinline__ bool HZ() const { return SfF<M>::fixed ? SfF<M>::z : (bool)a.has_z; }
   __device__ __forceinline__ bool WY() const { return SfF<M>::fixed ? SfF<M>::wy : (bool)a.write_y; }
   __device__ __forceinline__ bool CORR() const { return SfF<M>::fixed ? SfF<M>::corr : (bool)a.corr; }
@@ -472,7 +474,7 @@ struct SweepBodyF {
 template <int DIM, int M, bool COEF>
 __global__ void __launch_bounds__(NT, CMG_SWEEP_F32_MINB) k_sweep_f32(SweepArgs a) {
   using F = SfF<M>;
-  const bool has_y = F::fixed ? true : (bool)a.has_y, has_z = F::fixed ? F::z : (bool)a.has_z;
+  const bool has_y = F::fixed ? F::y : (bool)a.has_y, has_z = F::fixed ? F::z : (bool)a.has_z;
   const bool write_y = F::fixed ? F::wy : (bool)a.write_y, corr = F::fixed ? F::corr : (bool)a.corr;
   const bool write_uh = F::fixed ? F::uh : (bool)a.write_uh;
   __shared__ SmemF sm;
@@ -709,6 +711,14 @@ void launch_sweep_f32_dim(const SweepArgs &a, cudaStream_t st) {
     if (!a.corr && a.write_y && !a.write_w && !a.write_uh) m = a.has_z ? SF_UP : SF_DOWN;
     else if (a.corr && a.has_z && !a.write_y && !a.write_w) m = a.write_uh ? SF_UP_CORR_UH : SF_UP_CORR;
     else if (a.corr && a.has_z && !a.write_y && a.write_w && a.write_uh) m = SF_UP_CORR_W_UH;
+  } else if (!COEF && a.has_z && a.write_y && !a.corr && !a.write_w && !a.write_uh) {
+    m = SF_UP0;  // red-black smoothing (Poisson only)
+  }
+  if constexpr (!COEF) {
+    if (m == SF_UP0) {
+      k_sweep_f32<DIM, SF_UP0, COEF><<<grid, b, 0, st>>>(a);
+      return;
+    }
   }
   switch (m) {
     case SF_DOWN: k_sweep_f32<DIM, SF_DOWN, COEF><<<grid, b, 0, st>>>(a); break;

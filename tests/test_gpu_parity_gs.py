@@ -25,10 +25,7 @@ def cmg():
 
 def make_pair(cmg, name, Lmax, arith=0, **over):
     prob = P.make_problem(name, Lmax)
-    cfg = cmg.config_for(name, Lmax, arith=arith)
-    cfg.smoother, cfg.nu1, cfg.nu2 = 1, 0, 1
-    if prob.dim == 2:
-        cfg.omega_num, cfg.omega_log2den = 1, 0
+    cfg = cmg.config_for(name, Lmax, arith=arith, smoother=1)
     for k, v in over.items():
         setattr(cfg, k, v)
     s = cmg.Solver(cfg)
