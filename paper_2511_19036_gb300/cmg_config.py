@@ -31,9 +31,11 @@ def config_for(name: str, L_max: int, arith: int = 0, smoother: int = 0) -> Solv
     3-D: found by the Sec. 7.1 search on the manufactured 3-D problem).
 
     smoother = 1 gives the V(0,1) cycle with one red-black Gauss-Seidel sweep
-    (Algorithm 1's cycle) at the same widths and N: omega = 1 in 2-D (plain
-    Gauss-Seidel); in 3-D omega = 3/4, so that the point factor omega/6 is
-    dyadic and the exact cycle stays exact."""
+    (Algorithm 1's cycle): in 2-D omega = 1 (plain Gauss-Seidel) at Table 2's
+    widths and N, which are the paper's values for this cycle; in 3-D omega =
+    3/4, so that the point factor omega/6 is dyadic and the exact cycle stays
+    exact, with b2 one bit wider than for Jacobi V(2,2) (the cheapest widths
+    and N found to meet the Sec. 7.1 criterion on the manufactured problem)."""
     dim = 2 if ("2d" in name) else 3
     if smoother:
         if name.startswith("diffusion"):
@@ -42,6 +44,8 @@ def config_for(name: str, L_max: int, arith: int = 0, smoother: int = 0) -> Solv
         cfg.smoother, cfg.nu1, cfg.nu2 = 1, 0, 1
         if dim == 2:
             cfg.omega_num, cfg.omega_log2den = 1, 0
+        else:
+            cfg.b2 = 4
         return cfg
     if name.startswith("diffusion"):
         # rough coefficient (k over e^-3..e^3): Jacobi V(2,2) contracts by about
