@@ -146,6 +146,22 @@ def oracle_fmg_rate(prob_name: str, L: int, cfg, max_seconds: float = 30.0):
     return dofs / dt, dt, dofs
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The job's time is the slowest rank's (x on one rank; all ranks get it)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, dofs_per_rank: int, seconds: float) -> float:
+    """Whole-job DoF/s: every rank solves its own replica of dofs_per_rank unknowns
+    (weak scaling), all of them within `seconds` (the maximum over ranks)."""
+    return world * dofs_per_rank / seconds
+
+
 def smoother_of(args, prob_name: str) -> int:
     # red-black Gauss-Seidel is built for the Poisson problem
     return 1 if args.smoother == "rbgs" and not prob_name.startswith("diffusion") else 0
@@ -249,14 +265,10 @@ def run_gpu(args, wl):
     ev1.record(stream)
     barrier()
     clocks = clk.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     ms_step = ms_total / args.steps
     dofs = reports[0]["dofs"]
-    value = world * dofs / (ms_step * 1e-3)
+    value = job_rate(world, dofs, ms_step * 1e-3)
 
     # dominant kernel: the finest-level Jacobi sweep (events on the solver's stream)
     sw_ms = sum(r["sweep_ms_total"] for r in reports)
@@ -307,11 +319,7 @@ def run_gpu(args, wl):
             assert st == 0
         barrier()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = statistics.median(e2e_times)
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(statistics.median(e2e_times), dist, "cuda")
 
     # discretization-error check on sampled planes of the decoded solution
     n = (1 << Lmax) - 1
@@ -402,7 +410,7 @@ def run_gpu(args, wl):
         "kernels_last_step": kernels,
         "storage_model": storage,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * dofs / e2e_s, "unit": "DoF/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(world, dofs, e2e_s), "unit": "DoF/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -472,11 +480,7 @@ def run_adjoint(args, wl):
     ev1.record()
     barrier()
     clocks = clk.stop()
-    ms_step = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
     # end to end: H2D of g, gradient D2H, inside the timed region
     dm_host = torch.empty(dm.numel(), dtype=torch.float32).pin_memory()
     e2e = []
@@ -488,7 +492,7 @@ def run_adjoint(args, wl):
         dm_host.copy_(dm.reshape(-1), non_blocking=True)
         barrier()
         e2e.append(time.perf_counter() - t0)
-    e2e_s = statistics.median(e2e)
+    e2e_s = max_over_ranks(statistics.median(e2e), dist, "cuda")
     # the dominant kernel, from one timed forward solve of the same problem
     solver = cmg.Solver(cfg, timing=True)
     solver.set_coefficient(k)
@@ -523,7 +527,7 @@ def run_adjoint(args, wl):
                "kind": "oracle", "sample": "oracle forward + adjoint compact FMG + gradient at L_max=%d (%d DoF), %.1f s"
                % (Ls, sd, dt)}
     line = {
-        "metric": "adjoint gradient (forward + adjoint compact FMG + gradient) DoF/s", "value": world * dofs / (ms_step * 1e-3),
+        "metric": "adjoint gradient (forward + adjoint compact FMG + gradient) DoF/s", "value": job_rate(world, dofs, ms_step * 1e-3),
         "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 cycle + f64 refinement", "data": "synthetic",
@@ -535,7 +539,7 @@ def run_adjoint(args, wl):
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": None,
                      "peak_kind": peak_kind},
         "cpu_baseline": cpu,
-        "e2e": {"value": world * dofs / e2e_s, "unit": "DoF/s", "h2d_bytes_per_step": dofs * 8,
+        "e2e": {"value": job_rate(world, dofs, e2e_s), "unit": "DoF/s", "h2d_bytes_per_step": dofs * 8,
                 "d2h_bytes_per_step": dm.numel() * 4},
         "gpu_launches": int(2 * rep["launches"] + 1),
         "clocks": clocks,
