@@ -49,11 +49,22 @@ constexpr int TMAXP = 8;  // right-hand-side terms with per-thread products in s
 #endif
 
 // ------------------------------------------------------------------ the z-march
-struct SmemTile {
-  long long Fs[2][PLANE];   // in-plane operand, double-buffered
-  long long ring[4 * CRX];  // coarse ring of the operand's P_l t
+// V: the integer type of the operand (int64, or int32 where the CTA's
+// footprint bounds prove |2d F| + |neighbours| < 2^31 on the operand grid)
+template <class V>
+struct SmemT {
+  V Fs[2][PLANE];           // in-plane operand, double-buffered
+  V ring[4 * CRX];          // coarse ring of the operand's P_l t
   long long ringu[4 * CRX]; // coarse ring of P_l u^_(l-1)
 };
+using SmemTile = SmemT<long long>;
+union SmemAny {  // one shared buffer for either operand width
+  SmemT<long long> w64;
+  SmemT<int> w32;
+};
+
+// the 32-bit march is exact when |S| < 2^(MF + 4) fits: |F| < 2^MF on grid GF
+__device__ __forceinline__ bool narrow_operand(int GF, int MF) { return GF < GRID_NONE / 2 && MF + 4 - GF <= 30; }
 
 struct MarchIn {
   Sec s;         // operand section (if has_s)
@@ -72,9 +83,10 @@ struct MarchIn {
 // the CTA calls it.  A body with kRaw = true gets body.out_raw(k, Pc, Fm, F0,
 // Fp, s0) instead: Pc points at the node in the plane buffer (neighbours
 // Pc[-1], Pc[+1], Pc[-PW], Pc[+PW]), Fm / Fp are the z-neighbours.
-template <int DIM, class Body>
-__device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T, const MarchIn &in, SmemTile &sm,
+template <int DIM, class V, class Body>
+__device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T, const MarchIn &in, SmemT<V> &sm,
                                       Body &body) {
+  static_assert(sizeof(V) == 8 || !Body::kRaw, "raw bodies read 64-bit plane buffers");
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
   const int Ws = in.has_s ? in.s.W : 1;
   const Slot own = make_slot(g, Ws, T.x0 + lane, T.j0 + ty, ty + 1, lane + 1, T);
@@ -102,8 +114,8 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
   auto raw_at = [&](const Slot &sl, int kf) -> Raw {
     return raw_load(in.s, kf * pb + sl.bip, sl.cp, has_s && sl.ok && (unsigned)kf < (unsigned)g.nz);
   };
-  auto F_at = [&](const Slot &sl, const Raw &r, int kf, long long &sv) -> long long {
-    sv = has_s ? raw_val(r, sl.cp.boff, Ws, in.GF) : 0;
+  auto F_at = [&](const Slot &sl, const Raw &r, int kf, V &sv) -> V {
+    sv = has_s ? raw_val_as<V>(r, sl.cp.boff, Ws, in.GF) : 0;
     if (!in.has_t) return sv;
     int za, zb;
     zparents<DIM>(kf, za, zb);
@@ -128,18 +140,18 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
     Raw h0 = r0;
     if (has_h) h0 = raw_at(hal, 0);
     __syncthreads();
-    long long s0, sh;
-    const long long F0 = F_at(own, r0, 0, s0);
+    V s0, sh;
+    const V F0 = F_at(own, r0, 0, s0);
     sm.Fs[0][own.sm] = F0;
     if (has_h) sm.Fs[0][hal.sm] = F_at(hal, h0, 0, sh);
     __syncthreads();
-    const long long *P = sm.Fs[0];
+    const V *P = sm.Fs[0];
     body.advance();
     if constexpr (Body::kRaw) {
       body.out_raw(0, P + own.sm, 0, F0, 0, s0);
     } else {
-      const long long S = 4 * F0 - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
-      body.out(0, S, s0, F0, pu_at(0));
+      const V S = 4 * F0 - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
+      body.out(0, (long long)S, (long long)s0, (long long)F0, pu_at(0));
     }
     return;
   }
@@ -163,7 +175,7 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
   if (has_h) hn = raw_at(hal, T.k0 + 1);
   body.prefetch(T.k0);
   __syncthreads();
-  long long sx, s0, Fm, F0;
+  V sx, s0, Fm, F0;
   Fm = F_at(own, rm, T.k0 - 1, sx);
   F0 = F_at(own, r0, T.k0, s0);
   sm.Fs[T.k0 & 1][own.sm] = F0;
@@ -182,20 +194,19 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
     if (k + 2 <= T.k1) rn2 = raw_at(own, k + 2);
     if (has_h && k + 2 < T.k1) hn2 = raw_at(hal, k + 2);
     __syncthreads();  // plane k complete in Fs[k & 1]; ring planes for k + 1 staged
-    long long sp;
-    const long long Fp = F_at(own, rn, k + 1, sp);
+    V sp;
+    const V Fp = F_at(own, rn, k + 1, sp);
     if (k + 1 < T.k1) {
-      long long* nxt = sm.Fs[(k + 1) & 1];
+      V *nxt = sm.Fs[(k + 1) & 1];
       nxt[own.sm] = Fp;
       if (has_h) nxt[hal.sm] = F_at(hal, hn, k + 1, sx);
     }
-    const long long *P = sm.Fs[k & 1];
+    const V *P = sm.Fs[k & 1];
     if constexpr (Body::kRaw) {
       body.out_raw(k, P + own.sm, Fm, F0, Fp, s0);
     } else {
-      const long long S =
-          6 * F0 - Fm - Fp - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
-      body.out(k, S, s0, F0, pu_at(k));
+      const V S = 6 * F0 - Fm - Fp - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
+      body.out(k, (long long)S, (long long)s0, (long long)F0, pu_at(k));
     }
     if (stage) {
       if (in.has_t) stage_store(st0, sm.ring, cs, in.G1t, tid);
@@ -393,7 +404,7 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
   const bool has_y = F::fixed ? F::y : (bool)a.has_y, has_z = F::fixed ? F::z : (bool)a.has_z;
   const bool write_y = F::fixed ? F::wy : (bool)a.write_y, corr = F::fixed ? F::corr : (bool)a.corr;
   const bool write_uh = F::fixed ? F::uh : (bool)a.write_uh;
-  __shared__ SmemTile sm;
+  __shared__ SmemAny sm;
   __shared__ uint32_t pk[TY][33];
   __shared__ int smy[2], smu[2], smb[6];
   const Geo g = a.g;
@@ -441,8 +452,12 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
   in.GF = GF;
   in.G1t = GF + 1;
   in.G1u = b.G1u;
-  if (in.has_s || in.has_t || in.has_u) march<DIM>(g, a.gc, T, in, sm, b);
-  else march_none(T, DIM == 2, b);
+  if (in.has_s || in.has_t || in.has_u) {
+    if (narrow_operand(GF, MF)) march<DIM>(g, a.gc, T, in, sm.w32, b);
+    else march<DIM>(g, a.gc, T, in, sm.w64, b);
+  } else {
+    march_none(T, DIM == 2, b);
+  }
   ovf_flush(b.ovf, a.err, 102);
   if (write_y) meta_flush(b.my, a.y_out.meta, smy);
   if (corr) meta_flush(b.mu, a.u_out.meta, smu);
@@ -582,7 +597,7 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   const bool first_sweep = M == RS_FIRST ? true : (bool)a.first_sweep;
   const bool write_t = M == RS_FIRST ? false : (bool)a.write_t;
   const bool has_uhc = M == RS_FIRST ? true : (bool)a.has_uhc;
-  __shared__ SmemTile sm;
+  __shared__ SmemAny sm;
   __shared__ RhsSmem rs;
   __shared__ uint32_t pk[TY][33];
   __shared__ int smr[2], smy[2], smt[2], smb[6];
@@ -650,7 +665,8 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   in.GF = GF;
   in.G1t = GF + 1;
   in.G1u = 0;
-  march<DIM>(g, a.gc, T, in, sm, b);
+  if (narrow_operand(GF, MF)) march<DIM>(g, a.gc, T, in, sm.w32, b);
+  else march<DIM>(g, a.gc, T, in, sm.w64, b);
   ovf_flush(b.ovf, a.err, 202);
   meta_flush(b.mr, a.r_out.meta, smr);
   if (first_sweep) meta_flush(b.my, a.y_out.meta, smy);
@@ -809,7 +825,7 @@ struct RestrictBody {
 
 template <int DIM>
 __global__ void __launch_bounds__(NT, CMG_RESTRICT_MINB) k_restrict(RestrictArgs a) {
-  __shared__ SmemTile sm;
+  __shared__ SmemAny sm;
   __shared__ int smb[6];
   const Geo g = a.g;
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
@@ -846,8 +862,9 @@ __global__ void __launch_bounds__(NT, CMG_RESTRICT_MINB) k_restrict(RestrictArgs
   in.GF = GF;
   in.G1t = 0;
   in.G1u = 0;
-  if (in.has_s) march<DIM>(g, a.gc, T, in, sm, b);
-  else march_none(T, DIM == 2, b);
+  if (!in.has_s) march_none(T, DIM == 2, b);
+  else if (narrow_operand(GF, MF)) march<DIM>(g, a.gc, T, in, sm.w32, b);
+  else march<DIM>(g, a.gc, T, in, sm.w64, b);
   ovf_flush(b.ovf, a.err, 302);
 }
 

@@ -65,6 +65,19 @@ __device__ __forceinline__ long long raw_val(const Raw &r, int boff, int W, int 
   return (long long)((unsigned long long)(long long)raw_code(r, boff, W) << (r.e - W + 1 - G));
 }
 
+// the same value as a 32-bit integer, for a caller that proved |value| < 2^31
+// on grid G (then the shift is below 31)
+__device__ __forceinline__ int raw_val32(const Raw &r, int boff, int W, int G) {
+  if (r.e == -128) return 0;
+  return (int)((unsigned)raw_code(r, boff, W) << (r.e - W + 1 - G));
+}
+
+template <class V>
+__device__ __forceinline__ V raw_val_as(const Raw &r, int boff, int W, int G) {
+  if constexpr (sizeof(V) == 4) return raw_val32(r, boff, W, G);
+  else return raw_val(r, boff, W, G);
+}
+
 // Left shift for the paths whose static range check passed: there every shift
 // of a nonzero value is below 63, and a shift of 64 or more only meets a zero
 // (an operand whose footprint is all zero), so the count is taken mod 64.
@@ -136,7 +149,8 @@ __device__ __forceinline__ void zparents(int kf, int &za, int &zb) {
 }
 
 // (P_l t) at a slot from a ring, on the ring's grid minus one
-__device__ __forceinline__ long long ring_p(const long long *ring, const Slot &s, int za, int zb) {
+template <class V>
+__device__ __forceinline__ V ring_p(const V *ring, const Slot &s, int za, int zb) {
   return ring[(za & 3) * CRX + s.oa] + ring[(zb & 3) * CRX + s.ob];
 }
 
@@ -172,8 +186,11 @@ __device__ __forceinline__ void stage_load(Stager &s, const Tmp &t, const Geo &g
   }
 }
 
-__device__ __forceinline__ void stage_store(const Stager &s, long long *ring, int c, int G1, int tid) {
-  if (s.on) ring[(c & 3) * CRX + tid] = (s.gb & 0xff) ? shl_fast(s.v, (s.gb >> 8) - G1) : 0;
+// the staged value on the ring's grid G1 (a 32-bit ring only where the caller
+// proved every value below 2^31 on G1)
+template <class V>
+__device__ __forceinline__ void stage_store(const Stager &s, V *ring, int c, int G1, int tid) {
+  if (s.on) ring[(c & 3) * CRX + tid] = (V)((s.gb & 0xff) ? shl_fast(s.v, (s.gb >> 8) - G1) : 0);
 }
 
 // ------------------------------------------------------------------ footprint bounds

@@ -218,3 +218,75 @@ def test_solve_without_rhs_is_rejected(cmg):
     with pytest.raises(cmg.CmgError) as ei:
         s.fmg_solve()
     assert ei.value.status == cmg.EINVAL
+
+
+# ---------------------------------------------------------------- wide operands
+def _rows(x, n, npts):
+    rows = np.zeros((npts // n, 32 * ((n + 31) // 32)))
+    rows[:, :n] = x.reshape(npts // n, n)
+    return rows.ravel()
+
+
+@pytest.mark.parametrize("name,L,smoother", [("poisson3d_manufactured", 5, 0), ("poisson3d_manufactured", 5, 1),
+                                             ("poisson2d_manufactured", 6, 0), ("poisson2d_manufactured", 6, 1)])
+def test_cycle_on_operands_wider_than_32_bits(cmg, name, L, smoother):
+    """Sections whose rows are scaled over 16-36 binary orders (u~_L before the
+    residual, r~_L before the down-leg, y~_L before the finest up-sweep): the
+    stencil kernels meet footprints whose exact operands need more than 31 bits
+    (the 64-bit march) next to footprints that fit (the 32-bit march).  The
+    magnitudes keep every oracle operation exact; the bar is bit-exact."""
+    prob = P.make_problem(name, L)
+    cfg = cmg.config_for(name, L, smoother=smoother)
+    s = cmg.Solver(cfg)
+    s.set_rhs(prob.tables, prob.scale_exp)
+    o = oracle.Oracle.for_problem(prob, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1, nu2=cfg.nu2,
+                                  omega=cfg.omega, smoother=smoother)
+    s.start()
+    o.start()
+    for _ in range(L - 1):
+        s.prolongate()
+        o.next_level()
+        for _ in range(cfg.N_ir):
+            s.ir_iteration()
+            o.ir_iteration()
+    n = (1 << L) - 1
+    npts = n ** prob.dim
+    rng = np.random.default_rng(5)
+
+    def put(which_g, which_o, seed, lo, hi):
+        W = o.width(which_o, L)
+        x = random_block_values(npts, seed=seed, spread_bits=8) * np.repeat(
+            2.0 ** rng.integers(lo, hi, size=npts // n).astype(np.float64), n)
+        words, e, st = oracle.encode(_rows(x, n, npts), W)
+        assert st == 0
+        s.set_section(which_g, L, W, words, e)
+        o.set_section(which_o, L, W, words, e)
+
+    put(cmg.SEC_U, oracle.U, 17, -38, -22)
+    s.residual()
+    o.residual()
+    same_section(cmg, s, o, cmg.SEC_R, oracle.R, L, "residual")
+    put(cmg.SEC_R, oracle.R, 23, -50, -14)
+    for l in range(L, 1, -1):
+        s.down(l)
+        o.down(l)
+        same_section(cmg, s, o, cmg.SEC_RC, oracle.RC, l - 1, "restrict")
+    s.coarse()
+    o.coarse()
+    for l in range(2, L):
+        s.up(l)
+        o.up(l)
+        same_section(cmg, s, o, cmg.SEC_Y, oracle.Y, l, "up")
+    put(cmg.SEC_Y, oracle.Y, 29, -50, -14)
+    s.up(L)
+    o.up(L)
+    same_section(cmg, s, o, cmg.SEC_Y, oracle.Y, L, "up, finest")
+    s.correct()
+    o.correct()
+    for l in range(1, L + 1):
+        same_section(cmg, s, o, cmg.SEC_U, oracle.U, l, "correct")
+    s.ir_iteration()
+    o.ir_iteration()
+    for l in range(1, L + 1):
+        same_section(cmg, s, o, cmg.SEC_U, oracle.U, l, "fused iteration")
+    assert o.status == 0 and o.inexact == 0
