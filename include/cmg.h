@@ -100,7 +100,9 @@ typedef struct {
   double alg_bytes;       /* algorithmic bytes moved by all kernels (model) */
   double persistent_bits; /* compact u~, r, y~ (x2) storage at L_max, all levels,
                              mantissas + exponents + padding */
-  double temp_bytes;      /* int64 temporaries (levels <= L_max-1) */
+  double temp_bytes;      /* int64 temporaries (levels <= L_max-1) and, with
+                             nu1 = 0, the restriction chain's t^ sections
+                             ((p+1) L_max + b1 bits, every level) */
   /* dominant kernel statistics (finest-level Jacobi sweep); valid when the
    * context was created with timing enabled (cmg_set_timing). */
   double sweep_ms_total;

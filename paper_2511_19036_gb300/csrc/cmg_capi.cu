@@ -1019,6 +1019,8 @@ extern "C" cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *rep) {
       Geo g = make_geo(d, l);
       bits += (double)g.nblocks * (32.0 * (Wu(ctx, l, Lm) + 3 * Wr(ctx, l, Lm)) + 8.0 * 4);
       if (l < Lm) tb += 3.0 * 8.0 * g.nz * g.n * g.R;
+      // without pre-smoothing: the restriction chain's t^ section on every level
+      if (ctx->P.nu1 == 0) tb += (double)g.nblocks * (4.0 * (ctx->P.k_u * Lm + ctx->P.b1) + 1.0);
     }
     rep->persistent_bits = bits;
     rep->temp_bytes = tb;
