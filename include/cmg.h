@@ -102,7 +102,7 @@ typedef struct {
                              mantissas + exponents + padding */
   double temp_bytes;      /* int64 temporaries (levels <= L_max-1) and, with
                              nu1 = 0, the restriction chain's t^ sections
-                             ((p+1) L_max + b1 bits, every level) */
+                             ((p+1) L_max + b1 bits, levels <= L_max-1) */
   /* dominant kernel statistics (finest-level Jacobi sweep); valid when the
    * context was created with timing enabled (cmg_set_timing). */
   double sweep_ms_total;

@@ -317,7 +317,9 @@ extern "C" cmg_status cmg_create(const cmg_params *p, void *stream, cmg_ctx **ou
     if (l < p->L_max && (r = alloc_sec(ctx, v.rc, g, wr)) != CMG_OK) break;
     if ((r = alloc_sec(ctx, v.y[0], g, wr)) != CMG_OK) break;
     if ((r = alloc_sec(ctx, v.y[1], g, wr)) != CMG_OK) break;
-    if (p->nu1 == 0 && (r = alloc_sec(ctx, v.t, g, p->k_u * p->L_max + p->b1)) != CMG_OK) break;
+    // t^_l of the restriction chain (no pre-smoothing): the finest level restricts
+    // its t^ inside the residual kernel and needs none
+    if (p->nu1 == 0 && l < p->L_max && (r = alloc_sec(ctx, v.t, g, p->k_u * p->L_max + p->b1)) != CMG_OK) break;
     if (l < p->L_max || l == 1) {
       size_t nt = (size_t)g.nz * g.n * g.R;
       chk(cudaMalloc(&v.uh, nt * 8));
@@ -541,18 +543,24 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
     v.ycur = 0;
     v.y_zero = false;
   }
-  // without pre-smoothing, t^ (Table 1 width (p+1)L + b1) feeds the restriction chain
+  // without pre-smoothing, t^ (Table 1 width (p+1)L + b1) feeds the restriction
+  // chain; on level L the kernel restricts it at once (R t^_L into acc_(L-1))
   const bool chain = ctx->P.nu1 == 0 && L > 1;
   const int Wt = ctx->P.k_u * L + ctx->P.b1;
-  a.write_t = chain;
   if (chain) {
-    v.t.W = Wt;
-    if ((s = fresh_meta(ctx, v.t))) return s;
-    a.t_out = sec_of(v.t);
+    Level &c = LV(ctx, L - 1);
+    a.fuse_restrict = 1;
+    a.t_out.W = Wt;  // the rounding width of t^_L, which is not stored
+    if ((s = fresh_tmp_meta(ctx, c.accmeta))) return s;
+    a.racc = tmp_of(c.acc, nullptr, c.accmeta);
+    for (int l = 1; l <= L; l++) {
+      a.umeta[l] = LV(ctx, l).u.meta;
+      a.uW[l] = LV(ctx, l).u.W;
+    }
   }
   a.err = ctx->err;
   double bytes = sec_bytes(v.g, v.u.W) + (L > 1 ? tmp_bytes(a.gc) : 0) + sec_bytes(v.g, v.r.W) +
-                 (first_sweep ? sec_bytes(v.g, v.r.W) : 0) + (chain ? sec_bytes(v.g, Wt) : 0);
+                 (first_sweep ? sec_bytes(v.g, v.r.W) : 0) + (chain ? 2 * tmp_bytes(a.gc) : 0);
   ev_begin(ctx, kstat(ctx, CMG_KIND_RESIDUAL, L));
   if (diff) launch_residual_diffusion(d, a, ctx->st);
   else launch_residual(d, a, ctx->st);
@@ -561,18 +569,20 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
   if (chain) {  // t^_l = round(R t^_(l+1)), r_l = round(t^_l) (Algorithm 2)
     for (int l = L; l >= 2; l--) {
       Level &f = LV(ctx, l), &c = LV(ctx, l - 1);
-      RestrictArgs ra{};
-      ra.g = f.g;
-      ra.gc = c.g;
-      ra.has_y = 0;
-      ra.rc = sec_of(f.t);
-      if ((s = fresh_tmp_meta(ctx, c.accmeta))) return s;
-      ra.acc = tmp_of(c.acc, nullptr, c.accmeta);
-      ra.err = ctx->err;
-      ev_begin(ctx, kstat(ctx, CMG_KIND_RESTRICT, l));
-      launch_restrict(d, ra, ctx->st);
-      ev_end(ctx, kstat(ctx, CMG_KIND_RESTRICT, l), sec_bytes(f.g, Wt) + 2 * tmp_bytes(c.g));
-      if ((s = launched(ctx, sec_bytes(f.g, Wt) + 2 * tmp_bytes(c.g)))) return s;
+      if (l < L) {  // level L was restricted by the residual kernel
+        RestrictArgs ra{};
+        ra.g = f.g;
+        ra.gc = c.g;
+        ra.has_y = 0;
+        ra.rc = sec_of(f.t);
+        if ((s = fresh_tmp_meta(ctx, c.accmeta))) return s;
+        ra.acc = tmp_of(c.acc, nullptr, c.accmeta);
+        ra.err = ctx->err;
+        ev_begin(ctx, kstat(ctx, CMG_KIND_RESTRICT, l));
+        launch_restrict(d, ra, ctx->st);
+        ev_end(ctx, kstat(ctx, CMG_KIND_RESTRICT, l), sec_bytes(f.g, Wt) + 2 * tmp_bytes(c.g));
+        if ((s = launched(ctx, sec_bytes(f.g, Wt) + 2 * tmp_bytes(c.g)))) return s;
+      }
       AccArgs b{};
       b.g = c.g;
       b.acc = tmp_of(c.acc, nullptr, c.accmeta);
@@ -1020,7 +1030,7 @@ extern "C" cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *rep) {
       bits += (double)g.nblocks * (32.0 * (Wu(ctx, l, Lm) + 3 * Wr(ctx, l, Lm)) + 8.0 * 4);
       if (l < Lm) tb += 3.0 * 8.0 * g.nz * g.n * g.R;
       // without pre-smoothing: the restriction chain's t^ section on every level
-      if (ctx->P.nu1 == 0) tb += (double)g.nblocks * (4.0 * (ctx->P.k_u * Lm + ctx->P.b1) + 1.0);
+      if (ctx->P.nu1 == 0 && l < Lm) tb += (double)g.nblocks * (4.0 * (ctx->P.k_u * Lm + ctx->P.b1) + 1.0);
     }
     rep->persistent_bits = bits;
     rep->temp_bytes = tb;

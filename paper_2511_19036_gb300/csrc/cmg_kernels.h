@@ -45,6 +45,13 @@ struct ResidArgs {
   Sec y_out;
   int write_t;         // also store t^_L at the width of Table 1 (no pre-smoothing)
   Sec t_out;
+  // no pre-smoothing: restrict t^_L here, R t^_L accumulated into racc (level
+  // L-1, padded layout) on one grid below every t^_L value, derived from the
+  // u~_l sections' metadata (umeta, uW for l = 1..L); the grid goes to racc.meta[0]
+  int fuse_restrict;
+  Tmp racc;
+  const int *umeta[16];
+  int uW[16];
   int c_num, c_exp, cbits;
   const float *kfield;  // diffusion: nodal k on the finest grid, boundary included
   int kN;               // 2^Lmax + 1 (the field is kN^dim, x fastest)

@@ -520,7 +520,8 @@ struct ResidBody {
   const Geo &g;
   const RhsSmem &rs;
   int GF, GA, Gt, Gcr, k0;
-  bool fast, rhs_sm;
+  int Gd;               // fused restriction: grid of R t^_L is Gd - 1
+  bool fast, rhs_sm, dfast;
   int bip, lane, ty, i, j;
   bool rowok, pt;
   bool ovf;
@@ -529,6 +530,7 @@ struct ResidBody {
 
   __device__ __forceinline__ bool FS() const { return M == RS_FIRST ? true : (bool)a.first_sweep; }
   __device__ __forceinline__ bool WT() const { return M == RS_FIRST ? false : (bool)a.write_t; }
+  __device__ __forceinline__ bool FR() const { return M == RS_FIRST ? false : (bool)a.fuse_restrict; }
   __device__ __forceinline__ void prefetch(int) {}
   __device__ __forceinline__ void advance() {}
 
@@ -589,6 +591,19 @@ struct ResidBody {
         mt.add(et);
       }
     }
+    if (FR()) {  // t^_L at the width of Table 1, restricted at once: R t^_L on Gd - 1
+      int et, st;
+      const int qt = encode_block(t, Gt, a.t_out.W, et, st, a.err);
+      const long long th = rounded_value(t, qt, st);  // on grid Gt >= Gd
+      long long d;
+      if (dfast) {
+        d = shl_fast(th, Gt - Gd);
+      } else {
+        d = shl_ck(th, Gt - Gd, ovf);
+        ck58(d, ovf);
+      }
+      if (pt && d) scatter_restrict<DIM>((unsigned long long *)a.racc.v, a.gc, i + 1, j + 1, k + 1, d);
+    }
   }
 };
 
@@ -642,6 +657,23 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   // the bound |t| < 2^Mt is loose (t is a residual, far below |f| + |A F|): when
   // it does not fit, every value is checked instead
   b.fast = Mt - Gt <= 62 && (!first_sweep || Mt + 1 + a.cbits - Gt <= 62);
+  b.Gd = 0;
+  b.dfast = true;
+  if (!first_sweep && a.fuse_restrict) {
+    // every operand grid of the level is at least min over l of (grid of u~_l) - (L - l):
+    // u^_l = u~_l + P u^_(l-1), and P halves the grid at most once per level
+    int Glo = GRID_NONE;
+    for (int l = 1; l <= g.l; l++) {
+      Sec s{};
+      s.meta = const_cast<int *>(a.umeta[l]);
+      s.W = a.uW[l];
+      const int G = sec_lsb(s);
+      if (G < GRID_NONE / 2) Glo = imin(Glo, G - (g.l - l));
+    }
+    b.Gd = imin(a.Gf, Glo < GRID_NONE / 2 ? Glo - sA : GRID_NONE);
+    if (tid == 0 && first_cta()) a.racc.meta[0] = b.Gd - 1;
+    b.dfast = Mt - b.Gd <= 57;
+  }
   b.rhs_sm = rhs_sm;
   b.lane = lane;
   b.ty = ty;
