@@ -146,6 +146,22 @@ def oracle_fmg_rate(prob_name: str, L: int, cfg, max_seconds: float = 30.0):
     return dofs / dt, dt, dofs
 
 
+def oracle_rate_one_thread(prob_name: str, L: int, cfg):
+    """The oracle's compact FMG on one host thread (a child process, since the
+    OpenMP thread count is fixed at start). Returns (DoF/s, seconds, dofs) or None."""
+    import subprocess
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, oracle; oracle.build(); "
+            "from paper_2511_19036_gb300.cmg_config import config_for; "
+            "cfg = config_for(%r, %d, arith=%d, smoother=%d); "
+            "print(json.dumps(bench.oracle_fmg_rate(%r, %d, cfg)))"
+            % (ROOT, prob_name, cfg.L_max, cfg.arith, cfg.smoother, prob_name, L))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return None
+    return tuple(json.loads(r.stdout.strip().splitlines()[-1]))
+
+
 def max_over_ranks(x: float, dist, device: str) -> float:
     """The job's time is the slowest rank's (x on one rank; all ranks get it)."""
     if dist is None:
@@ -306,19 +322,23 @@ def run_gpu(args, wl):
     out_e = [torch.empty(nb[i], dtype=torch.int8).pin_memory() for i in range(Lmax)]
     h2d = tab_pinned.numel() * 4
     d2h = sum(w.numel() * 4 + e.numel() for w, e in zip(out_w, out_e))
-    e2e_times = []
+    e2e_times, phases = [], []
     lib = cmg.lib()
     for it in range(max(1, min(args.steps, 3))):
         barrier()
         t0 = time.perf_counter()
         st = lib.cmg_set_rhs_separable(solver._h, prob.nterms, tab_pinned.data_ptr(), prob.scale_exp)
         assert st == 0
+        t1 = time.perf_counter()
         solver.fmg_solve()
+        t2 = time.perf_counter()
         for l in range(1, Lmax + 1):
             st = lib.cmg_get_section(solver._h, 0, l, out_w[l - 1].data_ptr(), out_e[l - 1].data_ptr())
             assert st == 0
         barrier()
-        e2e_times.append(time.perf_counter() - t0)
+        t3 = time.perf_counter()
+        e2e_times.append(t3 - t0)
+        phases.append((t1 - t0, t2 - t1, t3 - t2))
     e2e_s = max_over_ranks(statistics.median(e2e_times), dist, "cuda")
 
     # discretization-error check on sampled planes of the decoded solution
@@ -387,6 +407,11 @@ def run_gpu(args, wl):
         r, dt, sdofs = oracle_fmg_rate(prob_name, Ls, cfg)
         cpu = {"value": r, "unit": "DoF/s", "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
                "sample": "oracle compact FMG of the same problem at L_max=%d (%d DoF), %.1f s" % (Ls, sdofs, dt)}
+        if not diffusion:
+            one = oracle_rate_one_thread(prob_name, min(Ls, 7 if cfg.dim == 3 else 10), cfg)
+            if one:
+                cpu["single_core"] = {"value": one[0], "unit": "DoF/s", "cores": 1,
+                                      "sample": "the same at %d DoF, %.1f s" % (one[2], one[1])}
     launches = int(sum(r["launches"] for r in reports))
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
@@ -411,7 +436,8 @@ def run_gpu(args, wl):
         "storage_model": storage,
         "cpu_baseline": cpu,
         "e2e": {"value": job_rate(world, dofs, e2e_s), "unit": "DoF/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h,
+                "phases_ms": [[round(1e3 * x, 2) for x in p] for p in phases]},  # set_rhs, solve, D2H
         "gpu_launches": launches,
         "clocks": clocks,
     }
