@@ -550,7 +550,7 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
   if (chain) {
     Level &c = LV(ctx, L - 1);
     a.fuse_restrict = 1;
-    a.t_out.W = Wt;  // the rounding width of t^_L, which is not stored
+    a.Wt = Wt;  // the rounding width of t^_L, which is not stored
     if ((s = fresh_tmp_meta(ctx, c.accmeta))) return s;
     a.racc = tmp_of(c.acc, nullptr, c.accmeta);
     for (int l = 1; l <= L; l++) {

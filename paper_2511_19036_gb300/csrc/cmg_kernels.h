@@ -43,12 +43,12 @@ struct ResidArgs {
   Sec r_out;
   int first_sweep;     // also y~ = round(c r)
   Sec y_out;
-  int write_t;         // also store t^_L at the width of Table 1 (no pre-smoothing)
-  Sec t_out;
-  // no pre-smoothing: restrict t^_L here, R t^_L accumulated into racc (level
-  // L-1, padded layout) on one grid below every t^_L value, derived from the
-  // u~_l sections' metadata (umeta, uW for l = 1..L); the grid goes to racc.meta[0]
+  // no pre-smoothing: t^_L = round(t) at the width Wt of Table 1, restricted
+  // here: R t^_L accumulated into racc (level L-1, padded layout) on one grid
+  // below every t^_L value, derived from the u~_l sections' metadata (umeta,
+  // uW for l = 1..L); the grid goes to racc.meta[0]
   int fuse_restrict;
+  int Wt;
   Tmp racc;
   const int *umeta[16];
   int uW[16];

@@ -525,11 +525,10 @@ struct ResidBody {
   int bip, lane, ty, i, j;
   bool rowok, pt;
   bool ovf;
-  MetaAcc mr, my, mt;
+  MetaAcc mr, my;
   uint32_t *pk;
 
   __device__ __forceinline__ bool FS() const { return M == RS_FIRST ? true : (bool)a.first_sweep; }
-  __device__ __forceinline__ bool WT() const { return M == RS_FIRST ? false : (bool)a.write_t; }
   __device__ __forceinline__ bool FR() const { return M == RS_FIRST ? false : (bool)a.fuse_restrict; }
   __device__ __forceinline__ void prefetch(int) {}
   __device__ __forceinline__ void advance() {}
@@ -582,18 +581,9 @@ struct ResidBody {
         my.add(ey);
       }
     }
-    if (WT()) {  // t^_L at the width of Table 1, for the restriction chain
+    if (FR()) {  // t^_L at the width of Table 1 (Wt), restricted at once: R t^_L on Gd - 1
       int et, st;
-      const int qt = encode_block(t, Gt, a.t_out.W, et, st, a.err);
-      pack_block(qt, a.t_out.W, pk, a.t_out.words + (long long)blk * a.t_out.W);
-      if (lane == 0) {
-        a.t_out.exps[blk] = (int8_t)et;
-        mt.add(et);
-      }
-    }
-    if (FR()) {  // t^_L at the width of Table 1, restricted at once: R t^_L on Gd - 1
-      int et, st;
-      const int qt = encode_block(t, Gt, a.t_out.W, et, st, a.err);
+      const int qt = encode_block(t, Gt, a.Wt, et, st, a.err);
       const long long th = rounded_value(t, qt, st);  // on grid Gt >= Gd
       long long d;
       if (dfast) {
@@ -610,16 +600,15 @@ struct ResidBody {
 template <int DIM, int M>
 __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   const bool first_sweep = M == RS_FIRST ? true : (bool)a.first_sweep;
-  const bool write_t = M == RS_FIRST ? false : (bool)a.write_t;
   const bool has_uhc = M == RS_FIRST ? true : (bool)a.has_uhc;
   __shared__ SmemAny sm;
   __shared__ RhsSmem rs;
   __shared__ uint32_t pk[TY][33];
-  __shared__ int smr[2], smy[2], smt[2], smb[6];
+  __shared__ int smr[2], smy[2], smb[6];
   const Geo g = a.g;
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
   const Tile T = make_tile(g);
-  if (tid == 0) smr[0] = smr[1] = smy[0] = smy[1] = smt[0] = smt[1] = 0;
+  if (tid == 0) smr[0] = smr[1] = smy[0] = smy[1] = 0;
   // the tile's slice of the separable right-hand side tables (Sec. 7 problems):
   // exact products need |sum| < 2^94 for the split accumulation
   const bool rhs_sm = a.nterms <= TMAXP && a.rhs_bits <= 94;
@@ -685,7 +674,6 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   b.ovf = false;
   b.mr.init();
   b.my.init();
-  b.mt.init();
   b.pk = pk[ty];
   MarchIn in;
   in.s = a.u;
@@ -702,7 +690,6 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   ovf_flush(b.ovf, a.err, 202);
   meta_flush(b.mr, a.r_out.meta, smr);
   if (first_sweep) meta_flush(b.my, a.y_out.meta, smy);
-  if (write_t) meta_flush(b.mt, a.t_out.meta, smt);
 }
 
 // ------------------------------------------------------------------ diffusion residual
@@ -935,7 +922,7 @@ void launch_sweep(int dim, const SweepArgs &a, cudaStream_t st) {
 
 void launch_residual(int dim, const ResidArgs &a, cudaStream_t st) {
   dim3 b(32, TY);
-  const bool first = a.first_sweep && !a.write_t && a.has_uhc;
+  const bool first = a.first_sweep && !a.fuse_restrict && a.has_uhc;
   if (dim == 3) {
     if (first) k_residual<3, RS_FIRST><<<stencil_grid(a.g), b, 0, st>>>(a);
     else k_residual<3, RS_GENERIC><<<stencil_grid(a.g), b, 0, st>>>(a);
