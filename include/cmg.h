@@ -206,13 +206,24 @@ cmg_status cmg_kernel_stats(cmg_ctx *ctx, int kind, int top, double *ms, int64_t
  * cmg_coarse: y~_1 = round(rc_1 / A_1).  cmg_up(l): nu2 sweeps on level l with
  * z_l = P_l w_(l-1), then w_l = y~_l + z_l.  cmg_correct: u~_l += y~_l (all l).
  * cmg_vcycle: the down legs, coarse solve and up legs.  cmg_ir_iteration: one
- * residual + cycle + correction with the fused production kernels. */
+ * residual + cycle + correction with the fused production kernels.
+ * cmg_smooth(l, sweeps, with_z): the smoothing of Algorithm 1 on level l
+ * (2 <= l <= L): with_z = 0 runs `sweeps` pre-smoothing sweeps from y~_l = 0
+ * (Jacobi only, CMG_EUNSUPPORTED with red-black Gauss-Seidel); with_z = 1 runs
+ * `sweeps` post-smoothing sweeps on eq. cfas with z_l = P_l w_(l-1) (needs
+ * w_(l-1): cmg_coarse or cmg_up on level l-1 first), the last one writing
+ * w_l = y~_l + z_l.  cmg_restrict(l): rc_(l-1) = round(R_l (rc_l - A_l y~_l));
+ * CMG_EUNSUPPORTED without pre-smoothing, where the residual's restriction
+ * chain forms every rc_l (Algorithm 2).  cmg_down(l) is cmg_smooth(l, nu1, 0)
+ * then cmg_restrict(l); cmg_up(l) is cmg_smooth(l, nu2, 1). */
 cmg_status cmg_start(cmg_ctx *ctx);
 cmg_status cmg_prolongate(cmg_ctx *ctx);
 cmg_status cmg_residual(cmg_ctx *ctx);
 cmg_status cmg_down(cmg_ctx *ctx, int level);
 cmg_status cmg_coarse(cmg_ctx *ctx);
 cmg_status cmg_up(cmg_ctx *ctx, int level);
+cmg_status cmg_smooth(cmg_ctx *ctx, int level, int sweeps, int with_z);
+cmg_status cmg_restrict(cmg_ctx *ctx, int level);
 cmg_status cmg_correct(cmg_ctx *ctx);
 cmg_status cmg_vcycle(cmg_ctx *ctx);
 cmg_status cmg_ir_iteration(cmg_ctx *ctx);

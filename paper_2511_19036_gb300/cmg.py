@@ -80,6 +80,8 @@ _SIGS = {
     "cmg_down": (_i32, [_vp, _i32]),
     "cmg_coarse": (_i32, [_vp]),
     "cmg_up": (_i32, [_vp, _i32]),
+    "cmg_smooth": (_i32, [_vp, _i32, _i32, _i32]),
+    "cmg_restrict": (_i32, [_vp, _i32]),
     "cmg_correct": (_i32, [_vp]),
     "cmg_vcycle": (_i32, [_vp]),
     "cmg_ir_iteration": (_i32, [_vp]),
@@ -283,6 +285,12 @@ class Solver:
 
     def up(self, level: int):
         self._chk(_lib.cmg_up(self._h, level), "cmg_up")
+
+    def smooth(self, level: int, sweeps: int, with_z: bool):
+        self._chk(_lib.cmg_smooth(self._h, level, sweeps, int(bool(with_z))), "cmg_smooth")
+
+    def restrict(self, level: int):
+        self._chk(_lib.cmg_restrict(self._h, level), "cmg_restrict")
 
     def correct(self):
         self._chk(_lib.cmg_correct(self._h), "cmg_correct")

@@ -891,6 +891,39 @@ static cmg_status post_sweep(cmg_ctx *ctx, int l, SweepOpts o) {
   return do_sweep(ctx, l, o);
 }
 
+extern "C" cmg_status cmg_smooth(cmg_ctx *ctx, int l, int sweeps, int with_z) {
+  if (!ctx) return CMG_EINVAL;
+  cmg_status s = need(ctx, l >= 2 && l <= ctx->L && sweeps >= 0 && (with_z == 0 || with_z == 1),
+                      "bad level, sweep count or with_z");
+  if (s) return s;
+  if (!with_z) {  // pre-smoothing: from y~_l = 0 while the coarser corrections are zero
+    if (ctx->P.smoother != CMG_SMOOTHER_JACOBI)
+      return fail(ctx, CMG_EUNSUPPORTED, "red-black Gauss-Seidel smooths on the up-leg only (nu1 = 0)");
+    LV(ctx, l).y_zero = true;
+    for (int k = 0; k < sweeps; k++) {
+      SweepOpts o;
+      if ((s = do_sweep(ctx, l, o))) return s;
+    }
+    return CMG_OK;
+  }
+  for (int k = 0; k < sweeps; k++) {  // post-smoothing with z_l = P_l w_(l-1); the last sweep writes w_l
+    SweepOpts o;
+    o.has_z = true;
+    o.write_w = (k == sweeps - 1) && l < ctx->P.L_max;
+    if ((s = post_sweep(ctx, l, o))) return s;
+  }
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_restrict(cmg_ctx *ctx, int l) {
+  if (!ctx) return CMG_EINVAL;
+  cmg_status s = need(ctx, l >= 2 && l <= ctx->L, "bad level");
+  if (s) return s;
+  if (ctx->P.nu1 == 0)
+    return fail(ctx, CMG_EUNSUPPORTED, "without pre-smoothing the residual's restriction chain forms rc (Algorithm 2)");
+  return do_restrict(ctx, l, false);
+}
+
 extern "C" cmg_status cmg_up(cmg_ctx *ctx, int l) {
   if (!ctx) return CMG_EINVAL;
   cmg_status s = need(ctx, l >= 2 && l <= ctx->L, "bad level");

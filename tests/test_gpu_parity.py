@@ -290,3 +290,53 @@ def test_cycle_on_operands_wider_than_32_bits(cmg, name, L, smoother):
     for l in range(1, L + 1):
         same_section(cmg, s, o, cmg.SEC_U, oracle.U, l, "fused iteration")
     assert o.status == 0 and o.inexact == 0
+
+
+# ---------------------------------------------------------------- smoothing and restriction calls
+@pytest.mark.parametrize("name,Lmax,smoother", [("poisson3d_fourier", 5, 0), ("poisson2d_manufactured", 6, 0),
+                                                ("poisson3d_manufactured", 5, 1)])
+def test_smooth_and_restrict_calls_match_the_cycle(cmg, name, Lmax, smoother):
+    """cmg_smooth(l, nu1, 0) + cmg_restrict(l) is the down-leg and cmg_smooth(l, nu2, 1)
+    the up-leg: bit-exact against the oracle's cycle steps."""
+    prob = P.make_problem(name, Lmax)
+    cfg = cmg.config_for(name, Lmax, smoother=smoother)
+    s = cmg.Solver(cfg)
+    s.set_rhs(prob.tables, prob.scale_exp)
+    o = oracle.Oracle.for_problem(prob, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1, nu2=cfg.nu2,
+                                  omega=cfg.omega, smoother=smoother)
+    s.start()
+    o.start()
+    for L in range(2, Lmax + 1):
+        s.prolongate()
+        o.next_level()
+        for it in range(cfg.N_ir):
+            s.residual()
+            o.residual()
+            for l in range(L, 1, -1):
+                if cfg.nu1 > 0:
+                    s.smooth(l, cfg.nu1, False)
+                    s.restrict(l)
+                else:
+                    s.down(l)
+                o.down(l)
+                same_section(cmg, s, o, cmg.SEC_RC, oracle.RC, l - 1, "restrict L=%d" % L)
+            s.coarse()
+            o.coarse()
+            for l in range(2, L + 1):
+                s.smooth(l, cfg.nu2, True)
+                o.up(l)
+                same_section(cmg, s, o, cmg.SEC_Y, oracle.Y, l, "up L=%d" % L)
+            s.correct()
+            o.correct()
+        for l in range(1, L + 1):
+            same_section(cmg, s, o, cmg.SEC_U, oracle.U, l, "L=%d" % L)
+    assert o.status == 0 and o.inexact == 0
+    if smoother:
+        with pytest.raises(cmg.CmgError) as ei:
+            s.smooth(Lmax, 1, False)
+        assert ei.value.status == cmg.EUNSUPPORTED
+        with pytest.raises(cmg.CmgError) as ei:
+            s.restrict(Lmax)
+        assert ei.value.status == cmg.EUNSUPPORTED
+    with pytest.raises(cmg.CmgError):
+        s.smooth(1, 1, True)
