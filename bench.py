@@ -426,6 +426,10 @@ def run_gpu(args, wl):
                    "parallelism": "replicas x%d" % world},
         "bits_per_dof": reports[0]["persistent_bits"] / dofs,
         "temp_bytes_per_dof": reports[0]["temp_bytes"] / dofs,
+        # the problem's inputs held on the device: the separable right-hand-side
+        # tables, and for diffusion the binary32 nodal coefficient (boundary included)
+        "input_bytes_per_dof": {"rhs_tables": prob.tables.size * 4 / dofs,
+                                "coefficient": (((1 << Lmax) + 1) ** cfg.dim * 4 / dofs) if diffusion else 0.0},
         "alg_bytes_per_step": reports[0]["alg_bytes"],
         "whole_solve_hbm_frac": whole_frac,
         "nodal_rel_err_sampled": nodal_rel,
