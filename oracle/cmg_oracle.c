@@ -362,6 +362,7 @@ struct cmgo_ctx {
   sec y[MAXL + 1];  /* correction sections y~_l */
   double *w[MAXL + 1]; /* w_l = y~_l + z_l after the up-leg on level l (exact) */
   double *t;           /* exact t_L of the last residual */
+  int t_level;         /* t holds a level this fine (0: not allocated) */
   float *kfield;       /* diffusion: nodal k on the finest grid, boundary included */
   double *grhs;        /* diffusion: nodal right-hand side g (interior of the finest grid), or NULL */
   long long inexact;
@@ -528,17 +529,7 @@ cmgo_ctx *cmgo_create(const cmgo_params *p, int nterms, const int32_t *tables, i
     int B = bitlen_u128(bound);
     c->fsh = B > 50 ? B - 50 : 0;
   }
-  for (int l = 1; l <= p->Lmax; l++) {
-    lev g = mklev(p->dim, l);
-    if (sec_alloc(&c->u[l], &g) || sec_alloc(&c->r[l], &g) || sec_alloc(&c->rc[l], &g) ||
-        sec_alloc(&c->y[l], &g))
-      goto fail;
-    c->w[l] = (double *)calloc((size_t)g.np, sizeof(double));
-    if (!c->w[l]) goto fail;
-  }
-  c->t = (double *)calloc((size_t)mklev(p->dim, p->Lmax).np, sizeof(double));
-  if (!c->t) goto fail;
-  c->L = 0;
+  c->L = 0;  /* level arrays come with the first visit of a level (ensure_level) */
   return c;
 fail:
   cmgo_destroy(c);
@@ -682,7 +673,33 @@ static double A1(int dim) { return ldexp(2.0 * dim, 2 - dim); }
 /* Algorithm 3 steps                                                          */
 /* ------------------------------------------------------------------------- */
 
+/* The arrays of level l (and the residual array t, sized for the finest level
+ * reached) are allocated when the FMG first reaches l, so that a hierarchy with
+ * a large L_max can run its coarser stages alone.  Memory only: no value depends
+ * on when a level was allocated. */
+static int ensure_level(cmgo_ctx *c, int l) {
+  if (c->w[l]) return CMGO_OK;
+  lev g = mklev(c->P.dim, l);
+  if (sec_alloc(&c->u[l], &g) || sec_alloc(&c->r[l], &g) || sec_alloc(&c->rc[l], &g) || sec_alloc(&c->y[l], &g))
+    return CMGO_ENOMEM;
+  double *w = (double *)calloc((size_t)g.np, sizeof(double));
+  if (!w) return CMGO_ENOMEM;
+  if (l > c->t_level) {
+    double *t = (double *)calloc((size_t)g.np, sizeof(double));
+    if (!t) {
+      free(w);
+      return CMGO_ENOMEM;
+    }
+    free(c->t);
+    c->t = t;
+    c->t_level = l;
+  }
+  c->w[l] = w;
+  return CMGO_OK;
+}
+
 int cmgo_start(cmgo_ctx *c) {
+  if (ensure_level(c, 1)) return setst(c, CMGO_ENOMEM);
   c->L = 1;
   c->inexact = 0;
   c->status = CMGO_OK;
@@ -695,6 +712,7 @@ int cmgo_start(cmgo_ctx *c) {
 
 int cmgo_next_level(cmgo_ctx *c) {
   if (c->L >= c->P.Lmax) return setst(c, CMGO_EINVAL);
+  if (ensure_level(c, c->L + 1)) return setst(c, CMGO_ENOMEM);
   c->L += 1;
   /* Prolongating a compact vector adds a zero section; raising L widens every
    * other section by k bits, which appends zero bits (exact, Sec. 4). */
@@ -1135,7 +1153,7 @@ static const sec *pick(const cmgo_ctx *c, int which, int l) {
 
 int cmgo_get_section(const cmgo_ctx *c, int which, int level, uint32_t *words, int8_t *e,
                      double *values) {
-  if (level < 1 || level > c->P.Lmax) return CMGO_EINVAL;
+  if (level < 1 || level > c->P.Lmax || !c->w[level]) return CMGO_EINVAL;  /* level not reached */
   const sec *s = pick(c, which, level);
   if (!s) return CMGO_EINVAL;
   lev g = mklev(c->P.dim, level);
@@ -1160,6 +1178,7 @@ int cmgo_get_section(const cmgo_ctx *c, int which, int level, uint32_t *words, i
 int cmgo_set_section(cmgo_ctx *c, int which, int level, int W, const uint32_t *words,
                      const int8_t *e) {
   if (level < 1 || level > c->P.Lmax || W < 2 || W > 32) return CMGO_EINVAL;
+  if (ensure_level(c, level)) return CMGO_ENOMEM;
   sec *s = (sec *)pick(c, which, level);
   if (!s) return CMGO_EINVAL;
   lev g = mklev(c->P.dim, level);

@@ -1,0 +1,130 @@
+"""The full-size configurations the bench times, on the GPU.
+
+The oracle cannot solve 2049^3 or 1025^3 in a test, so these tests check:
+
+* bit-exact parity of the FMG stages that the oracle can reach, run with the
+  full-size hierarchy (L_max = 11 for 2049^3, 10 for 1025^3: the same tables,
+  strides, widths and launch configuration as the bench; the oracle allocates
+  a level only when the FMG reaches it);
+* properties that hold at any size for the whole solve: two production solves
+  give bitwise identical compact states, every stored exponent is a valid BFP
+  exponent, and the decoded solution meets its accuracy bound on sampled planes
+  (the O(h^2) nodal error of the manufactured problem; for diffusion, the
+  distance to a wider-width reference solve of the same discrete problem).
+"""
+import hashlib
+
+import numpy as np
+import pytest
+
+import cmg_problems as P
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cmg():
+    from paper_2511_19036_gb300 import cmg as m
+    return m
+
+
+def same_section(cmg, s, o, which_g, which_o, level, what=""):
+    gw, ge = s.get_section(which_g, level)
+    ow, oe, _ = o.get_section(which_o, level)
+    assert s.width(which_g, level) == o.width(which_o, level)
+    assert np.array_equal(ge, oe), "exponents differ: %s level %d" % (what, level)
+    assert np.array_equal(gw, ow), "words differ: %s level %d" % (what, level)
+
+
+def state_digest(cmg, s, L):
+    h = hashlib.sha256()
+    for l in range(1, L + 1):
+        w, e = s.get_section(cmg.SEC_U, l)
+        assert np.all((e == -128) | ((e >= -127) & (e <= 127)))
+        h.update(memoryview(w))
+        h.update(memoryview(e))
+    return h.hexdigest()
+
+
+def test_poisson3d_2049(cmg):
+    name, Lmax, Lo = "poisson3d_manufactured", 11, 9
+    prob = P.make_problem(name, Lmax)
+    cfg = cmg.config_for(name, Lmax, smoother=1)  # the bench's default configuration
+    s = cmg.Solver(cfg)
+    s.set_rhs(prob.tables, prob.scale_exp)
+    o = oracle.Oracle.for_problem(prob, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1, nu2=cfg.nu2,
+                                  omega=cfg.omega, smoother=1)
+    s.start()
+    o.start()
+    for L in range(2, Lo + 1):
+        s.prolongate()
+        o.next_level()
+        for _ in range(cfg.N_ir):
+            s.ir_iteration()  # the production (fused) iteration
+            o.ir_iteration()
+    assert o.status == 0 and o.inexact == 0
+    for l in range(1, Lo + 1):
+        same_section(cmg, s, o, cmg.SEC_U, oracle.U, l, "2049^3 hierarchy, FMG stage %d" % Lo)
+    del o
+    # the whole solve, twice: bitwise identical
+    s.fmg_solve()
+    d1 = state_digest(cmg, s, Lmax)
+    s.fmg_solve()
+    assert state_digest(cmg, s, Lmax) == d1
+    # nodal accuracy on sampled planes (bench: 4.4e-5)
+    n = (1 << Lmax) - 1
+    h = 2.0 ** -Lmax
+    x = (np.arange(n) + 1.0) * h
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    err, top = 0.0, 0.0
+    for z in (n // 4, n // 2, (3 * n) // 4):
+        u = s.decode_solution(z, 1).cpu().numpy()[0]
+        ue = prob.exact_u(X, Y, (z + 1) * h)
+        err = max(err, float(np.max(np.abs(u - ue))))
+        top = max(top, float(np.max(np.abs(ue))))
+    assert err / top < 1e-4
+
+
+def test_diffusion3d_1025(cmg):
+    name, Lmax, Lo = "diffusion3d_grf", 10, 7
+    prob = P.make_problem(name, Lmax)
+    cfg = cmg.config_for(name, Lmax)
+    k_dev = prob.kfield(device="cuda").reshape(-1).contiguous()  # the seeded binary32 field (input)
+    k = k_dev.cpu().numpy()
+    s = cmg.Solver(cfg)
+    s.set_rhs(prob.tables, prob.scale_exp)
+    s.set_coefficient(k_dev)
+    o = oracle.Oracle(3, Lmax, prob.tables, prob.scale_exp, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1,
+                      nu2=cfg.nu2, omega=cfg.omega, arith=1, coef=1, kfield=k)
+    s.start()
+    o.start()
+    for L in range(2, Lo + 1):
+        s.prolongate()
+        o.next_level()
+        for _ in range(cfg.N_ir):
+            s.ir_iteration()
+            o.ir_iteration()
+    assert o.status == 0
+    for l in range(1, Lo + 1):
+        same_section(cmg, s, o, cmg.SEC_U, oracle.U, l, "1025^3 diffusion hierarchy, FMG stage %d" % Lo)
+    del o, k
+    s.fmg_solve()
+    d1 = state_digest(cmg, s, Lmax)
+    s.fmg_solve()
+    assert state_digest(cmg, s, Lmax) == d1
+    # against a wider-width reference solve of the same discrete problem (bench: 9.9e-6)
+    import dataclasses
+    ref = cmg.Solver(dataclasses.replace(cfg, b1=14, b2=10, N_ir=16))
+    ref.set_rhs(prob.tables, prob.scale_exp)
+    ref.set_coefficient(k_dev)
+    ref.fmg_solve()
+    n = (1 << Lmax) - 1
+    dmax, umax = 0.0, 0.0
+    for z in (n // 4, n // 2, (3 * n) // 4):
+        a = s.decode_solution(z, 1)
+        b = ref.decode_solution(z, 1)
+        dmax = max(dmax, float((a - b).abs().max()))
+        umax = max(umax, float(b.abs().max()))
+    assert dmax / umax < 1e-4

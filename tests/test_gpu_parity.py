@@ -140,6 +140,7 @@ FMG_CASES = [("poisson2d_manufactured", 8, {}),       # 257^2, the 2-D workload
              ("poisson2d_fourier", 7, {"nu1": 0, "nu2": 1}),
              ("poisson3d_fourier", 2, {}),
              ("poisson3d_fourier", 6, {}),
+             ("poisson3d_fourier", 8, {}),          # the 257^3 configuration, whole
              ("poisson3d_manufactured", 6, {"nu1": 1, "nu2": 1}),
              ("poisson3d_fourier", 5, {"nu1": 0, "nu2": 2, "N_ir": 4})]
 

@@ -79,6 +79,7 @@ def test_step_parity_red_black(cmg, name, Lmax, arith, over):
 
 
 FMG_CASES = [("poisson2d_manufactured", 8, 0, {}),   # Table 2's 2-D constants, 257^2
+             ("poisson3d_fourier", 8, 0, {}),        # the 257^3 configuration, whole
              ("poisson2d_fourier", 3, 0, {}),
              ("poisson3d_fourier", 6, 0, {}),
              ("poisson3d_manufactured", 5, 0, {"nu2": 2, "N_ir": 4}),
