@@ -137,3 +137,40 @@ def test_autograd_matches_central_differences(cmg):
         d2 = rng.standard_normal(n)
         fd = (Jexact(k, g + eps * d2) - Jexact(k, g - eps * d2)) / (2 * eps)
         assert abs(fd - dg @ d2) <= 2e-4 * abs(fd)
+
+
+def test_adjoint_workload_257_whole(cmg):
+    """The 257^3 adjoint configuration whole: k = exp(m), m a GRF (sigma 0.5, seed 2),
+    u_obs from m + a GRF (sigma 0.1, seed 3); forward solve, adjoint solve with the
+    right-hand side 2^(dL) (u - u_obs), and both gradients, bit-exact against the oracle."""
+    from cmg_problems.diffusion import diffusion_grf
+    dim, L = 3, 8
+    prob = diffusion_grf(dim, L, seed=2, sigma=0.5)
+    pert = diffusion_grf(dim, L, seed=3, sigma=0.1)
+    m = prob.g_field()
+    k = np.exp(m).astype(np.float32).ravel()
+    k_obs = np.exp(m + pert.g_field()).astype(np.float32).ravel()
+    cfg = cmg.config_for("diffusion3d_grf", L)
+    n = ((1 << L) - 1) ** dim
+    g = np.ones(n)
+
+    def solve_pair(kk, rhs):
+        s = cmg.Solver(cfg)
+        s.set_coefficient(torch.from_numpy(kk).cuda())
+        s.set_rhs_nodal(torch.from_numpy(rhs).cuda())
+        s.fmg_solve()
+        o = make_oracle(prob, cfg, kk)
+        o.set_rhs_nodal(rhs)
+        o.fmg()
+        assert o.status == 0
+        ug = s.decode_solution().reshape(-1).cpu().numpy()
+        uo = np.asarray(o.decode_solution()).ravel()
+        assert np.array_equal(ug, uo)
+        return s, o, uo
+
+    _, _, uobs = solve_pair(k_obs, g)
+    s, o, u = solve_pair(k, g)
+    _, _, lam = solve_pair(k, np.ldexp(u - uobs, dim * L))
+    dk, dg = s.gradient(torch.from_numpy(u).cuda(), torch.from_numpy(lam).cuda())
+    assert np.array_equal(dk.cpu().numpy(), o.gradient_k(u, lam))
+    assert np.array_equal(dg.cpu().numpy(), np.ldexp(lam, -dim * L))
