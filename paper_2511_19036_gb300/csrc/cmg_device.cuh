@@ -300,6 +300,46 @@ __device__ __forceinline__ int encode_block_f64(double x, int W, int &e, int *er
   return (int)q;
 }
 
+// Exact binary64 of a binary32 value by assembling the bits with integer
+// instructions (normal inputs; zero, subnormal, infinite and NaN inputs take the
+// conversion instruction).
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)x;
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
+                                          ((unsigned long long)(e + 896u) << 52) |
+                                          ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// v 2^G rounded to nearest-even into binary64 with integer instructions (exact
+// for |v| < 2^53); |v| < 2^63 - 1.  A result outside the normal range sets bad.
+__device__ __forceinline__ double i64_to_f64_rne(long long v, int G, bool &bad) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  int nb = 64 - __clzll((long long)u);  // 2^(nb-1) <= u < 2^nb
+  unsigned long long m;
+  if (nb <= 53) {
+    m = u << (53 - nb);
+  } else {
+    const int sh = nb - 53;
+    m = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) m += 1ull;
+    if (m >> 53) {  // rounded up to the next power of two
+      m >>= 1;
+      nb += 1;
+    }
+  }
+  const int be = nb - 1 + G + 1023;  // m in [2^52, 2^53): value = m 2^(nb - 53 + G)
+  if (be <= 0 || be >= 2047) {
+    bad = true;
+    return 0.0;
+  }
+  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1ull))));
+}
+
 __device__ __forceinline__ long long rounded_value(long long v, int q, int s) {
   return s > 0 ? shl((long long)q, s) : v;
 }

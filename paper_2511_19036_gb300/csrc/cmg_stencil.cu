@@ -704,7 +704,8 @@ struct ResidDiffBody {
   static constexpr bool kRaw = true;
   const ResidArgs &a;
   const Geo &g;
-  double scaleF, hs;  // 2^GF and h^(d-2)
+  int GF;             // grid of the raw operand values
+  double hs;          // h^(d-2)
   int kstride;
   int bip, lane, i, j;
   bool rowok, pt, bad;
@@ -717,9 +718,8 @@ struct ResidDiffBody {
   __device__ __forceinline__ float kat(int I, int J, int K) const {
     return __ldg(a.kfield + ((long long)(DIM == 3 ? K * kstride : 0) * a.kN + J * kstride) * a.kN + I * kstride);
   }
-  __device__ __forceinline__ double dv(long long v) {
+  __device__ __forceinline__ void ck53(long long v) {  // u^ must be an exact binary64 value
     if (v >= (1ll << 53) || v <= -(1ll << 53)) bad = true;
-    return __dmul_rn(__ll2double_rn(v), scaleF);
   }
   __device__ __forceinline__ void out(int, long long, long long, long long, long long) {}
 
@@ -729,16 +729,22 @@ struct ResidDiffBody {
     double t = 0.0;
     if (pt) {
       const int I = i + 1, J = j + 1, K = k + 1;
-      const double up = dv(F0);
-      const double kp = (double)kat(I, J, K);
+      ck53(F0);
+      const double kp = f32_to_f64(kat(I, J, K));
       const long long nv[6] = {Pc[-1], Pc[1], Pc[-PW], Pc[PW], Fm, Fp};
       double acc = 0.0;
+      // the oracle's acc + ((k_q + k_p) 0.5)(u_p - u_q) in FP64: u_p, u_q are exact
+      // doubles on one grid, so fl(u_p - u_q) is the RNE binary64 of the exact
+      // integer difference, formed here with integer instructions; k_q + k_p of
+      // two binary32 values is exact in binary64, and (s 0.5) d = s (d 0.5) is the
+      // same real product, so the 0.5 goes into the difference's exponent
 #pragma unroll
       for (int e = 0; e < 2 * DIM; e++) {
         const int Iq = I + (e == 0 ? -1 : e == 1 ? 1 : 0), Jq = J + (e == 2 ? -1 : e == 3 ? 1 : 0);
         const int Kq = K + (e == 4 ? -1 : e == 5 ? 1 : 0);
-        const double kf = __dmul_rn(__dadd_rn((double)kat(Iq, Jq, Kq), kp), 0.5);
-        acc = __dadd_rn(acc, __dmul_rn(kf, __dsub_rn(up, dv(nv[e]))));
+        ck53(nv[e]);
+        const double s = __dadd_rn(f32_to_f64(kat(Iq, Jq, Kq)), kp);
+        acc = __dadd_rn(acc, __dmul_rn(s, i64_to_f64_rne(F0 - nv[e], GF - 1, bad)));
       }
       double f;
       if (a.grhs) {  // nodal right-hand side, injected: f_L = h_L^d g
@@ -747,7 +753,9 @@ struct ResidDiffBody {
                                       : (long long)(J * s - 1) * n1 + (I * s - 1);
         f = __dmul_rn(__ldg(a.grhs + gi), __longlong_as_double((long long)(1023 - DIM * g.l) << 52));
       } else {
-        f = __dmul_rn((double)rhs_global<DIM>(a, I, J, K), __longlong_as_double((long long)(a.Gf + 1023) << 52));
+        const long long fq = rhs_global<DIM>(a, I, J, K);  // below 2^52 after the rounding shift
+        ck53(fq);
+        f = i64_to_f64_rne(fq, a.Gf, bad);
       }
       t = __dsub_rn(f, __dmul_rn(acc, hs));
     }
@@ -778,7 +786,7 @@ __global__ void __launch_bounds__(NT, 2) k_residual_diff(ResidArgs a) {
   if (tid == 0 && GF < GRID_NONE / 2 && MF + 4 - GF > 62) flag_range(a.err, 204, MF + 4, GF);
   ResidDiffBody<DIM> b{a, g};
   // 2^GF as a double (GF is at least -1022 for every operand that fits here)
-  b.scaleF = GF < GRID_NONE / 2 ? __longlong_as_double((long long)(imax(GF, -1022) + 1023) << 52) : 0.0;
+  b.GF = GF;
   b.hs = __longlong_as_double((long long)(1023 - (DIM - 2) * g.l) << 52);
   b.kstride = 1 << (a.Lmax - g.l);
   b.lane = lane;
