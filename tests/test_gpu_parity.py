@@ -45,7 +45,7 @@ def same_section(cmg, s, o, which_g, which_o, level, what=""):
 
 # ---------------------------------------------------------------- codec
 @pytest.mark.parametrize("W", [2, 3, 4, 5, 7, 8, 13, 16, 25, 31, 32])
-@pytest.mark.parametrize("n", [1, 31, 32, 33, 32 * 257 + 5])
+@pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 32 * 257 + 5])
 def test_codec_bit_exact(cmg, W, n):
     x = random_block_values(n, seed=1000 + W + n)
     ow, oe, st = oracle.encode(x, W)
@@ -341,3 +341,21 @@ def test_smooth_and_restrict_calls_match_the_cycle(cmg, name, Lmax, smoother):
         assert ei.value.status == cmg.EUNSUPPORTED
     with pytest.raises(cmg.CmgError):
         s.smooth(1, 1, True)
+
+
+@pytest.mark.parametrize("name", ["poisson3d_fourier", "poisson2d_manufactured"])
+def test_one_level_hierarchy(cmg, name):
+    """L_max = 1, one unknown: the FMG is the coarse solve u~_1 = round(f_1 / A_1); a
+    cycle on it is refused."""
+    prob, cfg, s, o = make_pair(cmg, name, 1)
+    s.fmg_solve()
+    o.fmg()
+    assert o.status == 0
+    same_section(cmg, s, o, cmg.SEC_U, oracle.U, 1, "L_max = 1")
+    assert np.array_equal(s.decode_solution().cpu().numpy(), o.decode_solution())
+    with pytest.raises(cmg.CmgError) as ei:
+        s.ir_iteration()
+    assert ei.value.status == cmg.EINVAL
+    with pytest.raises(cmg.CmgError) as ei:
+        s.coarse()
+    assert ei.value.status == cmg.EUNSUPPORTED
