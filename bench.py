@@ -60,18 +60,22 @@ def source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def read_traffic(kernel: str, workload: str):
-    """Per-DoF DRAM traffic of ``kernel`` from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+def read_profile(kernel: str, workload: str, key: str):
+    """A per-unit figure (``key``) of ``kernel`` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m_sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
-    m_val = re.search(r"dram_bytes_per_dof:\s*([0-9.eE+-]+)", txt)
+    m_val = re.search(r"%s:\s*([0-9.eE+-]+)" % re.escape(key), txt)
     if not m_sha or not m_val or m_sha.group(1) != source_sha():
         return None
     return float(m_val.group(1))
+
+
+def read_traffic(kernel: str, workload: str):
+    return read_profile(kernel, workload, "dram_bytes_per_dof")
 
 
 def measured_peak_hbm():
@@ -160,6 +164,41 @@ def oracle_rate_one_thread(prob_name: str, L: int, cfg):
     if r.returncode != 0:
         return None
     return tuple(json.loads(r.stdout.strip().splitlines()[-1]))
+
+
+class gpu_local_cpus:
+    """Runs the block on the CPUs next to the GPU (its sysfs local_cpulist), so
+    that host buffers pinned inside it land in the GPU's NUMA node; the thread's
+    affinity is restored afterwards.  No-op where the list is not available."""
+
+    def __init__(self, device: int):
+        self.device = device
+        self.old = None
+
+    def __enter__(self):
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.device)
+            path = "/sys/bus/pci/devices/%04x:%02x:%02x.0/local_cpulist" % (
+                p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+            cpus = set()
+            for part in open(path).read().strip().split(","):
+                if "-" in part:
+                    lo, hi = part.split("-")
+                    cpus.update(range(int(lo), int(hi) + 1))
+                elif part:
+                    cpus.add(int(part))
+            if cpus:
+                self.old = os.sched_getaffinity(0)
+                os.sched_setaffinity(0, cpus)
+        except (OSError, ValueError, AttributeError):
+            self.old = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.old is not None:
+            os.sched_setaffinity(0, self.old)
+        return False
 
 
 def max_over_ranks(x: float, dist, device: str) -> float:
@@ -300,6 +339,20 @@ def run_gpu(args, wl):
                 "alg_bytes_per_launch": sw_bytes / sw_n if sw_n else None,
                 "avg_launch_ms": sw_ms / sw_n if sw_n else None,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
+    # the bound that holds: instruction issue (4 warp-instructions per SM and clock)
+    # with the ncu instruction count per 32-value row of the same kernels
+    prof_wl = wl + ("_rbgs" if cfg.smoother else "_jacobi")
+    inst_row = read_profile("k_sweep", prof_wl, "warp_inst_per_row")
+    issue = None
+    if inst_row and sw_n and sw_ms > 0:
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+        rows = int(cmg.lib().cmg_section_blocks(cfg.dim, Lmax))
+        ach = inst_row * rows / (sw_ms / sw_n * 1e-3)
+        pk = 4.0 * nsm * mhz * 1e6 if mhz else None
+        issue = {"kernel": roofline["kernel"], "unit": "warp-instructions/s", "achieved": ach, "peak": pk,
+                 "frac": ach / pk if pk else None, "warp_inst_per_row": inst_row,
+                 "peak_kind": "4 issue slots per SM per clock x %d SMs x %s MHz (sampled SM clock)" % (nsm, mhz)}
     whole_frac = (reports[0]["alg_bytes"] / (ms_step * 1e-3) / 1e9) / peak
     # Sec. 6.2 storage model for this workload (mantissa bits, CMG vs BFPMG) next to
     # the measured layout (exponents, row padding and the Jacobi ping-pong included)
@@ -315,11 +368,13 @@ def run_gpu(args, wl):
 
     # end to end through the public API: H2D of the step's inputs (the RHS tables,
     # from pinned memory) and D2H of the step's result (the compact solution).
-    tab_pinned = torch.from_numpy(np.ascontiguousarray(prob.tables)).pin_memory()
+    with gpu_local_cpus(local):
+        tab_pinned = torch.from_numpy(np.ascontiguousarray(prob.tables)).pin_memory()
     nb = [int(cmg.lib().cmg_section_blocks(cfg.dim, l)) for l in range(1, Lmax + 1)]
     Wu = [cfg.k_u * (Lmax - l) + cfg.b1 for l in range(1, Lmax + 1)]
-    out_w = [torch.empty(nb[i] * Wu[i], dtype=torch.int32).pin_memory() for i in range(Lmax)]
-    out_e = [torch.empty(nb[i], dtype=torch.int8).pin_memory() for i in range(Lmax)]
+    with gpu_local_cpus(local):
+        out_w = [torch.empty(nb[i] * Wu[i], dtype=torch.int32).pin_memory() for i in range(Lmax)]
+        out_e = [torch.empty(nb[i], dtype=torch.int8).pin_memory() for i in range(Lmax)]
     h2d = tab_pinned.numel() * 4
     d2h = sum(w.numel() * 4 + e.numel() for w, e in zip(out_w, out_e))
     e2e_times, phases = [], []
@@ -436,6 +491,7 @@ def run_gpu(args, wl):
         "fp32_vs_exact": fp32_vs_exact,
         "diffusion_vs_reference": diffusion_vs_reference,
         "roofline": roofline,
+        "issue_roofline": issue,
         "kernels_last_step": kernels,
         "storage_model": storage,
         "cpu_baseline": cpu,
@@ -480,7 +536,8 @@ def run_adjoint(args, wl):
     n = (1 << Lmax) - 1
     dofs = n ** dim
     cfg = cmg.config_for("diffusion3d_grf", Lmax)
-    g_host = torch.ones(dofs, dtype=torch.float64).pin_memory()
+    with gpu_local_cpus(local):
+        g_host = torch.ones(dofs, dtype=torch.float64).pin_memory()
     g = g_host.cuda()
     with torch.no_grad():
         u_obs = diffusion_solve(k_obs, g, cfg).reshape(-1)
@@ -512,7 +569,8 @@ def run_adjoint(args, wl):
     clocks = clk.stop()
     ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
     # end to end: H2D of g, gradient D2H, inside the timed region
-    dm_host = torch.empty(dm.numel(), dtype=torch.float32).pin_memory()
+    with gpu_local_cpus(local):
+        dm_host = torch.empty(dm.numel(), dtype=torch.float32).pin_memory()
     e2e = []
     for _ in range(max(1, min(args.steps, 3))):
         barrier()
