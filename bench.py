@@ -227,8 +227,8 @@ def cycle_name(cfg) -> str:
 
 
 def pick_sample_level(prob_name: str, Lmax: int, dim: int) -> int:
-    # bounded oracle sample: a few to about 10 s of host work per solve on the
-    # GPU machine's cores (3-D L = 9 is 1.3e8 DoF)
+    # bounded oracle sample: a few to about 10 s of host work per solve on a
+    # 16-core host (3-D L = 9 is 1.3e8 DoF)
     if prob_name.startswith("diffusion"):  # the coefficient field is drawn on the host here
         return min(Lmax, 7 if dim == 3 else 10)
     return min(Lmax, 9 if dim == 3 else 12)

@@ -49,7 +49,7 @@ typedef enum {
   CMG_ECUDA = 4,        /* CUDA runtime error (see cmg_last_error) */
   CMG_ECORRUPT = 5,     /* code -2^(W-1) met while decoding */
   CMG_ETIMEOUT = 6,     /* reserved: no call waits on a device flag */
-  CMG_EUNSUPPORTED = 7  /* valid request this build does not implement */
+  CMG_EUNSUPPORTED = 7  /* a valid request the library does not implement */
 } cmg_status;
 
 /* Parameters of Algorithm 3 with the precisions of Table 1 (P1: p = 1, m = 1).
