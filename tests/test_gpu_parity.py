@@ -359,3 +359,29 @@ def test_one_level_hierarchy(cmg, name):
     with pytest.raises(cmg.CmgError) as ei:
         s.coarse()
     assert ei.value.status == cmg.EUNSUPPORTED
+
+
+def test_values_beyond_62_bits_raise_erange(cmg):
+    """u~_L with rows scaled over 120 binary orders: the residual's exact operand
+    would need more than 62 bits; the kernels flag it and the call reports
+    CMG_ERANGE (the values never wrap)."""
+    name, L = "poisson3d_fourier", 4
+    prob, cfg, s, o = make_pair(cmg, name, L)
+    s.start()
+    for _ in range(L - 1):
+        s.prolongate()
+    n = (1 << L) - 1
+    npts = n ** 3
+    W = s.width(cmg.SEC_U, L)
+    rng = np.random.default_rng(3)
+    x = random_block_values(npts, seed=5, spread_bits=4) * np.repeat(
+        2.0 ** rng.integers(-120, 0, size=npts // n).astype(np.float64), n)
+    rows = np.zeros((npts // n, 32 * ((n + 31) // 32)))
+    rows[:, :n] = x.reshape(npts // n, n)
+    words, e, st = oracle.encode(rows.ravel(), W)
+    assert st == 0
+    s.set_section(cmg.SEC_U, L, W, words, e)
+    with pytest.raises(cmg.CmgError) as ei:
+        s.residual()
+        s.sync()
+    assert ei.value.status == cmg.ERANGE
