@@ -98,6 +98,14 @@ class SeparableProblem:
         return np.ldexp(acc, self.scale_exp)
 
 
+def _sin(a):  # the closed forms below take numpy arrays or torch tensors (device diagnostics)
+    return a.sin() if hasattr(a, "sin") else np.sin(a)
+
+
+def _cos(a):
+    return a.cos() if hasattr(a, "cos") else np.cos(a)
+
+
 def _nodes(Lmax: int) -> np.ndarray:
     n1 = (1 << Lmax) - 1
     return (np.arange(n1, dtype=np.float64) + 1.0) * (2.0 ** -Lmax)
@@ -141,10 +149,10 @@ def poisson2d_manufactured(Lmax: int) -> SeparableProblem:
     tables, se = quantise_tables(funcs, 2)
 
     def exact_u(X, Y):
-        return np.sin(pi * X) * np.sin(pi * Y) * (1.0 + X * X * Y)
+        return _sin(pi * X) * _sin(pi * Y) * (1.0 + X * X * Y)
 
     def exact_grad(X, Y):
-        sx, sy, cx, cy = np.sin(pi * X), np.sin(pi * Y), np.cos(pi * X), np.cos(pi * Y)
+        sx, sy, cx, cy = _sin(pi * X), _sin(pi * Y), _cos(pi * X), _cos(pi * Y)
         g = 1.0 + X * X * Y
         return (pi * cx * sy * g + sx * sy * 2 * X * Y,
                 sx * (pi * cy * g + sy * X * X))
@@ -174,11 +182,11 @@ def poisson3d_manufactured(Lmax: int) -> SeparableProblem:
     tables, se = quantise_tables(funcs, 3)
 
     def exact_u(X, Y, Z):
-        return np.sin(pi * X) * np.sin(pi * Y) * np.sin(pi * Z) * (1.0 + X * X * Y * Z)
+        return _sin(pi * X) * _sin(pi * Y) * _sin(pi * Z) * (1.0 + X * X * Y * Z)
 
     def exact_grad(X, Y, Z):
-        sx, sy, sz = np.sin(pi * X), np.sin(pi * Y), np.sin(pi * Z)
-        cx, cy, cz = np.cos(pi * X), np.cos(pi * Y), np.cos(pi * Z)
+        sx, sy, sz = _sin(pi * X), _sin(pi * Y), _sin(pi * Z)
+        cx, cy, cz = _cos(pi * X), _cos(pi * Y), _cos(pi * Z)
         g = 1.0 + X * X * Y * Z
         sss = sx * sy * sz
         return (pi * cx * sy * sz * g + sss * 2 * X * Y * Z,
@@ -210,17 +218,17 @@ def poisson3d_fourier(Lmax: int, seed: int = 0, nmodes: int = 8, kmax: int = 8) 
         out = 0.0
         for a, k in modes:
             out = out + a / (pi * pi * (k[0] ** 2 + k[1] ** 2 + k[2] ** 2)) * \
-                np.sin(k[0] * pi * X) * np.sin(k[1] * pi * Y) * np.sin(k[2] * pi * Z)
+                _sin(k[0] * pi * X) * _sin(k[1] * pi * Y) * _sin(k[2] * pi * Z)
         return out
 
     def exact_grad(X, Y, Z):
         gx = gy = gz = 0.0
         for a, k in modes:
             c = a / (pi * pi * (k[0] ** 2 + k[1] ** 2 + k[2] ** 2))
-            sx, sy, sz = np.sin(k[0] * pi * X), np.sin(k[1] * pi * Y), np.sin(k[2] * pi * Z)
-            gx = gx + c * k[0] * pi * np.cos(k[0] * pi * X) * sy * sz
-            gy = gy + c * k[1] * pi * sx * np.cos(k[1] * pi * Y) * sz
-            gz = gz + c * k[2] * pi * sx * sy * np.cos(k[2] * pi * Z)
+            sx, sy, sz = _sin(k[0] * pi * X), _sin(k[1] * pi * Y), _sin(k[2] * pi * Z)
+            gx = gx + c * k[0] * pi * _cos(k[0] * pi * X) * sy * sz
+            gy = gy + c * k[1] * pi * sx * _cos(k[1] * pi * Y) * sz
+            gz = gz + c * k[2] * pi * sx * sy * _cos(k[2] * pi * Z)
         return gx, gy, gz
 
     desc = "sum of %d modes, seed %d: %s" % (nmodes, seed, ", ".join(
@@ -245,15 +253,15 @@ def poisson2d_fourier(Lmax: int, seed: int = 0, nmodes: int = 8, kmax: int = 8) 
         out = 0.0
         for a, k in modes:
             out = out + a / (pi * pi * (k[0] ** 2 + k[1] ** 2)) * \
-                np.sin(k[0] * pi * X) * np.sin(k[1] * pi * Y)
+                _sin(k[0] * pi * X) * _sin(k[1] * pi * Y)
         return out
 
     def exact_grad(X, Y):
         gx = gy = 0.0
         for a, k in modes:
             c = a / (pi * pi * (k[0] ** 2 + k[1] ** 2))
-            gx = gx + c * k[0] * pi * np.cos(k[0] * pi * X) * np.sin(k[1] * pi * Y)
-            gy = gy + c * k[1] * pi * np.sin(k[0] * pi * X) * np.cos(k[1] * pi * Y)
+            gx = gx + c * k[0] * pi * _cos(k[0] * pi * X) * _sin(k[1] * pi * Y)
+            gy = gy + c * k[1] * pi * _sin(k[0] * pi * X) * _cos(k[1] * pi * Y)
         return gx, gy
 
     return SeparableProblem("poisson2d_fourier", 2, Lmax, tables, se, exact_u,

@@ -108,3 +108,45 @@ def exact_on_grid(prob, level: int) -> np.ndarray:
 def nodal_rel_l2(prob, U: np.ndarray, level: int) -> float:
     ue = exact_on_grid(prob, level)
     return float(np.sqrt(np.mean((U.reshape(ue.shape) - ue) ** 2)) / np.sqrt(np.mean(ue ** 2)))
+
+
+def h1_error_slabs(prob, decode, level: int, zchunk: int = 8) -> float:
+    """``h1_error`` for a 3-D problem, streamed over slabs of z-planes with torch.
+
+    ``decode(z0, nz)`` returns the interior nodal values of planes z0 .. z0+nz-1
+    as a float64 torch tensor of shape (nz, n, n) (on the GPU for the full-size
+    solutions, which are never held whole); the quadrature is that of
+    ``h1_error``, evaluated on the tensor's device.
+    """
+    import torch
+    assert prob.dim == 3
+    n = 1 << level  # cubes per axis; padded planes 0 .. n, interior planes 1 .. n-1
+    h = 1.0 / n
+    total = 0.0
+    dev = None
+    for z0 in range(0, n, zchunk):
+        z1 = min(n, z0 + zchunk)  # cubes z0 .. z1-1 use padded planes z0 .. z1
+        lo, hi = max(z0, 1) - 1, min(z1, n - 1) - 1  # interior planes among them
+        U = decode(lo, hi - lo + 1)
+        dev = U.device
+        V = torch.zeros((z1 - z0 + 1, n + 1, n + 1), dtype=torch.float64, device=dev)
+        V[lo + 1 - z0: hi + 2 - z0, 1:n, 1:n] = U.reshape(hi - lo + 1, n - 1, n - 1)
+        ar = torch.arange(n, dtype=torch.float64, device=dev)
+        i0, j0 = ar.view(1, 1, n), ar.view(1, n, 1)
+        k0 = torch.arange(z0, z1, dtype=torch.float64, device=dev).view(-1, 1, 1)
+        nz = z1 - z0
+        for path in itertools.permutations(range(3)):
+            verts = [(0, 0, 0)]
+            for ax in path:
+                v = list(verts[-1])
+                v[ax] += 1
+                verts.append(tuple(v))
+            vals = [V[vz:vz + nz, vy:vy + n, vx:vx + n] for (vx, vy, vz) in verts]
+            G = [None, None, None]
+            for k, ax in enumerate(path):
+                G[ax] = (vals[k + 1] - vals[k]) / h
+            for bary, w in _TET:
+                p = [sum(bary[k] * verts[k][a] for k in range(4)) for a in range(3)]
+                gx, gy, gz = prob.exact_grad((i0 + p[0]) * h, (j0 + p[1]) * h, (k0 + p[2]) * h)
+                total += w * float(((G[0] - gx) ** 2 + (G[1] - gy) ** 2 + (G[2] - gz) ** 2).sum())
+    return math.sqrt(total * h ** 3 / 6.0)

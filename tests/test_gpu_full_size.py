@@ -128,3 +128,30 @@ def test_diffusion3d_1025(cmg):
         dmax = max(dmax, float((a - b).abs().max()))
         umax = max(umax, float(b.abs().max()))
     assert dmax / umax < 1e-4
+
+
+def test_poisson3d_2049_meets_the_success_criterion(cmg):
+    """Sec. 7.1 at the full size: |u~ - u|_H1 <= 2 |u_h - u|_H1 at L = 11, and the
+    compact solution's error order from L = 10 to 11 at least 0.95.  u_h is taken
+    from a near-lossless solve of the same discrete problem (Jacobi V(2,2),
+    b1 = b2 = 12, N = 8: the widest b1 the 32-bit codes allow at L = 11)."""
+    import dataclasses
+    import math
+    from cmg_problems.diagnostics import h1_error_slabs
+    name = "poisson3d_manufactured"
+    errs = {}
+    for L in (10, 11):
+        prob = P.make_problem(name, L)
+        base = cmg.config_for(name, L)
+        for tag, cfg in (("cmg", cmg.config_for(name, L, smoother=1)),
+                         ("ref", dataclasses.replace(base, b1=12, b2=12, N_ir=8))):
+            s = cmg.Solver(cfg)
+            s.set_rhs(prob.tables, prob.scale_exp)
+            s.fmg_solve()
+            errs[(tag, L)] = h1_error_slabs(prob, lambda z0, nz: s.decode_solution(z0, nz), L)
+            del s
+    ratio = errs[("cmg", 11)] / errs[("ref", 11)]
+    order = math.log2(errs[("cmg", 10)] / errs[("cmg", 11)])
+    print("H1 errors", {"%s L=%d" % k: v for k, v in errs.items()}, "ratio %.4f order %.4f" % (ratio, order))
+    assert ratio <= 2.0
+    assert order >= 0.95

@@ -215,3 +215,19 @@ def test_storage_is_linear():
                 assert abs(per - prev) < 0.5
             prev = per
         assert per < 1.1 * (c * b + c / (2 ** dim - 1) * k) + 8 / 32 + 1.0
+
+
+def test_slab_h1_error_equals_the_whole_array_one():
+    """The slab-streamed H^1 error (used on the GPU at full size) equals the
+    whole-array one on the same nodal values."""
+    torch = pytest.importorskip("torch")
+    from cmg_problems.diagnostics import h1_error_slabs
+    prob = P.make_problem("poisson3d_manufactured", 5)
+    n = (1 << 5) - 1
+    rng = np.random.default_rng(1)
+    U = np.asarray(prob.exact_u(*np.meshgrid(*(np.arange(1, n + 1) / 32.0,) * 3, indexing="ij")[::-1]))
+    U = U + 1e-3 * rng.standard_normal(U.shape)
+    Ut = torch.from_numpy(U)
+    a = h1_error(prob, U, 5)
+    b = h1_error_slabs(prob, lambda z0, nz: Ut[z0:z0 + nz], 5, zchunk=3)
+    assert abs(a - b) <= 1e-12 * a
