@@ -430,6 +430,24 @@ def run_gpu(args, wl):
         diffusion_vs_reference = {"max_rel_diff_sampled": dmax / umax,
                                   "reference": "b1=14, b2=10, N_ir=16, same binary32 cycle"}
         del ref
+    # Sec. 7.1 at this size: the H1 error of the solution against that of a
+    # near-lossless solve of the same discrete problem (Jacobi V(2,2), b1 = b2 = 12,
+    # N = 8), integrated on the GPU slab by slab (manufactured 3-D problems)
+    discretization_check = None
+    if args.h1 and not diffusion and cfg.dim == 3 and prob_name.endswith("manufactured"):
+        import dataclasses
+        from cmg_problems.diagnostics import h1_error_slabs
+        rcfg = dataclasses.replace(cmg.config_for(prob_name, Lmax), b1=min(12, 32 - cfg.k_u * (Lmax - 1)),
+                                   b2=12, N_ir=8)
+        ref = cmg.Solver(rcfg, stream=stream)
+        ref.set_rhs(prob.tables, prob.scale_exp)
+        ref.fmg_solve()
+        e_ref = h1_error_slabs(prob, lambda z0, nz: ref.decode_solution(z0, nz), Lmax)
+        del ref
+        e_cmg = h1_error_slabs(prob, lambda z0, nz: solver.decode_solution(z0, nz), Lmax)
+        discretization_check = {"h1_error": e_cmg, "h1_error_reference": e_ref, "ratio": e_cmg / e_ref,
+                                "criterion": "Sec. 7.1: ratio <= 2", "met": e_cmg <= 2 * e_ref,
+                                "reference": "Jacobi V(2,2), b1=%d, b2=12, N_ir=8" % rcfg.b1}
     # the FP32 cycle: its solution against the exact cycle's on the same planes
     fp32_vs_exact = None
     if cfg.arith == 1 and not diffusion:
@@ -488,6 +506,7 @@ def run_gpu(args, wl):
         "alg_bytes_per_step": reports[0]["alg_bytes"],
         "whole_solve_hbm_frac": whole_frac,
         "nodal_rel_err_sampled": nodal_rel,
+        "discretization_check": discretization_check,
         "fp32_vs_exact": fp32_vs_exact,
         "diffusion_vs_reference": diffusion_vs_reference,
         "roofline": roofline,
@@ -646,6 +665,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-h1", dest="h1", action="store_false",
+                    help="skip the H1 error check against a near-lossless solve (manufactured 3-D problems)")
     ap.add_argument("--arith", default="exact", choices=["exact", "fp32"],
                     help="exact V-cycle, or the binary32 V-cycle inside exact iterative refinement")
     ap.add_argument("--smoother", default="rbgs", choices=["rbgs", "jacobi"],
