@@ -7,7 +7,6 @@ library has not been built, importing this module raises ImportError.
 from __future__ import annotations
 
 import ctypes
-import dataclasses
 import os
 from typing import Optional, Tuple
 
