@@ -340,6 +340,22 @@ __device__ __forceinline__ double i64_to_f64_rne(long long v, int G, bool &bad) 
   return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1ull))));
 }
 
+// fl(a + b) in binary64 of two binary32 values with integer instructions: the
+// significands aligned in int64 and summed exactly, then rounded to nearest-even
+// (what the FP64 addition of the two exact doubles gives).  Zero, subnormal and
+// non-finite inputs, and exponents more than 38 apart, take the FP64 addition.
+__device__ __forceinline__ double f32_sum_f64(float a, float b, bool &bad) {
+  const unsigned ua = __float_as_uint(a), ub = __float_as_uint(b);
+  const int ea = (int)((ua >> 23) & 0xffu), eb = (int)((ub >> 23) & 0xffu);
+  if (ea == 0 || ea == 0xff || eb == 0 || eb == 0xff || ea - eb > 38 || eb - ea > 38)
+    return __dadd_rn((double)a, (double)b);
+  long long ma = (long long)((ua & 0x7fffffu) | 0x800000u), mb = (long long)((ub & 0x7fffffu) | 0x800000u);
+  if (ua >> 31) ma = -ma;
+  if (ub >> 31) mb = -mb;
+  const int e = ea < eb ? ea : eb;
+  return i64_to_f64_rne((ma << (ea - e)) + (mb << (eb - e)), e - 150, bad);  // value m 2^(e - 127 - 23)
+}
+
 __device__ __forceinline__ long long rounded_value(long long v, int q, int s) {
   return s > 0 ? shl((long long)q, s) : v;
 }

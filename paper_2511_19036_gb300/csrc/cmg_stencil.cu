@@ -730,7 +730,7 @@ struct ResidDiffBody {
     if (pt) {
       const int I = i + 1, J = j + 1, K = k + 1;
       ck53(F0);
-      const double kp = f32_to_f64(kat(I, J, K));
+      const float kp = kat(I, J, K);
       const long long nv[6] = {Pc[-1], Pc[1], Pc[-PW], Pc[PW], Fm, Fp};
       double acc = 0.0;
       // the oracle's acc + ((k_q + k_p) 0.5)(u_p - u_q) in FP64: u_p, u_q are exact
@@ -743,7 +743,7 @@ struct ResidDiffBody {
         const int Iq = I + (e == 0 ? -1 : e == 1 ? 1 : 0), Jq = J + (e == 2 ? -1 : e == 3 ? 1 : 0);
         const int Kq = K + (e == 4 ? -1 : e == 5 ? 1 : 0);
         ck53(nv[e]);
-        const double s = __dadd_rn(f32_to_f64(kat(Iq, Jq, Kq)), kp);
+        const double s = f32_sum_f64(kat(Iq, Jq, Kq), kp, bad);
         acc = __dadd_rn(acc, __dmul_rn(s, i64_to_f64_rne(F0 - nv[e], GF - 1, bad)));
       }
       double f;
