@@ -604,7 +604,8 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
   return CMG_OK;
 }
 
-// one Jacobi sweep on level l reading y[ycur] (unless y_zero), writing y[1-ycur]
+// one sweep (or, with rb, one colour's half-sweep) on level l reading y[ycur]
+// (unless y_zero), writing y[1-ycur]
 struct SweepOpts {
   bool has_z = false, write_y = true, corr = false, write_w = false, write_uh = false;
   int rb = 0;  // red-black half-sweep: 1 red nodes only, 2 black nodes only

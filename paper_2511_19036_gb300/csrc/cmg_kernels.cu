@@ -3,18 +3,22 @@
 // Every kernel reads its operands in the compact BFP form (Sec. 6.1.3 of the
 // paper), computes exactly in int64 fixed point on locally chosen grids (see
 // cmg_device.cuh), and writes BFP sections rounded to nearest-even (Sec. 4).
-// The stencil kernels march a CTA through z, keeping three planes of the
-// decoded stencil operand in shared memory (one x-block of 32 plus a one-node
-// halo, by TY rows plus halo); one warp owns one output block row.
+// The stencil kernels (cmg_stencil.cu, cmg_stencil_f32.cu) march a CTA through
+// z, keeping the planes k-1, k, k+1 of each column's decoded operand in
+// registers and the in-plane neighbours in two shared-memory plane buffers
+// (one x-block of 32 plus a one-node halo, by TY rows plus halo); one warp owns
+// one output block row.
 //
 // Kernels (one launch covers one level):
-//   k_sweep     weighted-Jacobi sweep y~ <- round(y~ + c (rc - A (y~ + P w_(l-1))))
-//               (Algorithm 1 smoothing step on eq. cfas), with optional fused
-//               correction u~ <- round(u~ + y~) (Algorithm 3), w_l = y~ + z_l and
-//               u^_l = u~_l + P u^_(l-1) for the next level / residual
+//   k_sweep     smoothing sweep y~ <- round(y~ + c (rc - A (y~ + P w_(l-1))))
+//               (Algorithm 1 smoothing step on eq. cfas) at every node, or at
+//               the nodes of one colour (red-black Gauss-Seidel half-sweep),
+//               with optional fused correction u~ <- round(u~ + y~)
+//               (Algorithm 3), w_l = y~ + z_l and u^_l = u~_l + P u^_(l-1) for
+//               the next level / residual
 //   k_residual  Algorithm 2 on the finest level: t = f - A (u~_L + P u^_(L-1)),
 //               r = round(t); optional first Jacobi sweep from y~ = 0 fused in,
-//               or t^ (Table 1 width) stored for the restriction chain
+//               or t^ (Table 1 width) restricted into the level L-1 accumulator
 //   k_restrict  d = rc - A y~ (or d = rc) scattered as R_l d into an int64
 //               accumulator by exact, order-free integer atomics
 //   k_acc_encode round an accumulator into BFP section(s) (+ optional first sweep)

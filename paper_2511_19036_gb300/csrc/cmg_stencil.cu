@@ -1,5 +1,6 @@
-// Stencil kernels of the compact FMG path for GB300 (sm_103a): the weighted
-// Jacobi sweep, the residual of Algorithm 2 and the restriction R_l = P_l^T.
+// Stencil kernels of the compact FMG path for GB300 (sm_103a): the smoothing
+// sweep (weighted Jacobi, or one colour's half of a red-black Gauss-Seidel
+// sweep), the residual of Algorithm 2 and the restriction R_l = P_l^T.
 //
 // Tiling.  A CTA of TY warps owns a 32 x TY column tile of a level and marches
 // it through up to ZC planes in z.  Thread (lane, ty) owns the column

@@ -1,5 +1,6 @@
-// FP32 V-cycle kernels (sm_103a): the weighted-Jacobi sweep and the
-// restriction of the compact cycle with binary32 arithmetic, inside the exact
+// FP32 V-cycle kernels (sm_103a): the smoothing sweep (weighted Jacobi, or a
+// red-black Gauss-Seidel half-sweep) and the restriction of the compact cycle
+// with binary32 arithmetic, inside the exact
 // iterative refinement (the precision split of Table 1: the cycle needs only
 // progressive(+m, b4) precision, the fmgResidual progressive(+p+m+1, b3)).
 //
