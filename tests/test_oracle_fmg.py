@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import cmg_problems as P
-from cmg_problems.diagnostics import h1_error
+from cmg_problems.diagnostics import exact_on_grid, h1_error
 from fem_dense import load_vector_exact, prolongation, stiffness
 
 CFG2 = dict(b1=4, b2=4, N=3, nu1=2, nu2=2, omega=0.75)   # 2-D widths (Table 2, Poisson 2D, p=1)
@@ -231,3 +231,21 @@ def test_slab_h1_error_equals_the_whole_array_one():
     a = h1_error(prob, U, 5)
     b = h1_error_slabs(prob, lambda z0, nz: Ut[z0:z0 + nz], 5, zchunk=3)
     assert abs(a - b) <= 1e-12 * a
+
+
+@pytest.mark.parametrize("name,levels", [("poisson2d_manufactured", (5, 6, 7, 8)),
+                                         ("poisson3d_manufactured", (4, 5, 6))])
+def test_nodal_error_is_second_order(name, levels):
+    """The discrete solution (lossless FMG, 12 IR iterations) converges to the
+    manufactured u at the nodes with order 2 (P1 on the uniform Kuhn mesh): a
+    dropped term or a wrong sign in the operator or in f breaks it."""
+    errs = []
+    for L in levels:
+        prob = P.make_problem(name, L)
+        o = oracle.Oracle.for_problem(prob, b1=0, b2=0, N=12, nu1=2, nu2=2, omega=0.75)
+        o.fmg()
+        U = np.asarray(o.decode_solution()).reshape(-1)
+        ue = np.asarray(exact_on_grid(prob, L)).reshape(-1)
+        errs.append(np.max(np.abs(U - ue)))
+    orders = -np.log2(np.array(errs[1:]) / np.array(errs[:-1]))
+    assert np.all(orders > 1.9), orders
