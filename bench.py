@@ -40,6 +40,8 @@ WORKLOADS = {
                       "GRF (sigma 0.5, seed 2), u_obs from m + GRF (sigma 0.1, seed 3); a step is the forward "
                       "compact FMG, J, and the backward (adjoint compact FMG + gradient kernel) through "
                       "torch.autograd"),
+    "diffusion3d_513": ("diffusion3d_grf", 9,
+                        "3-D -div(k grad u) = 1, 513^3 grid (511^3 = 1.33e8 DoF), k = exp(g) as diffusion3d_1025"),
     "diffusion3d_257": ("diffusion3d_grf", 8,
                         "3-D -div(k grad u) = 1, 257^3 grid, k = exp(g) as diffusion3d_1025"),
     "poisson3d_257": ("poisson3d_fourier", 8,
@@ -327,15 +329,19 @@ def run_gpu(args, wl):
     # dominant kernel: the finest-level Jacobi sweep (events on the solver's stream)
     sw_ms = sum(r["sweep_ms_total"] for r in reports)
     sw_n = sum(r["sweep_launches"] for r in reports)
-    sw_bytes = sum(r["sweep_alg_bytes"] for r in reports)
+    # a diffusion sweep also reads the nodal binary32 coefficient once per launch
+    # (4 B per node); the library's byte model counts sections and temporaries only
+    coef_bytes = 4.0 * ((1 << Lmax) + 1) ** cfg.dim if diffusion else 0.0
+    sw_bytes = sum(r["sweep_alg_bytes"] for r in reports) + sw_n * coef_bytes
     peak, peak_kind = measured_peak_hbm()
     achieved = (sw_bytes / sw_n) / (sw_ms / sw_n * 1e-3) / 1e9 if sw_n and sw_ms > 0 else None
     traffic_per_dof = read_traffic("k_sweep", wl + ("_rbgs" if cfg.smoother else "_jacobi"))
-    roofline = {"kernel": "k_sweep<3> finest level" if cfg.dim == 3 else "k_sweep<2> finest level",
+    roofline = {"kernel": "%s<%d> finest level" % ("k_sweep_f32" if cfg.arith else "k_sweep", cfg.dim),
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
                 "traffic": traffic_per_dof * dofs if traffic_per_dof else None,
                 "alg_bytes_per_launch": sw_bytes / sw_n if sw_n else None,
+                "coefficient_bytes_per_launch": coef_bytes,
                 "avg_launch_ms": sw_ms / sw_n if sw_n else None,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
     # the bound that holds: instruction issue (4 warp-instructions per SM and clock)
@@ -485,6 +491,8 @@ def run_gpu(args, wl):
                 cpu["single_core"] = {"value": one[0], "unit": "DoF/s", "cores": 1,
                                       "sample": "the same at %d DoF, %.1f s" % (one[2], one[1])}
     launches = int(sum(r["launches"] for r in reports))
+    if diffusion:  # a diffusion restriction step is two kernels, counted once by the library
+        launches += args.steps * sum(kernels.get(k, {}).get("launches", 0) for k in ("restrict_top", "restrict_lower"))
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -605,8 +613,12 @@ def run_adjoint(args, wl):
     solver.set_rhs_nodal(g)
     rep = solver.fmg_solve()
     peak, peak_kind = measured_peak_hbm()
-    ks = solver.kernel_stats()["sweep_top"]
-    achieved = ks["bytes"] / (ks["ms"] * 1e-3) / 1e9 if ks["ms"] > 0 else None
+    kst = solver.kernel_stats()
+    ks = kst["sweep_top"]
+    nres = kst["restrict_top"]["launches"] + kst["restrict_lower"]["launches"]
+    # plus the binary32 coefficient, read once by every finest-level sweep
+    coef_bytes = 4.0 * k.numel()
+    achieved = (ks["bytes"] + ks["launches"] * coef_bytes) / (ks["ms"] * 1e-3) / 1e9 if ks["ms"] > 0 else None
     if rank != 0:
         return 0
     cpu = None
@@ -643,11 +655,13 @@ def run_adjoint(args, wl):
         "J": float(J.detach()),
         "roofline": {"kernel": "k_sweep_f32<3> finest level (forward solve)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": None,
-                     "peak_kind": peak_kind},
+                     "coefficient_bytes_per_launch": coef_bytes, "peak_kind": peak_kind},
         "cpu_baseline": cpu,
         "e2e": {"value": job_rate(world, dofs, e2e_s), "unit": "DoF/s", "h2d_bytes_per_step": dofs * 8,
                 "d2h_bytes_per_step": dm.numel() * 4},
-        "gpu_launches": int(2 * rep["launches"] + 1),
+        # forward and adjoint solves (a restriction step is two kernels, counted once by
+        # the library) and the gradient kernel
+        "gpu_launches": int(2 * (rep["launches"] + nres) + 1),
         "clocks": clocks,
     }
     print(json.dumps(line))
