@@ -96,15 +96,20 @@ typedef struct {
 typedef struct {
   double solve_ms;        /* device time of the whole FMG (CUDA events) */
   int64_t dofs;           /* interior unknowns on the finest level */
-  int64_t launches;       /* kernels launched by the solve */
-  double alg_bytes;       /* algorithmic bytes moved by all kernels (model) */
+  int64_t launches;       /* launch steps of the solve: one per kernel, except
+                             that a restriction step of a diffusion problem
+                             (coef = 1) runs two kernels and counts once */
+  double alg_bytes;       /* algorithmic bytes moved by all kernels (model):
+                             sections, exponents and temporaries; the reads
+                             of a diffusion problem's coefficient field are
+                             not included */
   double persistent_bits; /* compact u~, r, y~ (x2) storage at L_max, all levels,
                              mantissas + exponents + padding */
   double temp_bytes;      /* int64 temporaries (levels <= L_max-1) and, with
                              nu1 = 0, the restriction chain's t^ sections
                              ((p+1) L_max + b1 bits, levels <= L_max-1) */
-  /* dominant kernel statistics (finest-level Jacobi sweep); valid when the
-   * context was created with timing enabled (cmg_set_timing). */
+  /* dominant kernel statistics (finest-level sweeps and residuals, bytes as
+   * alg_bytes); the times are valid when timing is enabled (cmg_set_timing). */
   double sweep_ms_total;
   int64_t sweep_launches;
   double sweep_alg_bytes;
