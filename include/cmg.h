@@ -220,7 +220,11 @@ cmg_status cmg_kernel_stats(cmg_ctx *ctx, int kind, int top, double *ms, int64_t
  * w_l = y~_l + z_l.  cmg_restrict(l): rc_(l-1) = round(R_l (rc_l - A_l y~_l));
  * CMG_EUNSUPPORTED without pre-smoothing, where the residual's restriction
  * chain forms every rc_l (Algorithm 2).  cmg_down(l) is cmg_smooth(l, nu1, 0)
- * then cmg_restrict(l); cmg_up(l) is cmg_smooth(l, nu2, 1). */
+ * then cmg_restrict(l); cmg_up(l) is cmg_smooth(l, nu2, 1).
+ * Errors: CMG_EINVAL for a NULL context, a level outside 2..L (L = cmg_level),
+ * or a call before cmg_start; CMG_EUNSUPPORTED for a cycle on a one-level
+ * hierarchy; data-dependent errors (CMG_ERANGE, CMG_ECORRUPT) surface at the
+ * next synchronising call (cmg_sync). */
 cmg_status cmg_start(cmg_ctx *ctx);
 cmg_status cmg_prolongate(cmg_ctx *ctx);
 cmg_status cmg_residual(cmg_ctx *ctx);
@@ -236,9 +240,16 @@ int cmg_level(const cmg_ctx *ctx); /* current FMG level L (0 before cmg_start) *
 /* Waits for the stream and reports data-dependent errors (CMG_ERANGE, ...). */
 cmg_status cmg_sync(cmg_ctx *ctx);
 
-/* Section access (synchronises).  words_host: nblocks * W uint32 where W is
- * cmg_section_width(); exps_host: nblocks int8.  cmg_set_section replaces a
- * section (for checkpoint restore and step-wise checking). */
+/* Section access (synchronises).  which: CMG_SEC_*; level 1..L.  words_host:
+ * nblocks * W uint32 where W is cmg_section_width(); exps_host: nblocks int8;
+ * both host memory of the caller, written before the call returns
+ * (cmg_get_section takes words_host = NULL to read the exponents only).
+ * cmg_set_section copies a caller's section in (for checkpoint restore and
+ * step-wise checking); W must lie in 2..32 and not exceed the width the section
+ * was allocated for.  Setting u~ invalidates the decoded u^ chain from that
+ * level up, which the next residual or decode rebuilds.  Errors: CMG_EINVAL for
+ * a bad context, which, level, width or NULL pointer; CMG_ECUDA; a pending
+ * data-dependent error of earlier work (as cmg_sync). */
 int64_t cmg_section_blocks(int dim, int level);
 int cmg_section_width(const cmg_ctx *ctx, int which, int level);
 cmg_status cmg_get_section(cmg_ctx *ctx, int which, int level, uint32_t *words_host,
@@ -249,11 +260,20 @@ cmg_status cmg_set_section(cmg_ctx *ctx, int which, int level, int W,
 /* Decode the standard representation u^_L (eq. compact-to-standard) of planes
  * z0 .. z0+nz-1 of the current finest level into out_dev (nz * n * n doubles,
  * dense, device memory of the caller; n = 2^L - 1; in 2-D z0 = 0, nz = 1).
- * Values needing more than 53 bits are rounded to nearest by the conversion. */
+ * Values needing more than 53 bits are rounded to nearest by the conversion.
+ * Synchronises.  Errors: CMG_EINVAL before cmg_start, for a NULL out_dev or
+ * for planes outside 0..n-1; CMG_ECORRUPT / CMG_ERANGE for an invalid code or
+ * an out-of-range value in the sections. */
 cmg_status cmg_decode_solution(cmg_ctx *ctx, int64_t z0, int64_t nz, double *out_dev);
 
-/* Checkpoint of the compact solution state (level, widths, sections).
- * cmg_state_save with buf == NULL returns the needed size in *len. */
+/* Checkpoint of the compact solution state (level, widths, sections of u~),
+ * in host memory of the caller; both calls synchronise.  cmg_state_save with
+ * buf == NULL returns the needed size in *len, and CMG_EINVAL when *len is
+ * smaller than that.  cmg_state_load accepts only a checkpoint written by a
+ * context with identical cmg_params (CMG_EINVAL otherwise, or when the buffer
+ * is truncated) and resumes the FMG at the saved level, with the corrections
+ * y~ zero; it may be called on a fresh context.  cmg_state_save returns
+ * CMG_EINVAL before cmg_start. */
 cmg_status cmg_state_save(cmg_ctx *ctx, void *buf, size_t *len);
 cmg_status cmg_state_load(cmg_ctx *ctx, const void *buf, size_t len);
 
