@@ -77,3 +77,35 @@ def test_host_side_parameter_validation(libpath):
     assert cmg.lib().cmg_section_blocks(3, 8) == 255 * 255 * 8
     assert cmg.lib().cmg_section_blocks(2, 8) == 255 * 8
     assert cmg.lib().cmg_section_blocks(4, 8) == -1
+
+
+def test_host_side_parameter_validation_edges(libpath):
+    from paper_2511_19036_gb300 import cmg
+
+    def check(name, L, **kw):
+        c = cmg.config_for(name, L, smoother=kw.pop("smoother", 0))
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return cmg.params_check(c)
+
+    # binary32 cycle: every r~ / y~ code must be exact in binary32
+    assert check("poisson3d_manufactured", 11, arith=1) == cmg.OK
+    assert check("poisson3d_manufactured", 11, arith=1, b2=14) == cmg.ERANGE
+    # diffusion runs only as the binary32 cycle, with pre-smoothing
+    assert check("diffusion3d_grf", 8) == cmg.OK
+    assert check("diffusion3d_grf", 8, arith=0) == cmg.EINVAL
+    assert check("diffusion3d_grf", 8, nu1=0) == cmg.EINVAL
+    for k, v in [("arith", 2), ("coef", 2), ("omega_log2den", 31), ("omega_log2den", -1), ("N_ir", 0),
+                 ("nu1", 65), ("b1", 1), ("k_u", -1)]:
+        assert check("poisson3d_fourier", 8, **{k: v}) == cmg.EINVAL, k
+    # without pre-smoothing t^ carries (p+1) L + b1 bits, at most 32
+    assert check("poisson3d_manufactured", 11, smoother=1) == cmg.OK
+    assert check("poisson3d_manufactured", 11, smoother=1, b1=10) == cmg.OK  # 32 bits
+    assert check("poisson3d_manufactured", 11, smoother=1, b1=11) == cmg.ERANGE  # 33 bits
+    assert check("poisson3d_manufactured", 11, b1=11) == cmg.OK  # Jacobi V(2,2): no chain
+    # 3-D: omega / 6 must be dyadic
+    assert check("poisson3d_fourier", 8, omega_num=1, omega_log2den=0) == cmg.EINVAL
+    # block and plane indices of the finest level fit 31 bits: 3-D L = 12 does, L = 13 not
+    assert check("poisson3d_fourier", 12, b1=4) == cmg.OK
+    assert check("poisson3d_fourier", 13, b1=4, b2=2, k_u=1) == cmg.ERANGE
+    assert check("poisson3d_fourier", 15) == cmg.EINVAL  # above the deepest hierarchy
