@@ -249,3 +249,33 @@ def test_nodal_error_is_second_order(name, levels):
         errs.append(np.max(np.abs(U - ue)))
     orders = -np.log2(np.array(errs[1:]) / np.array(errs[:-1]))
     assert np.all(orders > 1.9), orders
+
+
+@pytest.mark.parametrize("name,Lmax,cfg", [("poisson2d_manufactured", 5, CFG2),
+                                           ("poisson3d_manufactured", 4, CFG3),
+                                           ("poisson3d_fourier", 4, CFG3_RB)])
+def test_fmg_level_step_is_p1_interpolation(name, Lmax, cfg):
+    """Algorithm 3's level step in the compact representation (eq.
+    compact-to-standard): a zero finest section and coarser sections widened by
+    k_u = p + 1 zero bits, so the decoded solution on the new level is exactly
+    the P1 interpolation of the previous level's solution."""
+    prob = P.make_problem(name, Lmax)
+    o = oracle.Oracle.for_problem(prob, **cfg)
+    o.start()
+    for L in range(2, Lmax + 1):
+        if L > 2:
+            for _ in range(cfg["N"]):
+                o.ir_iteration()
+        coarse = o.decode_solution().ravel()
+        before = [o.get_section(0, l)[2].copy() for l in range(1, L)]
+        widths = [o.width(0, l) for l in range(1, L)]
+        o.next_level()
+        assert o.level == L
+        fine = o.decode_solution().ravel()
+        assert np.array_equal(fine, prolongation(prob.dim, L) @ coarse)
+        _, e, vals = o.get_section(0, L)
+        assert not vals.any() and np.all(e == -128)
+        for l in range(1, L):
+            assert o.width(0, l) == widths[l - 1] + 2
+            assert np.array_equal(o.get_section(0, l)[2], before[l - 1])
+    assert o.inexact == 0
