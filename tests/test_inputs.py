@@ -4,6 +4,8 @@
   derived here symbolically, independently of the hand-expanded separable
   terms in the generator, and must match the quantised tables to their 30-bit
   precision.
+- The Fourier-mode right-hand sides are read back by a sine transform: at
+  most 8 modes, wavenumbers in 1..8, and -Lap u = f mode by mode.
 - The diffusion coefficient's field g is a Gaussian random field with standard
   deviation sigma and squared-exponential covariance
   sigma^2 exp(-r^2 / (2 corr^2)). Its sample variance and correlation over
@@ -76,3 +78,26 @@ def test_coefficient_is_exp_g_in_binary32():
     assert k.dtype == np.float32 and k.shape == g.shape
     assert np.array_equal(k, np.exp(g).astype(np.float32))
     assert np.all(k > 0)
+
+
+@pytest.mark.parametrize("name,dim", [("poisson3d_fourier", 3), ("poisson2d_fourier", 2)])
+def test_fourier_modes_by_sine_transform(name, dim):
+    """C2's recipe (f = sum of 8 modes a_j prod sin(k pi x), k in 1..8; u with
+    -Lap u = f) read back from the nodal values by a DST-I, which represents
+    every sin(k pi x), k < 2^L, exactly on the interior nodes."""
+    from scipy.fft import dstn
+    L = 5
+    prob = P.make_problem(name, L)
+    idx = np.meshgrid(*([np.arange(prob.n1)] * dim), indexing="ij")
+    F = prob.rhs_float(tuple(idx))
+    U = prob.exact_u(*[(i + 1.0) * 2.0 ** -L for i in idx])
+    Fh, Uh = dstn(F, type=1), dstn(U, type=1)
+    tol = 1e-6 * np.max(np.abs(Fh))
+    on = np.abs(Fh) > tol
+    assert 1 <= on.sum() <= 8
+    k = np.argwhere(on) + 1  # wavenumbers of the modes present
+    assert k.min() >= 1 and k.max() <= 8
+    ksq = (k * k).sum(axis=1)
+    ratio = Fh[on] / Uh[on]
+    assert np.allclose(ratio, math.pi**2 * ksq, rtol=1e-6)
+    assert np.max(np.abs(Uh[~on])) <= 1e-6 * np.max(np.abs(Uh))
