@@ -109,3 +109,17 @@ def test_host_side_parameter_validation_edges(libpath):
     assert check("poisson3d_fourier", 12, b1=4) == cmg.OK
     assert check("poisson3d_fourier", 13, b1=4, b2=2, k_u=1) == cmg.ERANGE
     assert check("poisson3d_fourier", 15) == cmg.EINVAL  # above the deepest hierarchy
+
+
+def test_section_blocks_agree_with_the_oracle(libpath):
+    """The BFP layout's block count (rows of ceil((2^l - 1)/32) blocks), from the
+    library and from the oracle, on every level the library accepts."""
+    import oracle
+    from paper_2511_19036_gb300 import cmg
+    for dim in (2, 3):
+        for level in range(1, 15):
+            n = (1 << level) - 1
+            want = (n if dim == 3 else 1) * n * ((n + 31) // 32)
+            assert cmg.lib().cmg_section_blocks(dim, level) == want
+            if level <= 9:
+                assert oracle.nblocks(dim, level) == want
