@@ -32,7 +32,8 @@ def config_for(name: str, L_max: int, arith: int = 0, smoother: int = 0) -> Solv
 
     smoother = 1 gives the V(0,1) cycle with one red-black Gauss-Seidel sweep
     (Algorithm 1's cycle): in 2-D omega = 1 (plain Gauss-Seidel) at Table 2's
-    widths and N, which are the paper's values for this cycle; in 3-D omega =
+    widths and N, the paper's values for this cycle (found there with Q1
+    elements; they meet the Sec. 7.1 criterion with P1 too); in 3-D omega =
     3/4, so that the point factor omega/6 is dyadic and the exact cycle stays
     exact, with b2 one bit wider than for Jacobi V(2,2) (the cheapest widths
     and N found to meet the Sec. 7.1 criterion on the manufactured problem)."""
