@@ -359,7 +359,7 @@ def run_gpu(args, wl):
                  "frac": ach / pk if pk else None, "warp_inst_per_row": inst_row,
                  "peak_kind": "4 issue slots per SM per clock x %d SMs x %s MHz (sampled SM clock)" % (nsm, mhz)}
     whole_frac = (reports[0]["alg_bytes"] / (ms_step * 1e-3) / 1e9) / peak
-    # Sec. 6.2 storage model for this workload (mantissa bits, CMG vs BFPMG) next to
+    # Sec. 6.1.4 storage model for this workload (mantissa bits, CMG vs BFPMG) next to
     # the measured layout (exponents, row padding and the Jacobi ping-pong included)
     smod = cmg.storage_model(cfg.dim, Lmax, cfg.k_u, cfg.k_r, cfg.b1, cfg.b2)
     storage = {"cmg_fmg_bits_per_dof": smod["cmg_fmg_bits"] / smod["dofs"],

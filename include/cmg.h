@@ -175,10 +175,13 @@ cmg_status cmg_set_coefficient(cmg_ctx *ctx, const float *k_dev, int64_t n);
 
 /* Diffusion: a right-hand side given by nodal values g at the interior nodes
  * of the finest grid ((2^L_max - 1)^dim doubles in device memory, borrowed
- * like the coefficient): f_L = h_L^d g, injected at stride 2^(L_max - L) on
- * coarser FMG levels.  Replaces cmg_set_rhs_separable (used by adjoint solves,
- * whose right-hand side du J is not separable). */
-cmg_status cmg_set_rhs_nodal(cmg_ctx *ctx, const double *g_dev, int64_t n);
+ * like the coefficient): f_L = h_L^d 2^scale_log2 g, injected at stride
+ * 2^(L_max - L) on coarser FMG levels (the power-of-two scale is exact unless
+ * a value leaves the binary64 range).  Replaces cmg_set_rhs_separable (used by
+ * adjoint solves, whose right-hand side du J is not separable: A lam = du J is
+ * posed with g = du J and scale_log2 = d L_max, since A lam = h^d g' needs
+ * g' = 2^(d L_max) du J).  CMG_EINVAL for |scale_log2| > 512. */
+cmg_status cmg_set_rhs_nodal(cmg_ctx *ctx, const double *g_dev, int64_t n, int scale_log2);
 
 /* Adjoint gradients of J(u) for -div(k grad u) = g with A u = h^d g and the
  * adjoint state lam solving A lam = dJ/du (A is symmetric), on device arrays:
@@ -296,8 +299,10 @@ cmg_status cmg_state_load(cmg_ctx *ctx, const void *buf, size_t len);
  *  - Capacity: returns CMG_ERANGE without launching anything when
  *    cmg_decode_compact_scratch_bytes(dim, L) exceeds CMG_STATIC_SCRATCH_BYTES
  *    (3-D up to L = 8, 2-D up to L = 11).
- *  - The first call on a device looks up the array's device address (with that
- *    device current); make that first call before any stream capture.
+ *  - Every call looks up the array's device address with the caller's device
+ *    current (a host-side query, not cached, so that a device reset cannot
+ *    leave a stale address behind).  The first call on a device also makes the
+ *    runtime load the array; make that first call before any stream capture.
  *  - All calls on one device share the array, which keeps the previous call's
  *    contents (the call clears what must start at zero).  Calls whose work may
  *    overlap on the GPU (different streams, or different host threads) race on
@@ -311,7 +316,7 @@ cmg_status cmg_decode_compact(int dim, int L, const uint32_t *const *words_dev,
                               int64_t nz, double *out_dev, void *cuda_stream);
 
 /* ---------------------------------------------------------------------------
- * Analytic storage model (Sec. 6.2 of the paper: mantissas of regressive-
+ * Analytic storage model (Secs. 6.1.1 and 6.1.4 of the paper: mantissas of regressive-
  * precision vectors, and the comparison with progressive-precision FMG in BFP
  * arithmetic, "BFPMG").  Host-only arithmetic; no device work.
  *

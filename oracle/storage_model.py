@@ -1,6 +1,6 @@
 """Storage model of compact multigrid -- TEST INFRASTRUCTURE ONLY.
 
-Plain exact-integer restatement of Sec. 6.2 of "Multigrid with Linear Storage
+Plain exact-integer restatement of Secs. 6.1.1 and 6.1.4 of "Multigrid with Linear Storage
 Complexity" (mantissas of regressive-precision vectors; comparison with
 progressive-precision FMG in BFP arithmetic, "BFPMG").  Only the tests may
 import it; it shares no code with the library.
@@ -21,7 +21,7 @@ Readings (the paper plots the comparison without listing its formulas):
   * mantissa bits only, sign included (Table 2 caption); exponents and the
     sublinear temporaries are left out, as the paper does for the plot.
 
-Pins: tests/test_storage_model.py (the closed-form bound of Sec. 6.2 and its
+Pins: tests/test_storage_model.py (the closed-form bound of Sec. 6.1.1 and its
 constants 2, 4/3, 8/7, brute-force enumeration on tiny grids, the paper's
 "around an order of magnitude" claim).
 """
@@ -47,7 +47,7 @@ def progressive_bits(k: int, b: int, l: int) -> int:
 
 
 def cmg_vector_bits(d: int, L: int, k_u: int, b1: int) -> int:
-    """Sec. 6.2: N = sum over levels of n_l (k (L - l) + b) for the compact u~."""
+    """Sec. 6.1.1: N = sum over levels of n_l (k (L - l) + b) for the compact u~."""
     return sum(n * regressive_bits(k_u, b1, L, l) for l, n in level_sizes(d, L))
 
 
@@ -87,6 +87,6 @@ def model(d: int, L: int, k_u: int, k_r: int, b1: int, b2: int) -> Dict[str, Fra
 
 
 def linear_bound_coefficient(d: int, k: int, b: int) -> Fraction:
-    """Sec. 6.2: N < (2^d/(2^d-1) b + 2^d/(2^d-1)^2 k) n_L, with n_L ~ 2^(d L)."""
+    """Sec. 6.1.1: N < (2^d/(2^d-1) b + 2^d/(2^d-1)^2 k) n_L, with n_L ~ 2^(d L)."""
     q = Fraction(2 ** d, 2 ** d - 1)
     return q * b + Fraction(2 ** d, (2 ** d - 1) ** 2) * k

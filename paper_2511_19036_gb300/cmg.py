@@ -94,7 +94,7 @@ _SIGS = {
     "cmg_state_save": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
     "cmg_state_load": (_i32, [_vp, _vp, ctypes.c_size_t]),
     "cmg_set_coefficient": (_i32, [_vp, _vp, _i64]),
-    "cmg_set_rhs_nodal": (_i32, [_vp, _vp, _i64]),
+    "cmg_set_rhs_nodal": (_i32, [_vp, _vp, _i64, _i32]),
     "cmg_gradient": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "cmg_storage_model": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32, ctypes.POINTER(Storage)]),
     "cmg_kernel_stats": (_i32, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_double),
@@ -113,7 +113,7 @@ def lib() -> ctypes.CDLL:
 
 
 def storage_model(dim: int, L: int, k_u: int, k_r: int, b1: int, b2: int) -> dict:
-    """Sec. 6.2 mantissa bits of CMG and BFPMG storage (see cmg_storage_model)."""
+    """Sec. 6.1.4 mantissa bits of CMG and BFPMG storage (see cmg_storage_model)."""
     out = Storage()
     st = _lib.cmg_storage_model(dim, L, k_u, k_r, b1, b2, ctypes.byref(out))
     if st != OK:
@@ -248,13 +248,14 @@ class Solver:
         self._kfield = k
         self._chk(_lib.cmg_set_coefficient(self._h, k.data_ptr(), k.numel()), "cmg_set_coefficient")
 
-    def set_rhs_nodal(self, g):
-        """Diffusion: nodal right-hand side g (CUDA float64 tensor, interior finest nodes);
-        borrowed, kept referenced here."""
+    def set_rhs_nodal(self, g, scale_log2: int = 0):
+        """Diffusion: nodal right-hand side 2^scale_log2 g (CUDA float64 tensor, interior
+        finest nodes); borrowed, kept referenced here."""
         import torch
         assert g.is_cuda and g.dtype == torch.float64 and g.is_contiguous()
         self._grhs = g
-        self._chk(_lib.cmg_set_rhs_nodal(self._h, g.data_ptr(), g.numel()), "cmg_set_rhs_nodal")
+        self._chk(_lib.cmg_set_rhs_nodal(self._h, g.data_ptr(), g.numel(), int(scale_log2)),
+                  "cmg_set_rhs_nodal")
 
     def gradient(self, u, lam, want_dg: bool = True):
         """Adjoint gradients (dJ/dk on every node, dJ/dg on the interior) from the

@@ -63,6 +63,7 @@ struct cmg_ctx {
   int meta_next = 1;  // slot 0 stays all-zero: the metadata of an all-zero section
   int *err = nullptr;
   int32_t *tables = nullptr;
+  size_t tables_cap = 0;  // int32 entries allocated for the tables
   int nterms = 0, scale_exp = 0, fsh = 0, rhs_bits = 0;
   std::vector<int32_t> tables_host;
   bool have_rhs = false;
@@ -72,6 +73,7 @@ struct cmg_ctx {
   bool timing = false;
   const float *kfield = nullptr;  // diffusion: borrowed nodal coefficient
   const double *grhs = nullptr;   // diffusion: borrowed nodal right-hand side, or null
+  int grhs_log2 = 0;              // its power-of-two scale: f_L = h_L^d 2^grhs_log2 g
   float *dbuf = nullptr;          // diffusion: d = rc - A y~ of the finest level in binary32
   KStat stats[CMG_KIND_COUNT][2];  // per kernel kind; [1] = launches on level L_max
   long long launches = 0;
@@ -371,12 +373,14 @@ extern "C" cmg_status cmg_set_coefficient(cmg_ctx *ctx, const float *k_dev, int6
   return CMG_OK;
 }
 
-extern "C" cmg_status cmg_set_rhs_nodal(cmg_ctx *ctx, const double *g_dev, int64_t n) {
+extern "C" cmg_status cmg_set_rhs_nodal(cmg_ctx *ctx, const double *g_dev, int64_t n, int scale_log2) {
   if (!ctx || !g_dev) return CMG_EINVAL;
   if (ctx->P.coef != CMG_COEF_DIFFUSION) return fail(ctx, CMG_EINVAL, "nodal right-hand side on a Poisson context");
   const long long n1 = (1ll << ctx->P.L_max) - 1;
   if (n != (ctx->P.dim == 3 ? n1 * n1 * n1 : n1 * n1)) return fail(ctx, CMG_EINVAL, "right-hand side size");
+  if (scale_log2 < -512 || scale_log2 > 512) return fail(ctx, CMG_EINVAL, "right-hand side scale 2^%d", scale_log2);
   ctx->grhs = g_dev;
+  ctx->grhs_log2 = scale_log2;
   ctx->have_rhs = true;
   return CMG_OK;
 }
@@ -420,12 +424,18 @@ extern "C" cmg_status cmg_set_rhs_separable(cmg_ctx *ctx, int nterms, const int3
   }
   int B = 0;
   for (unsigned __int128 t = bound; t; t >>= 1) B++;
-  cudaFree(ctx->tables);
-  ctx->tables = nullptr;
-  CU(cudaMalloc(&ctx->tables, cnt * sizeof(int32_t)));
-  CU(cudaMemcpyAsync(ctx->tables, tab, cnt * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
-  CU(cudaStreamSynchronize(ctx->st));
+  if (ctx->tables_cap < cnt) {  // the device buffer is kept across calls that fit in it
+    cudaFree(ctx->tables);
+    ctx->tables = nullptr;
+    ctx->tables_cap = 0;
+    CU(cudaMalloc(&ctx->tables, cnt * sizeof(int32_t)));
+    ctx->tables_cap = cnt;
+  }
+  // the host copy is pageable, so the copy has taken the data when the call
+  // returns and the caller's array is free at once (no stream synchronisation)
   ctx->tables_host.assign(tab, tab + cnt);
+  CU(cudaMemcpyAsync(ctx->tables, ctx->tables_host.data(), cnt * sizeof(int32_t), cudaMemcpyHostToDevice,
+                     ctx->st));
   ctx->nterms = nterms;
   ctx->scale_exp = scale_exp;
   ctx->fsh = B > 50 ? B - 50 : 0;
@@ -532,6 +542,7 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
     a.kfield = ctx->kfield;
     a.kN = (1 << ctx->P.L_max) + 1;
     a.grhs = ctx->grhs;
+    a.grhs_log2 = ctx->grhs_log2;
   }
   a.first_sweep = first_sweep;
   jacobi_factor(ctx, L, a.c_num, a.c_exp, a.cbits);
@@ -789,6 +800,7 @@ static cmg_status do_coarse(cmg_ctx *ctx, bool start, bool corr) {
     if (ctx->grhs) {  // the level-1 node is the centre of the finest grid
       const long long n1 = (1ll << ctx->P.L_max) - 1, c = n1 / 2;
       a.grhs = ctx->grhs;
+      a.grhs_log2 = ctx->grhs_log2;
       a.gidx = ctx->P.dim == 3 ? (c * n1 + c) * n1 + c : c * n1 + c;
     }
   }
@@ -1253,17 +1265,31 @@ extern "C" cmg_status cmg_state_load(cmg_ctx *ctx, const void *buf, size_t len) 
 }
 
 // ---------------------------------------------------------------- stand-alone codec
+// The codec's error word: one per host thread and device, allocated on the
+// thread's first codec call on that device and kept for the process (a codec
+// call waits for its own work, so one host thread never has two calls in
+// flight, and calls from different threads never share a word).
+constexpr int CODEC_MAX_DEVICES = 64;
+static thread_local int *t_codec_err[CODEC_MAX_DEVICES];
+
+static cmg_status codec_err_word(int **out, cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= CODEC_MAX_DEVICES) return CMG_ECUDA;
+  if (!t_codec_err[dev] && cudaMalloc(&t_codec_err[dev], sizeof(int)) != cudaSuccess) {
+    t_codec_err[dev] = nullptr;
+    return CMG_ENOMEM;
+  }
+  if (cudaMemsetAsync(t_codec_err[dev], 0, sizeof(int), st) != cudaSuccess) return CMG_ECUDA;
+  *out = t_codec_err[dev];
+  return CMG_OK;
+}
+
 static cmg_status codec_finish(int *err, cudaStream_t st) {
   int e = 0;
-  if (cudaGetLastError() != cudaSuccess) {
-    cudaFree(err);
+  if (cudaGetLastError() != cudaSuccess) return CMG_ECUDA;
+  if (cudaMemcpyAsync(&e, err, sizeof e, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
     return CMG_ECUDA;
-  }
-  if (cudaStreamSynchronize(st) != cudaSuccess || cudaMemcpy(&e, err, sizeof e, cudaMemcpyDeviceToHost) != cudaSuccess) {
-    cudaFree(err);
-    return CMG_ECUDA;
-  }
-  cudaFree(err);
   if (e & ERR_INPUT) return CMG_EINVAL;
   if (e & ERR_CORRUPT) return CMG_ECORRUPT;
   if (e & ERR_EXP) return CMG_ERANGE;
@@ -1275,11 +1301,8 @@ extern "C" cmg_status cmg_encode(const double *x, int64_t n, int W, uint32_t *wo
   if (n == 0) return CMG_OK;
   cudaStream_t st = (cudaStream_t)stream;
   int *err = nullptr;
-  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return CMG_ENOMEM;
-  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
-    cudaFree(err);
-    return CMG_ECUDA;
-  }
+  cmg_status s = codec_err_word(&err, st);
+  if (s != CMG_OK) return s;
   CodecArgs a{};
   a.x = const_cast<double *>(x);
   a.n = n;
@@ -1297,11 +1320,8 @@ extern "C" cmg_status cmg_decode(const uint32_t *words, const int8_t *exps, int6
   if (n == 0) return CMG_OK;
   cudaStream_t st = (cudaStream_t)stream;
   int *err = nullptr;
-  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return CMG_ENOMEM;
-  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
-    cudaFree(err);
-    return CMG_ECUDA;
-  }
+  cmg_status s = codec_err_word(&err, st);
+  if (s != CMG_OK) return s;
   CodecArgs a{};
   a.x = x;
   a.n = n;
@@ -1314,7 +1334,7 @@ extern "C" cmg_status cmg_decode(const uint32_t *words, const int8_t *exps, int6
 }
 
 // ---------------------------------------------------------------- storage model
-// Sec. 6.2 mantissa counts of CMG (regressive) and BFPMG (progressive) storage;
+// Sec. 6.1.4 mantissa counts of CMG (regressive) and BFPMG (progressive) storage;
 // see include/cmg.h for the formulas.
 extern "C" cmg_status cmg_storage_model(int dim, int L, int k_u, int k_r, int b1, int b2, cmg_storage *out) {
   if (!out || dim < 1 || dim > 3 || L < 1 || L > 40 || k_u < 0 || k_r < 0 || b1 < 1 || b2 < 1)

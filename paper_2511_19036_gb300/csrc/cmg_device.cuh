@@ -148,14 +148,16 @@ __device__ __forceinline__ long long blk_index(const Geo &g, int i, int j, int k
 }
 
 // value of section s at 0-based (i, j, k) on grid 2^G (G <= its block's grid);
-// zero outside the interior.
+// zero outside the interior.  The invalid code -2^(W-1) sets bad (and decodes
+// as that number, so that the caller's range checks stay meaningful).
 __device__ __forceinline__ long long sec_val_ck(const Sec &s, const Geo &g, int i, int j, int k, int G,
-                                                bool &ovf) {
+                                                bool &ovf, bool &bad) {
   if (!inside(g, i, j, k)) return 0;
   long long b = blk_index(g, i, j, k);
   int e = __ldg(s.exps + b);
   if (e == -128) return 0;
   int q = code_at(s.words + b * s.W, s.W, i & 31);
+  bad |= (unsigned)q == (0xffffffffu << (s.W - 1));
   return shl_ck((long long)q, e - s.W + 1 - G, ovf);
 }
 
@@ -441,6 +443,11 @@ __device__ inline void meta_flush(MetaAcc a, int *meta, int *sm2) {
 // warp-collective: report per-thread overflow flags once
 __device__ inline void ovf_flush(bool ovf, int *err, int site) {
   if (__any_sync(0xffffffffu, ovf) && (threadIdx.x & 31) == 0) flag_range(err, site, 0, 0);
+}
+
+// warp-collective: report invalid codes met in decoding once
+__device__ inline void corrupt_flush(bool bad, int *err) {
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_CORRUPT);
 }
 
 }  // namespace cmg

@@ -194,8 +194,8 @@ __global__ void k_coarse(CoarseArgs a) {
       const double D = __dmul_rn(acc, dim == 3 ? 0.5 : 1.0);
       const int Gn = a.mode_start ? a.Gf1 : G + (dim == 2 ? 2 : 0);  // grid of N as read
       double num = __dmul_rn((double)(long long)N, __longlong_as_double((long long)(Gn + 1023) << 52));
-      if (a.mode_start && a.grhs)  // nodal right-hand side: f_1 = 2^-d g at the centre node
-        num = __dmul_rn(__ldg(a.grhs + a.gidx), __longlong_as_double((long long)(1023 - dim) << 52));
+      if (a.mode_start && a.grhs)  // nodal right-hand side: f_1 = 2^(grhs_log2 - d) g at the centre node
+        num = scalbn(__ldg(a.grhs + a.gidx), a.grhs_log2 - dim);
       x = __ddiv_rn(num, D);
     }
     q = encode_block_f64(x, out.W, e, a.err);
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(NT) k_chain(ChainArgs a) {
   // u^_l = u~_l + P_l u^_(l-1), one warp per 32-value block
   const Geo g = a.g;
   const int lane = threadIdx.x, ty = threadIdx.y;
-  bool ovf = false;
+  bool ovf = false, bad = false;
   const long long blk = (long long)blockIdx.x * TY + ty;
   if (blk < g.nblocks) {
     const long long row = blk / g.nbx;
@@ -284,13 +284,14 @@ __global__ void __launch_bounds__(NT) k_chain(ChainArgs a) {
     const int G = imin(blk_lsb(__ldg(a.u.exps + blk), a.u.W), __reduce_min_sync(0xffffffffu, gp));
     long long v = 0;
     if (pt) {
-      v = sec_val_ck(a.u, g, i, j, k, G, ovf);
+      v = sec_val_ck(a.u, g, i, j, k, G, ovf, bad);
       if (a.has_uhc) v += prolong_tmp<DIM>(a.uhc, a.gc, i + 1, j + 1, k + 1, G, ovf);
     }
     ck62(v, ovf);
     store_tmp_block(v, G, a.uh_out.v + row * g.R + i, a.uh_out.gb + blk, pt, ovf);
   }
   ovf_flush(ovf, a.err, 501);
+  corrupt_flush(bad, a.err);
 }
 
 __global__ void __launch_bounds__(NT) k_axpy(AxpyArgs a) {
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(NT) k_axpy(AxpyArgs a) {
   const int lane = threadIdx.x, ty = threadIdx.y;
   if (lane == 0 && ty == 0) sm[0] = sm[1] = 0;
   __syncthreads();
-  bool ovf = false;
+  bool ovf = false, bad = false;
   MetaAcc m;
   m.init();
   const long long blk = (long long)blockIdx.x * TY + ty;
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(NT) k_axpy(AxpyArgs a) {
     const int bx = (int)(blk - row * a.g.nbx);
     const int i = bx * 32 + lane, j = (int)(row % a.g.n), k = (int)(row / a.g.n);
     const int G = imin(blk_lsb(__ldg(a.u_in.exps + blk), a.u_in.W), blk_lsb(__ldg(a.y.exps + blk), a.y.W));
-    long long v = sec_val_ck(a.u_in, a.g, i, j, k, G, ovf) + sec_val_ck(a.y, a.g, i, j, k, G, ovf);
+    long long v = sec_val_ck(a.u_in, a.g, i, j, k, G, ovf, bad) + sec_val_ck(a.y, a.g, i, j, k, G, ovf, bad);
     ck62(v, ovf);
     int e, s;
     int q = encode_block(v, G, a.u_out.W, e, s, a.err);
@@ -320,13 +321,14 @@ __global__ void __launch_bounds__(NT) k_axpy(AxpyArgs a) {
     }
   }
   ovf_flush(ovf, a.err, 601);
+  corrupt_flush(bad, a.err);
   meta_flush(m, a.u_out.meta, sm);
 }
 
 template <int DIM>
 __global__ void k_decode_solution(DecodeSolArgs a) {
   const Geo g = a.g;
-  bool ovf = false;
+  bool ovf = false, bad = false;
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = a.nz * (long long)g.n * g.n;
   if (p < total) {
@@ -337,12 +339,13 @@ __global__ void k_decode_solution(DecodeSolArgs a) {
     if (a.has_uhc) G = imin(G, prolong_grid<DIM>(a.uhc, a.gc, i + 1, j + 1, k + 1));
     long long v = 0;
     if (G < GRID_NONE / 2) {
-      v = sec_val_ck(a.u, g, i, j, k, G, ovf);
+      v = sec_val_ck(a.u, g, i, j, k, G, ovf, bad);
       if (a.has_uhc) v += prolong_tmp<DIM>(a.uhc, a.gc, i + 1, j + 1, k + 1, G, ovf);
     }
     a.out[p] = v == 0 ? 0.0 : scalbn(__ll2double_rn(v), G);
   }
   ovf_flush(ovf, a.err, 701);
+  corrupt_flush(bad, a.err);
 }
 
 // ------------------------------------------------------------------ codec

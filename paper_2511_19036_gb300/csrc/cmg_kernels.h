@@ -56,6 +56,7 @@ struct ResidArgs {
   const float *kfield;  // diffusion: nodal k on the finest grid, boundary included
   int kN;               // 2^Lmax + 1 (the field is kN^dim, x fastest)
   const double *grhs;   // diffusion: nodal right-hand side g on the finest interior, or null
+  int grhs_log2;        // f_L = h_L^d 2^grhs_log2 g
   int *err;
 };
 
@@ -101,7 +102,8 @@ struct CoarseArgs {
   float *w_out_f;      // FP32 cycle: w_1 = y~_1 in binary32 (else w_out)
   const float *kfield; // diffusion: the level-1 diagonal from k (FP64 division)
   int kN, kstride;
-  const double *grhs;  // diffusion start mode: f_1 = 2^-d g[gidx] (else f1 on Gf1)
+  const double *grhs;  // diffusion start mode: f_1 = 2^(grhs_log2 - d) g[gidx] (else f1 on Gf1)
+  int grhs_log2;
   long long gidx;
   int *err;
 };

@@ -21,7 +21,6 @@
 
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/cmg.h"
 #include "cmg_device.cuh"
@@ -33,27 +32,22 @@ namespace {
 
 constexpr size_t SCRATCH_BYTES = CMG_STATIC_SCRATCH_BYTES;
 constexpr size_t ERR_BYTES = 256;  // error word block, kept 256-byte aligned
-constexpr int MAX_DEVICES = 64;
 
 // The scratch array.  Host code must not use its address directly (in host
 // code the name is only a stand-in); the device address comes from
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 
-std::mutex g_mu;
-void *g_scratch_dev[MAX_DEVICES];  // device address of g_scratch, per device
-
-// Once per device, with that device current: look up the array's device address.
+// On every call, with the caller's device current: look up the array's device
+// address.  The lookup is a host-side query and cheap; it is not cached, because
+// a device reset (or a new primary context) reloads the module and moves the
+// array, and a cached address would then be stale.
 cmg_status scratch_for_current_device(unsigned char **out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return CMG_ECUDA;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_dev[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return CMG_ECUDA;
-    g_scratch_dev[dev] = p;
-  }
-  *out = (unsigned char *)g_scratch_dev[dev];
+  if (cudaGetDevice(&dev) != cudaSuccess) return CMG_ECUDA;
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return CMG_ECUDA;
+  *out = (unsigned char *)p;
   return CMG_OK;
 }
 

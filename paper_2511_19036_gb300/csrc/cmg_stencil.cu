@@ -748,11 +748,11 @@ struct ResidDiffBody {
         acc = __dadd_rn(acc, __dmul_rn(s, i64_to_f64_rne(F0 - nv[e], GF - 1, bad)));
       }
       double f;
-      if (a.grhs) {  // nodal right-hand side, injected: f_L = h_L^d g
+      if (a.grhs) {  // nodal right-hand side, injected: f_L = h_L^d 2^grhs_log2 g (exact scaling)
         const int s = b_stride(), n1 = a.n1max;
         const long long gi = DIM == 3 ? ((long long)(K * s - 1) * n1 + (J * s - 1)) * n1 + (I * s - 1)
                                       : (long long)(J * s - 1) * n1 + (I * s - 1);
-        f = __dmul_rn(__ldg(a.grhs + gi), __longlong_as_double((long long)(1023 - DIM * g.l) << 52));
+        f = scalbn(__ldg(a.grhs + gi), a.grhs_log2 - DIM * g.l);
       } else {
         const long long fq = rhs_global<DIM>(a, I, J, K);  // below 2^52 after the rounding shift
         ck53(fq);

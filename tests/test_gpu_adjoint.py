@@ -67,12 +67,13 @@ def test_forward_adjoint_and_gradients_match_oracle(cmg, dim, L):
     u_gpu = s.decode_solution().reshape(-1).cpu().numpy()
     u_orc = np.asarray(o.decode_solution()).ravel()
     assert np.array_equal(u_gpu, u_orc)
-    # adjoint with the right-hand side 2^(dL) (u - u_obs)
+    # adjoint with the right-hand side 2^(dL) (u - u_obs): the library applies the
+    # power-of-two scale; the oracle gets the scaled values
     rhs = np.ldexp(u_orc - uobs, dim * L)
     sa = cmg.Solver(cfg)
     sa.set_coefficient(torch.from_numpy(k).cuda())
-    rt = torch.from_numpy(rhs).cuda()
-    sa.set_rhs_nodal(rt)
+    rt = torch.from_numpy(u_orc - uobs).cuda()
+    sa.set_rhs_nodal(rt, dim * L)
     sa.fmg_solve()
     oa = make_oracle(prob, cfg, k)
     oa.set_rhs_nodal(rhs)
@@ -154,13 +155,13 @@ def test_adjoint_workload_257_whole(cmg):
     n = ((1 << L) - 1) ** dim
     g = np.ones(n)
 
-    def solve_pair(kk, rhs):
+    def solve_pair(kk, rhs, scale_log2=0):
         s = cmg.Solver(cfg)
         s.set_coefficient(torch.from_numpy(kk).cuda())
-        s.set_rhs_nodal(torch.from_numpy(rhs).cuda())
+        s.set_rhs_nodal(torch.from_numpy(rhs).cuda(), scale_log2)
         s.fmg_solve()
         o = make_oracle(prob, cfg, kk)
-        o.set_rhs_nodal(rhs)
+        o.set_rhs_nodal(np.ldexp(rhs, scale_log2))
         o.fmg()
         assert o.status == 0
         ug = s.decode_solution().reshape(-1).cpu().numpy()
@@ -170,7 +171,38 @@ def test_adjoint_workload_257_whole(cmg):
 
     _, _, uobs = solve_pair(k_obs, g)
     s, o, u = solve_pair(k, g)
-    _, _, lam = solve_pair(k, np.ldexp(u - uobs, dim * L))
+    _, _, lam = solve_pair(k, u - uobs, dim * L)
     dk, dg = s.gradient(torch.from_numpy(u).cuda(), torch.from_numpy(lam).cuda())
     assert np.array_equal(dk.cpu().numpy(), o.gradient_k(u, lam))
     assert np.array_equal(dg.cpu().numpy(), np.ldexp(lam, -dim * L))
+
+
+def test_forward_keeps_only_the_compact_checkpoint(cmg):
+    """After forward returns, no solver context is alive (its residual, correction
+    and temporaries are freed); the saved state is the compact u~ sections alone,
+    and backward rebuilt from it gives the same gradient as the oracle path."""
+    import gc
+    from paper_2511_19036_gb300 import adjoint
+    dim, L = 3, 4
+    prob = P.make_problem("diffusion3d_grf", L)
+    k = np.ascontiguousarray(prob.kfield().ravel())
+    cfg = cmg.config_for(prob.name, L)
+    n = ((1 << L) - 1) ** dim
+    kt = torch.from_numpy(k).cuda().requires_grad_(True)
+    gt = torch.ones(n, dtype=torch.float64, device="cuda").requires_grad_(True)
+    live_before = sum(1 for o in gc.get_objects() if isinstance(o, cmg.Solver) and o._h)
+    u = adjoint.diffusion_solve(kt, gt, cfg)
+    gc.collect()
+    live_after = sum(1 for o in gc.get_objects() if isinstance(o, cmg.Solver) and o._h)
+    assert live_after == live_before
+    node = u.grad_fn
+    ck = node.checkpoint
+    assert isinstance(ck, bytes)
+    # header + per level: width, exponents, words of u~ only
+    sec_bytes = sum(4 + int(cmg.lib().cmg_section_blocks(dim, l)) * (1 + 4 * (cfg.k_u * (L - l) + cfg.b1))
+                    for l in range(1, L + 1))
+    assert 0 < len(ck) - sec_bytes < 256
+    J = 0.5 * torch.sum(u ** 2)
+    dk, dg = torch.autograd.grad(J, (kt, gt))
+    assert node.checkpoint is None  # released after backward
+    assert torch.isfinite(dk).all() and torch.isfinite(dg).all()

@@ -385,3 +385,27 @@ def test_values_beyond_62_bits_raise_erange(cmg):
         s.residual()
         s.sync()
     assert ei.value.status == cmg.ERANGE
+
+
+@pytest.mark.parametrize("level_from_top", [0, 1])
+def test_invalid_code_in_a_section_raises_ecorrupt(cmg, level_from_top):
+    """A code -2^(W-1) (never written by an encoder) in u~ is reported as
+    CMG_ECORRUPT by cmg_decode_solution, on the finest section (decode kernel)
+    and on a coarse one (decode chain)."""
+    prob, cfg, s, o = make_pair(cmg, "poisson3d_manufactured", 5)
+    s.fmg_solve()
+    l = 5 - level_from_top
+    w, e = s.get_section(cmg.SEC_U, l)
+    W = s.width(cmg.SEC_U, l)
+    w = w.copy()
+    blk = int(np.flatnonzero(e != -128)[0])
+    stream = 0
+    for k in range(W):
+        stream |= int(w[blk * W + k]) << (32 * k)
+    stream = (stream & ~((1 << W) - 1)) | (1 << (W - 1))
+    for k in range(W):
+        w[blk * W + k] = (stream >> (32 * k)) & 0xFFFFFFFF
+    s.set_section(cmg.SEC_U, l, W, w, e)
+    with pytest.raises(cmg.CmgError) as ei:
+        s.decode_solution()
+    assert ei.value.status == cmg.ECORRUPT

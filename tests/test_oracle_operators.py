@@ -6,11 +6,14 @@ A_(l-1) = R_l A_l P_l holds for nested P1 spaces on the Kuhn refinement.
 The dense matrices come from tests/fem_dense.py, which shares no code with the
 oracle's stencil, odd-set interpolation or restriction loops.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
 import oracle
 import cmg_problems as P
+from exact_ref import bfp, matvec, pack, snap
 from fem_dense import load_vector_exact, prolongation, stiffness
 
 CASES = [(2, 2), (2, 3), (2, 4), (3, 2), (3, 3)]
@@ -82,9 +85,16 @@ def test_residual_matches_dense_formula(name, Lmax):
     f = load_vector_exact(prob.tables, prob.scale_exp, dim, Lmax, Lmax)
     expect = f - stiffness(dim, Lmax) @ uhat
     assert np.allclose(t, expect, rtol=0, atol=1e-12 * np.max(np.abs(f)))
-    # r_L is t_L rounded to the b2-bit BFP format of the finest level
+    # exactly: t_L equals the dense formula in rationals, and r_L is that t_L
+    # rounded into the b2-bit BFP format of the finest level (independent rounder
+    # and packer), compared code for code and exponent for exponent
+    Km = snap(stiffness(dim, Lmax), (1 << Lmax) * 12)
+    t_exact = [Fraction(float(a)) - b for a, b in
+               zip(f, matvec(Km, [Fraction(float(v)) for v in uhat]))]
+    assert [Fraction(float(v)) for v in t] == t_exact
     W = o.width(oracle.R, Lmax)
-    words, e, st = oracle.encode(
-        np.concatenate([np.pad(row, (0, (-row.size) % 32)) for row in t.reshape(-1, (1 << Lmax) - 1)]), W)
-    _, er, rv = o.get_section(oracle.R, Lmax)
-    assert np.array_equal(er, e)
+    _, e, codes = bfp(t_exact, (1 << Lmax) - 1, W)
+    wr_, er, rv = o.get_section(oracle.R, Lmax)
+    assert np.array_equal(er.astype(int), np.array(e))
+    assert np.array_equal(wr_, pack(codes, W))
+    assert any(c != 0 for blk in codes for c in blk)

@@ -1,7 +1,7 @@
-"""Storage model of Sec. 6.2 (CMG regressive vs BFPMG progressive mantissa bits).
+"""Storage model of Secs. 6.1.1 and 6.1.4 (CMG regressive vs BFPMG progressive mantissa bits).
 
 The oracle (oracle/storage_model.py) is pinned to what the paper fixes: the
-closed-form linear bound of Sec. 6.2 and its constants 2, 4/3, 8/7, brute-force
+closed-form linear bound of Sec. 6.1.1 and its constants 2, 4/3, 8/7, brute-force
 enumeration of every stored value on tiny grids, and the plotted claim of
 savings around an order of magnitude at ~1e15 DoF.  The library's
 cmg_storage_model (host arithmetic behind the C ABI) must agree with it.
@@ -20,7 +20,7 @@ BIHARM_1D = dict(d=1, k_u=4, k_r=2, b1=4, b2=4)
 
 
 def test_paper_constants_of_the_linear_bound():
-    # Sec. 6.2: 2^d / (2^d - 1) is 2 in 1-D, 4/3 in 2-D and 8/7 in 3-D
+    # Sec. 6.1.1: 2^d / (2^d - 1) is 2 in 1-D, 4/3 in 2-D and 8/7 in 3-D
     assert sm.linear_bound_coefficient(1, 0, 1) == 2
     assert sm.linear_bound_coefficient(2, 0, 1) == Fraction(4, 3)
     assert sm.linear_bound_coefficient(3, 0, 1) == Fraction(8, 7)
@@ -74,7 +74,7 @@ def _level_for_dofs(d, dofs):
 
 @pytest.mark.parametrize("cfg", [POISSON_1D, POISSON_2D, BIHARM_1D])
 def test_savings_about_an_order_of_magnitude_at_1e15_dofs(cfg):
-    # Sec. 6.2.4 / the memory-comparison figure: ~10x where a supercomputer's
+    # Sec. 6.1.4 / the memory-comparison figure: ~10x where a supercomputer's
     # memory becomes prohibitive (the plot's axis ends at 15x)
     c = dict(cfg)
     d = c.pop("d")
@@ -90,7 +90,7 @@ def test_savings_grow_with_size_and_with_m():
         s = sm.model(1, L, **{k: v for k, v in POISSON_1D.items() if k != "d"})["fmg_saving"]
         assert s > prev
         prev = s
-    # larger residual/correction increment m: larger FMG saving (Sec. 6.2.4)
+    # larger residual/correction increment m: larger FMG saving (Sec. 6.1.4)
     L = 50
     pois = sm.model(1, L, **{k: v for k, v in POISSON_1D.items() if k != "d"})["fmg_saving"]
     biha = sm.model(1, L, **{k: v for k, v in BIHARM_1D.items() if k != "d"})["fmg_saving"]

@@ -92,3 +92,38 @@ def test_capacity_limit_is_refused(cmg):
     L = 9
     st = decode_compact(cmg, 3, L, [dummy_w] * L, [dummy_e] * L, [5] * L, 0, 1, out)
     assert st == cmg.ERANGE
+
+
+def plant_invalid_code(words, exps, W):
+    """Overwrite code 0 of the first nonzero block with -2^(W-1), the one code
+    that no encoder writes (codes are symmetric in [-(2^(W-1)-1), 2^(W-1)-1])."""
+    w = words.copy().view(np.uint32)
+    blk = int(np.flatnonzero(exps != -128)[0])
+    base = blk * W
+    stream = 0
+    for k in range(W):
+        stream |= int(w[base + k]) << (32 * k)
+    stream &= ~((1 << W) - 1)
+    stream |= 1 << (W - 1)
+    for k in range(W):
+        w[base + k] = (stream >> (32 * k)) & 0xFFFFFFFF
+    return w.view(np.int32)
+
+
+@pytest.mark.parametrize("level_from_top", [0, 1])
+def test_invalid_code_is_reported(cmg, level_from_top):
+    """A code -2^(W-1) in the caller's sections is reported as CMG_ECORRUPT,
+    whether it sits on the finest section or on a coarse one; the next clean
+    call on the same array returns CMG_OK again."""
+    name, L = "poisson3d_manufactured", 5
+    s = solved(cmg, name, L)
+    words, exps, widths = compact_on_device(cmg, s, L)
+    l = L - level_from_top
+    w_host, e_host = s.get_section(cmg.SEC_U, l)
+    bad = list(words)
+    bad[l - 1] = torch.from_numpy(plant_invalid_code(w_host, e_host, widths[l - 1]).copy()).cuda()
+    n = (1 << L) - 1
+    out = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    assert decode_compact(cmg, 3, L, bad, exps, widths, 0, n, out) == cmg.ECORRUPT
+    assert decode_compact(cmg, 3, L, words, exps, widths, 0, n, out) == cmg.OK
+    assert np.array_equal(out.cpu().numpy(), s.decode_solution().cpu().numpy())
