@@ -157,6 +157,18 @@ cmg_status cmg_create(const cmg_params *p, void *cuda_stream, cmg_ctx **out);
 void cmg_destroy(cmg_ctx *ctx);
 const char *cmg_last_error(const cmg_ctx *ctx); /* never NULL */
 cmg_status cmg_set_timing(cmg_ctx *ctx, int enable); /* per-kernel CUDA events */
+/* Specialised kernels (3-D exact path; on by default): the red half-sweep from
+ * y~ = 0, the black half-sweep with the correction of u~ and the residual with
+ * the restriction of t^_L run in kernels with 32-bit arithmetic where per-CTA
+ * and per-block bounds allow it (other tiles and blocks run exactly in 64 bits).
+ * They compute the same bits as the generic kernels; enable = 0 runs the
+ * generic kernels only (for comparisons).  Takes effect at the next launch. */
+cmg_status cmg_set_fast_kernels(cmg_ctx *ctx, int enable);
+/* CTAs (32 x 8 x 32-node tiles) the specialised kernels were launched with since
+ * the last cmg_start (or the solve's start), and how many of them left their
+ * tile to the generic kernel because the tile's footprint exceeds the kernel's
+ * number range; top = 1 counts only launches on level L_max.  Synchronises. */
+cmg_status cmg_fast_stats(cmg_ctx *ctx, int top, int64_t *ctas, int64_t *fallback_ctas);
 
 /* Right-hand side (matrix-free, Sec. 5.1): F(x) = 2^scale_exp * sum_t prod_a
  * T[t][a][i_a], with T an int32 table [nterms][dim][2^L_max - 1] sampled at the

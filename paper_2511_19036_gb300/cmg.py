@@ -71,6 +71,8 @@ _SIGS = {
     "cmg_destroy": (None, [_vp]),
     "cmg_last_error": (ctypes.c_char_p, [_vp]),
     "cmg_set_timing": (_i32, [_vp, _i32]),
+    "cmg_set_fast_kernels": (_i32, [_vp, _i32]),
+    "cmg_fast_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "cmg_set_rhs_separable": (_i32, [_vp, _i32, _vp, _i32]),
     "cmg_fmg_solve": (_i32, [_vp, ctypes.POINTER(Report)]),
     "cmg_start": (_i32, [_vp]),
@@ -185,7 +187,7 @@ def params_check(cfg: SolverConfig) -> int:
 class Solver:
     """Compact FMG context on the current CUDA device."""
 
-    def __init__(self, cfg: SolverConfig, stream=None, timing: bool = False):
+    def __init__(self, cfg: SolverConfig, stream=None, timing: bool = False, fast: bool = True):
         self.cfg = cfg
         self._p = to_params(cfg)
         self._stream = _stream_handle(stream)
@@ -196,6 +198,8 @@ class Solver:
         self._h = h
         if timing:
             _lib.cmg_set_timing(self._h, 1)
+        if not fast:
+            _lib.cmg_set_fast_kernels(self._h, 0)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -238,6 +242,16 @@ class Solver:
                                                 ctypes.byref(by)), "cmg_kernel_stats")
                 out["%s_%s" % (name, "top" if top else "lower")] = {
                     "ms": ms.value, "launches": n.value, "bytes": by.value}
+        return out
+
+    def fast_stats(self) -> dict:
+        """CTAs of the specialised kernels since the solve started, and how many left
+        their tile to the generic kernel (all levels and the finest level)."""
+        out = {}
+        for top, name in ((0, "all"), (1, "top")):
+            n, fb = ctypes.c_int64(), ctypes.c_int64()
+            self._chk(_lib.cmg_fast_stats(self._h, top, ctypes.byref(n), ctypes.byref(fb)), "cmg_fast_stats")
+            out[name] = {"ctas": n.value, "fallback_ctas": fb.value}
         return out
 
     def set_coefficient(self, k):

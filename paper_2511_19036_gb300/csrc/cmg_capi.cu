@@ -78,7 +78,17 @@ struct cmg_ctx {
   KStat stats[CMG_KIND_COUNT][2];  // per kernel kind; [1] = launches on level L_max
   long long launches = 0;
   double alg_bytes = 0;
+  // specialised 3-D kernels (cmg_fast.cu): on by default for the exact path
+  bool fast = true;
+  unsigned *fb_tiles = nullptr;  // fallback tile list (one level's worth of tiles)
+  int *fb_counts = nullptr;      // one zeroed count per specialised launch, FB_SLOTS in all
+  int fb_next = 0;
+  long long fast_ctas = 0, fast_ctas_top = 0;   // CTAs of specialised launches since cmg_start
+  long long fb_done = 0, fb_done_top = 0;       // fallback tiles of slots already summed
+  std::vector<char> fb_top;                     // slot on level L_max?
 };
+
+constexpr int FB_SLOTS = 4096;
 
 // ---------------------------------------------------------------- helpers
 static cmg_status fail(cmg_ctx *c, cmg_status s, const char *fmt, ...) {
@@ -272,6 +282,8 @@ extern "C" void cmg_destroy(cmg_ctx *ctx) {
     stat_reset(ctx->stats[k][1]);
   }
   cudaFree(ctx->dbuf);
+  cudaFree(ctx->fb_tiles);
+  cudaFree(ctx->fb_counts);
   cudaFree(ctx->meta_pool);
   cudaFree(ctx->err);
   cudaFree(ctx->tables);
@@ -307,6 +319,14 @@ extern "C" cmg_status cmg_create(const cmg_params *p, void *stream, cmg_ctx **ou
   if (r == CMG_OK) {
     chk(cudaMemsetAsync(ctx->meta_pool, 0, META_CAP * sizeof(int), ctx->st));
     chk(cudaMemsetAsync(ctx->err, 0, 8 * sizeof(int), ctx->st));
+  }
+  if (r == CMG_OK && p->dim == 3 && p->arith == CMG_ARITH_EXACT) {
+    // fallback tiles of the specialised kernels: at most every tile of the finest level
+    const Geo g = make_geo(3, p->L_max);
+    const size_t tiles = (size_t)g.nbx * ((g.n + TY - 1) / TY) * ((g.nz + ZC - 1) / ZC);
+    chk(cudaMalloc(&ctx->fb_tiles, tiles * sizeof(unsigned)));
+    chk(cudaMalloc(&ctx->fb_counts, FB_SLOTS * sizeof(int)));
+    if (r == CMG_OK) chk(cudaMemsetAsync(ctx->fb_counts, 0, FB_SLOTS * sizeof(int), ctx->st));
   }
   for (int l = 1; l <= p->L_max && r == CMG_OK; l++) {
     Level &v = ctx->lv[l];
@@ -349,6 +369,53 @@ extern "C" const char *cmg_last_error(const cmg_ctx *ctx) { return ctx ? ctx->ms
 extern "C" cmg_status cmg_set_timing(cmg_ctx *ctx, int enable) {
   if (!ctx) return CMG_EINVAL;
   ctx->timing = enable != 0;
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_set_fast_kernels(cmg_ctx *ctx, int enable) {
+  if (!ctx) return CMG_EINVAL;
+  ctx->fast = enable != 0;
+  return CMG_OK;
+}
+
+// sums the fallback counts of the slots used so far into fb_done (synchronises)
+static cmg_status fb_collect(cmg_ctx *ctx) {
+  if (!ctx->fb_counts || ctx->fb_next == 0) return CMG_OK;
+  std::vector<int> c(ctx->fb_next);
+  CU(cudaStreamSynchronize(ctx->st));
+  CU(cudaMemcpy(c.data(), ctx->fb_counts, c.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < ctx->fb_next; k++) {
+    ctx->fb_done += c[k];
+    if (ctx->fb_top[k]) ctx->fb_done_top += c[k];
+  }
+  CU(cudaMemsetAsync(ctx->fb_counts, 0, FB_SLOTS * sizeof(int), ctx->st));
+  ctx->fb_next = 0;
+  return CMG_OK;
+}
+
+// a zeroed fallback count for the next specialised launch on level l (the slots
+// are summed and cleared together, once every FB_SLOTS launches)
+static cmg_status fb_slot(cmg_ctx *ctx, int l, int **slot) {
+  if (ctx->fb_next >= FB_SLOTS) {
+    cmg_status s = fb_collect(ctx);
+    if (s) return s;
+  }
+  if ((int)ctx->fb_top.size() < FB_SLOTS) ctx->fb_top.resize(FB_SLOTS);
+  ctx->fb_top[ctx->fb_next] = l == ctx->P.L_max;
+  *slot = ctx->fb_counts + ctx->fb_next++;
+  return CMG_OK;
+}
+
+static long long tiles_of(const Geo &g) {
+  return (long long)g.nbx * ((g.n + TY - 1) / TY) * ((g.nz + ZC - 1) / ZC);
+}
+
+extern "C" cmg_status cmg_fast_stats(cmg_ctx *ctx, int top, int64_t *ctas, int64_t *fallback_ctas) {
+  if (!ctx || top < 0 || top > 1) return CMG_EINVAL;
+  cmg_status s = fb_collect(ctx);
+  if (s) return s;
+  if (ctas) *ctas = top ? ctx->fast_ctas_top : ctx->fast_ctas;
+  if (fallback_ctas) *fallback_ctas = top ? ctx->fb_done_top : ctx->fb_done;
   return CMG_OK;
 }
 
@@ -572,10 +639,20 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
   a.err = ctx->err;
   double bytes = sec_bytes(v.g, v.u.W) + (L > 1 ? tmp_bytes(a.gc) : 0) + sec_bytes(v.g, v.r.W) +
                  (first_sweep ? sec_bytes(v.g, v.r.W) : 0) + (chain ? 2 * tmp_bytes(a.gc) : 0);
+  if (!diff && ctx->fast && ctx->fb_tiles) {
+    a.tiles = ctx->fb_tiles;
+    if ((s = fb_slot(ctx, L, &a.ntiles))) return s;
+  }
+  bool fast = false;
   ev_begin(ctx, kstat(ctx, CMG_KIND_RESIDUAL, L));
   if (diff) launch_residual_diffusion(d, a, ctx->st);
-  else launch_residual(d, a, ctx->st);
+  else if (!(fast = a.tiles && launch_residual_fast(a, ctx->st))) launch_residual(d, a, ctx->st);
   ev_end(ctx, kstat(ctx, CMG_KIND_RESIDUAL, L), bytes);
+  if (fast) {
+    ctx->launches++;  // the generic kernel over the fallback tiles
+    ctx->fast_ctas += tiles_of(v.g);
+    if (L == ctx->P.L_max) ctx->fast_ctas_top += tiles_of(v.g);
+  }
   if ((s = launched(ctx, bytes))) return s;
   if (chain) {  // t^_l = round(R t^_(l+1)), r_l = round(t^_l) (Algorithm 2)
     for (int l = L; l >= 2; l--) {
@@ -677,10 +754,20 @@ static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
                  (o.write_uh ? tmp_bytes(v.g) + tmp_bytes(a.gc) : 0);
   if (ctx->P.arith == CMG_ARITH_FP32)  // binary32 w: half the bytes
     bytes -= 0.5 * ((o.has_z ? tmp_bytes(a.gc) : 0) + (o.write_w ? tmp_bytes(v.g) : 0));
+  bool fast = false;
+  if (ctx->P.arith != CMG_ARITH_FP32 && ctx->fast && ctx->fb_tiles) {
+    a.tiles = ctx->fb_tiles;
+    if ((s = fb_slot(ctx, l, &a.ntiles))) return s;
+  }
   ev_begin(ctx, kstat(ctx, CMG_KIND_SWEEP, l));
   if (ctx->P.arith == CMG_ARITH_FP32) launch_sweep_f32(d, a, ctx->st);
-  else launch_sweep(d, a, ctx->st);
+  else if (!(fast = a.tiles && launch_sweep_fast(a, ctx->st))) launch_sweep(d, a, ctx->st);
   ev_end(ctx, kstat(ctx, CMG_KIND_SWEEP, l), bytes);
+  if (fast) {
+    ctx->launches++;  // the generic kernel over the fallback tiles
+    ctx->fast_ctas += tiles_of(v.g);
+    if (l == ctx->P.L_max) ctx->fast_ctas_top += tiles_of(v.g);
+  }
   if ((s = launched(ctx, bytes))) return s;
   if (o.write_y) {
     v.ycur = 1 - v.ycur;
@@ -824,6 +911,11 @@ extern "C" cmg_status cmg_start(cmg_ctx *ctx) {
   ctx->meta_next = 1;
   CU(cudaMemsetAsync(ctx->meta_pool + 2 * ctx->meta_next, 0,
                      (size_t)(META_CAP - 2 * ctx->meta_next) * sizeof(int), ctx->st));
+  if (ctx->fb_counts) {
+    CU(cudaMemsetAsync(ctx->fb_counts, 0, FB_SLOTS * sizeof(int), ctx->st));
+    ctx->fb_next = 0;
+  }
+  ctx->fast_ctas = ctx->fast_ctas_top = ctx->fb_done = ctx->fb_done_top = 0;
   CU(cudaMemsetAsync(ctx->err, 0, 8 * sizeof(int), ctx->st));
   for (int l = 1; l <= ctx->P.L_max; l++) {
     Level &v = LV(ctx, l);

@@ -28,6 +28,11 @@ struct SweepArgs {
   float omega;         // diffusion: Jacobi weight (factor omega / D_p per node)
   int rb;              // 0: every node; 1 / 2: only the red / black nodes (red: the
                        // 1-based node numbers I + J [+ K] even), the others keep y~
+  // fallback tiles: the specialised kernel appends the tiles it leaves to the
+  // generic one; the generic kernel with list_mode = 1 runs only those
+  unsigned *tiles;
+  int *ntiles;
+  int list_mode;
   int *err;
 };
 
@@ -57,6 +62,9 @@ struct ResidArgs {
   int kN;               // 2^Lmax + 1 (the field is kN^dim, x fastest)
   const double *grhs;   // diffusion: nodal right-hand side g on the finest interior, or null
   int grhs_log2;        // f_L = h_L^d 2^grhs_log2 g
+  unsigned *tiles;      // fallback tiles (as in SweepArgs)
+  int *ntiles;
+  int list_mode;
   int *err;
 };
 
@@ -148,6 +156,13 @@ struct CodecArgs {
 
 void launch_sweep(int dim, const SweepArgs &a, cudaStream_t st);
 void launch_residual(int dim, const ResidArgs &a, cudaStream_t st);
+// the generic kernels over a fallback tile list (a.tiles, a.ntiles on the device)
+void launch_sweep_list(int dim, const SweepArgs &a, cudaStream_t st);
+void launch_residual_list(int dim, const ResidArgs &a, cudaStream_t st);
+// specialised 3-D Poisson kernels of the exact path (cmg_fast.cu); each returns
+// false (launching nothing) when the step is not one it covers
+bool launch_sweep_fast(const SweepArgs &a, cudaStream_t st);
+bool launch_residual_fast(const ResidArgs &a, cudaStream_t st);
 void launch_restrict(int dim, const RestrictArgs &a, cudaStream_t st);
 void launch_residual_diffusion(int dim, const ResidArgs &a, cudaStream_t st);
 

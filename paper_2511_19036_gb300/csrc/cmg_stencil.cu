@@ -400,7 +400,7 @@ struct SweepBody {
 };
 
 template <int DIM, int M>
-__global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
+__device__ __forceinline__ void sweep_tile(const SweepArgs &a, const Tile &T) {
   using F = SwF<M>;
   const bool has_y = F::fixed ? F::y : (bool)a.has_y, has_z = F::fixed ? F::z : (bool)a.has_z;
   const bool write_y = F::fixed ? F::wy : (bool)a.write_y, corr = F::fixed ? F::corr : (bool)a.corr;
@@ -410,7 +410,6 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
   __shared__ int smy[2], smu[2], smb[6];
   const Geo g = a.g;
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
-  const Tile T = make_tile(g);
   if (tid == 0) smy[0] = smy[1] = smu[0] = smu[1] = 0;
   const bool uring_wanted = write_uh && a.has_uhc;
   Bounds bs, bt, bu;
@@ -462,6 +461,21 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
   ovf_flush(b.ovf, a.err, 102);
   if (write_y) meta_flush(b.my, a.y_out.meta, smy);
   if (corr) meta_flush(b.mu, a.u_out.meta, smu);
+}
+
+// every tile of the level, or (list_mode) the fallback tiles the specialised
+// kernel left, one after the other per CTA
+template <int DIM, int M>
+__global__ void __launch_bounds__(NT, CMG_SWEEP_MINB) k_sweep(SweepArgs a) {
+  if (a.list_mode) {
+    const int n = *a.ntiles;
+    for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
+      sweep_tile<DIM, M>(a, tile_of_code(a.g, a.tiles[idx]));
+      __syncthreads();
+    }
+    return;
+  }
+  sweep_tile<DIM, M>(a, make_tile(a.g));
 }
 
 // ------------------------------------------------------------------ residual
@@ -599,7 +613,7 @@ struct ResidBody {
 };
 
 template <int DIM, int M>
-__global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
+__device__ __forceinline__ void residual_tile(const ResidArgs &a, const Tile &T) {
   const bool first_sweep = M == RS_FIRST ? true : (bool)a.first_sweep;
   const bool has_uhc = M == RS_FIRST ? true : (bool)a.has_uhc;
   __shared__ SmemAny sm;
@@ -608,7 +622,6 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   __shared__ int smr[2], smy[2], smb[6];
   const Geo g = a.g;
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
-  const Tile T = make_tile(g);
   if (tid == 0) smr[0] = smr[1] = smy[0] = smy[1] = 0;
   // the tile's slice of the separable right-hand side tables (Sec. 7 problems):
   // exact products need |sum| < 2^94 for the split accumulation
@@ -691,6 +704,19 @@ __global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
   ovf_flush(b.ovf, a.err, 202);
   meta_flush(b.mr, a.r_out.meta, smr);
   if (first_sweep) meta_flush(b.my, a.y_out.meta, smy);
+}
+
+template <int DIM, int M>
+__global__ void __launch_bounds__(NT, CMG_RESID_MINB) k_residual(ResidArgs a) {
+  if (a.list_mode) {
+    const int n = *a.ntiles;
+    for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
+      residual_tile<DIM, M>(a, tile_of_code(a.g, a.tiles[idx]));
+      __syncthreads();
+    }
+    return;
+  }
+  residual_tile<DIM, M>(a, make_tile(a.g));
 }
 
 // ------------------------------------------------------------------ diffusion residual
@@ -927,6 +953,33 @@ static void launch_sweep_dim(const SweepArgs &a, cudaStream_t st) {
 void launch_sweep(int dim, const SweepArgs &a, cudaStream_t st) {
   if (dim == 3) launch_sweep_dim<3>(a, st);
   else launch_sweep_dim<2>(a, st);
+}
+
+// the fallback tiles of a specialised 3-D launch: a fixed grid of CTAs that
+// each read the list length and run their share (usually none)
+static unsigned list_grid(const Geo &g) {
+  const long long tiles = (long long)stencil_grid(g).x * stencil_grid(g).y * stencil_grid(g).z;
+  return (unsigned)(tiles < 456 ? tiles : 456);
+}
+
+void launch_sweep_list(int dim, const SweepArgs &a, cudaStream_t st) {
+  SweepArgs b = a;
+  b.list_mode = 1;
+  b.rb = a.rb;
+  const dim3 t(32, TY);
+  int m = SW_GENERIC;
+  if (!a.has_y && a.has_z && a.write_y && !a.corr && !a.write_w && !a.write_uh) m = SW_UP0;
+  else if (a.has_y && a.corr && a.has_z && !a.write_y && !a.write_w && !a.write_uh) m = SW_UP_CORR;
+  if (dim != 3) return;
+  if (m == SW_UP0) k_sweep<3, SW_UP0><<<list_grid(a.g), t, 0, st>>>(b);
+  else if (m == SW_UP_CORR) k_sweep<3, SW_UP_CORR><<<list_grid(a.g), t, 0, st>>>(b);
+  else k_sweep<3, SW_GENERIC><<<list_grid(a.g), t, 0, st>>>(b);
+}
+
+void launch_residual_list(int dim, const ResidArgs &a, cudaStream_t st) {
+  ResidArgs b = a;
+  b.list_mode = 1;
+  if (dim == 3) k_residual<3, RS_GENERIC><<<list_grid(a.g), dim3(32, TY), 0, st>>>(b);
 }
 
 void launch_residual(int dim, const ResidArgs &a, cudaStream_t st) {

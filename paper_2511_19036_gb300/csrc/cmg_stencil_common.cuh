@@ -99,16 +99,32 @@ struct Tile {
   int cr0, cx0;  // coarse row / column of ring entry (0, 0)
 };
 
-__device__ __forceinline__ Tile make_tile(const Geo &g) {
+__device__ __forceinline__ Tile make_tile_at(const Geo &g, int bx, int by, int bz) {
   Tile T;
-  T.bx = blockIdx.x;
+  T.bx = bx;
   T.x0 = T.bx * 32;
-  T.j0 = blockIdx.y * TY;
-  T.k0 = blockIdx.z * ZC;
+  T.j0 = by * TY;
+  T.k0 = bz * ZC;
   T.k1 = imin(g.nz, T.k0 + ZC);
   T.cr0 = ((T.j0 - 1) >> 1) - 1;
   T.cx0 = ((T.x0 - 1) >> 1) - 1;
   return T;
+}
+
+__device__ __forceinline__ Tile make_tile(const Geo &g) { return make_tile_at(g, blockIdx.x, blockIdx.y, blockIdx.z); }
+
+// Fallback tile lists: a CTA of a specialised kernel whose footprint does not fit
+// that kernel's number range appends its tile, and the generic kernel of the
+// same step then runs the listed tiles only.  Entry: bx | by << 10 | bz << 22
+// (blocks per row < 1024, row tiles < 4096, plane tiles < 1024 for L <= 14).
+__device__ __forceinline__ unsigned tile_code(const Tile &T) {
+  return (unsigned)T.bx | ((unsigned)(T.j0 / TY) << 10) | ((unsigned)(T.k0 / ZC) << 22);
+}
+__device__ __forceinline__ Tile tile_of_code(const Geo &g, unsigned c) {
+  return make_tile_at(g, (int)(c & 1023u), (int)((c >> 10) & 4095u), (int)(c >> 22));
+}
+__device__ __forceinline__ void tile_push(unsigned *list, int *count, const Tile &T) {
+  list[atomicAdd(count, 1)] = tile_code(T);
 }
 
 // One decode slot of a thread: a fixed (i, j) column of the CTA footprint.
