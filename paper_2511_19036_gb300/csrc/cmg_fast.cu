@@ -152,10 +152,21 @@ struct Packer {
   bool bad_exp;
 };
 
+// Width 4 packs inside the warp: 8 codes per word, gathered by a butterfly of
+// ORs over groups of 8 lanes; lane 8w writes word w.  (W = 4 is the finest-level
+// residual and correction width of the red-black configurations.)
+__device__ __forceinline__ void pack_w4(int q, uint32_t *words, int lane) {
+  uint32_t v = ((uint32_t)q & 15u) << (4 * (lane & 7));
+  v |= __shfl_xor_sync(FULL, v, 1);
+  v |= __shfl_xor_sync(FULL, v, 2);
+  v |= __shfl_xor_sync(FULL, v, 4);
+  if ((lane & 7) == 0) words[lane >> 3] = v;
+}
+
 template <int WC>
 __device__ __forceinline__ void pack_plane(Packer &pk, const Sec &out, const Geo &g, const Tile &T, int k,
                                            const int *cs, const int *ce) {
-  if (pk.job.on && T.j0 + pk.job.b < g.n) {
+  if (WC != 4 && pk.job.on && T.j0 + pk.job.b < g.n) {
     const long long blk = ((long long)k * g.n + T.j0 + pk.job.b) * g.nbx + T.bx;
     out.words[blk * (WC ? WC : pk.W) + pk.job.kw] = pack_word<WC>(cs + pk.job.b * CSW, pk.job, pk.W);
   }
@@ -417,7 +428,8 @@ __global__ void __launch_bounds__(NT, MODE == 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
       q = qu;
       e = euo;
     }
-    cs[k & 1][ty * CSW + lane] = (int)((unsigned)q & cmask);
+    if constexpr (WO == 4) pack_w4(q, out.words + ((long long)k * pb + bip) * 4, lane);
+    else cs[k & 1][ty * CSW + lane] = (int)((unsigned)q & cmask);
     if (lane == 0) ce[k & 1][ty] = e;
   };
 
@@ -525,7 +537,9 @@ __device__ __forceinline__ int enc64b(long long v, int G, int W, int bmax, int &
 // right-hand side is formed exactly from the separable tables with 32 x 32-bit
 // multiply-adds; x-adjacent contributions to the same coarse node are added in
 // the warp before the atomics.
+template <int NTERMS, int WR>  // right-hand-side terms and r~ width (0: run time)
 __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArgs a) {
+  const int nterms = NTERMS ? NTERMS : a.nterms;
   __shared__ long long Fs[2][PLANE];
   __shared__ long long ring[4 * CRX];
   __shared__ RhsTab rs;
@@ -539,13 +553,13 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
   const bool rowok = j < g.n, pt = rowok && i < g.n;
   {  // the tile's slice of the separable tables
     const int stride = 1 << (a.Lmax - g.l), n1 = a.n1max;
-    for (int t = 0; t < a.nterms; t++) {
+    for (int t = 0; t < nterms; t++) {
       const int32_t *Tt = a.tables + (long long)t * 3 * n1;
       const long long p = pt ? (long long)__ldg(Tt + (i + 1) * stride - 1) * __ldg(Tt + n1 + (j + 1) * stride - 1) : 0;
       const int lo = (int)((p & 0x7fffffffll) ^ 0x40000000ll) - 0x40000000;
       rs.pxy[t][tid] = make_int2(lo, (int)((p - lo) >> 31));
     }
-    for (int idx = tid; idx < a.nterms * ZC; idx += NT) {
+    for (int idx = tid; idx < nterms * ZC; idx += NT) {
       const int t = idx / ZC, r = idx - t * ZC, kk = T.k0 + r;
       rs.tz[t][r] = kk < g.nz ? __ldg(a.tables + (long long)t * 3 * n1 + 2 * n1 + (kk + 1) * stride - 1) : 0;
     }
@@ -576,7 +590,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
   // do not prove the range, every shifted value is checked (as the generic kernel does)
   const bool fast = Mt - Gt <= 62, dfast = Mt - Gd <= 57;
   bool ovf = false;
-  const int Wr = a.r_out.W, Wt = a.Wt, Ws = a.u.W;
+  const int Wr = WR ? WR : a.r_out.W, Wt = a.Wt, Ws = a.u.W;
   const unsigned cmask = Wr == 32 ? FULL : (1u << Wr) - 1u;
   Packer pk = make_packer(Wr);
   const int bip = rowok ? j * g.nbx + T.bx : 0;
@@ -622,12 +636,24 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     if (pt) {
       // F_q = sum_t (T_x T_y) T_z exactly: A 2^31 + B0 + B1, then f = RNE(F / 2^fsh)
       long long A = 0, B0 = 0, B1 = 0;
-      for (int q = 0; q < a.nterms; q++) {
-        const int2 p = rs.pxy[q][tid];
-        const int z = rs.tz[q][k - T.k0];
-        A += (long long)p.y * z;
-        if (q < 4) B0 += (long long)p.x * z;
-        else B1 += (long long)p.x * z;
+      if constexpr (NTERMS != 0) {
+#pragma unroll
+        for (int q = 0; q < NTERMS; q++) {
+          const int2 p = rs.pxy[q][tid];
+          const int z = rs.tz[q][k - T.k0];
+          A += (long long)p.y * z;
+          if (q < 4) B0 += (long long)p.x * z;
+          else B1 += (long long)p.x * z;
+        }
+      } else {
+#pragma unroll 1
+        for (int q = 0; q < nterms; q++) {
+          const int2 p = rs.pxy[q][tid];
+          const int z = rs.tz[q][k - T.k0];
+          A += (long long)p.y * z;
+          if (q < 4) B0 += (long long)p.x * z;
+          else B1 += (long long)p.x * z;
+        }
       }
       long long lo = (B0 & 0x7fffffffll) + (B1 & 0x7fffffffll);
       const long long hi = A + (B0 >> 31) + (B1 >> 31) + (lo >> 31);
@@ -643,7 +669,8 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     const int bmax = block_bitlen(t);
     int e, sh;
     const int qr = enc64b(t, Gt, Wr, bmax, e, sh, a.err);
-    cs[k & 1][ty * CSW + lane] = (int)((unsigned)qr & cmask);
+    if constexpr (WR == 4) pack_w4(qr, a.r_out.words + ((long long)k * pb + bip) * 4, lane);
+    else cs[k & 1][ty * CSW + lane] = (int)((unsigned)qr & cmask);
     if (lane == 0) ce[k & 1][ty] = e;
     int et, stt;
     const int qt = enc64b(t, Gt, Wt, bmax, et, stt, a.err);
@@ -697,7 +724,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     if (k + 2 <= T.k1) rn2 = raw_at(own, k + 2);
     if (has_h && k + 2 < T.k1) hn2 = raw_at(hal, k + 2);
     __syncthreads();
-    if (k > T.k0) pack_plane<0>(pk, a.r_out, g, T, k - 1, cs[(k - 1) & 1], ce[(k - 1) & 1]);
+    if (k > T.k0) pack_plane<WR>(pk, a.r_out, g, T, k - 1, cs[(k - 1) & 1], ce[(k - 1) & 1]);
     const long long Fp = F_at(own, rn, k + 1);
     if (k + 1 < T.k1) {
       long long *nxt = Fs[(k + 1) & 1];
@@ -717,7 +744,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     hn = hn2;
   }
   __syncthreads();
-  pack_plane<0>(pk, a.r_out, g, T, T.k1 - 1, cs[(T.k1 - 1) & 1], ce[(T.k1 - 1) & 1]);
+  pack_plane<WR>(pk, a.r_out, g, T, T.k1 - 1, cs[(T.k1 - 1) & 1], ce[(T.k1 - 1) & 1]);
   packer_flush(pk, a.r_out.meta, a.err);
   ovf_flush(ovf, a.err, 202);
 }
@@ -762,7 +789,11 @@ bool launch_residual_fast(const ResidArgs &a, cudaStream_t st) {
   if (a.g.nz == 1 || !a.tiles || !a.ntiles || a.first_sweep || !a.fuse_restrict || !a.has_uhc || a.kfield ||
       a.grhs || a.nterms < 1 || a.nterms > FMAXT || a.rhs_bits > 94 || a.fsh < 32 || a.Wt > 31)
     return false;
-  k_fast_resid<<<fast_grid(a.g), dim3(32, TY), 0, st>>>(a);
+  const dim3 grid = fast_grid(a.g), b(32, TY);
+  const bool w4 = a.r_out.W == 4;
+  if (a.nterms == 4 && w4) k_fast_resid<4, 4><<<grid, b, 0, st>>>(a);
+  else if (a.nterms == 8 && w4) k_fast_resid<8, 4><<<grid, b, 0, st>>>(a);
+  else k_fast_resid<0, 0><<<grid, b, 0, st>>>(a);
   launch_residual_list(3, a, st);
   return true;
 }
