@@ -344,6 +344,22 @@ def run_gpu(args, wl):
                 "coefficient_bytes_per_launch": coef_bytes,
                 "avg_launch_ms": sw_ms / sw_n if sw_n else None,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
+    # the same launches against the survey's algorithmic bytes (bits per finest DoF of
+    # mantissas, exponent bytes and the coarse sources each launch must touch once):
+    # red-black: red = r + z-source + y~ written, black = y~ + r + z-source + u~ read and
+    # written; Jacobi: down = 3 y~/r sections, up = the same + z-source, last up = 2
+    # sections + z-source + u~ read and written.  z-source = (b2 + 1.25)/8 + 1.
+    sec_r, sec_u = cfg.b2 + 0.25, cfg.b1 + 0.25
+    zsrc = (cfg.b2 + 1.25) / 8 + 1
+    if cfg.smoother:
+        survey_bits = ((2 * sec_r + zsrc) + (2 * sec_r + zsrc + 2 * sec_u)) / 2
+    else:
+        survey_bits = (3 * sec_r + (3 * sec_r + zsrc) + (2 * sec_r + zsrc + 2 * sec_u)) / 3
+    if achieved:
+        roofline["survey_bytes_per_dof"] = survey_bits / 8
+        ach_s = survey_bits / 8 * dofs / (sw_ms / sw_n * 1e-3) / 1e9
+        roofline["achieved_survey"] = ach_s
+        roofline["frac_survey"] = ach_s / peak
     # the bound that holds: instruction issue (4 warp-instructions per SM and clock)
     # with the ncu instruction count per 32-value row of the same kernels
     prof_wl = wl + ("_rbgs" if cfg.smoother else "_jacobi")
@@ -453,24 +469,32 @@ def run_gpu(args, wl):
         discretization_check = {"h1_error": e_cmg, "h1_error_reference": e_ref, "ratio": e_cmg / e_ref,
                                 "criterion": "Sec. 7.1: ratio <= 2", "met": e_cmg <= 2 * e_ref,
                                 "reference": "Jacobi V(2,2), b1=%d, b2=12, N_ir=8" % rcfg.b1}
-    # the FP32 cycle: its solution against the exact cycle's on the same planes
+    # the precision split (binary32 cycle inside the exact refinement) against the
+    # exact cycle, on the same GPU and problem, after the timed region: the other
+    # form is solved once (its device time by CUDA events on the solver's stream),
+    # and both solutions are compared on the sampled planes
     fp32_vs_exact = None
-    if cfg.arith == 1 and not diffusion:
-        cfg64 = cmg.config_for(prob_name, Lmax, smoother=cfg.smoother)
-        ref = cmg.Solver(cfg64, stream=stream)
+    if not diffusion and not args.no_compare:
+        other = cmg.config_for(prob_name, Lmax, arith=0 if cfg.arith else 1, smoother=cfg.smoother)
+        ref = cmg.Solver(other, stream=stream)
         ref.set_rhs(prob.tables, prob.scale_exp)
-        ref.fmg_solve()
-        dmax, umax, err64 = 0.0, 0.0, []
+        ref_ms = ref.fmg_solve()["solve_ms"]
+        dmax, umax, err_other = 0.0, 0.0, []
         for z in planes:
             a = solver.decode_solution(z, 1).cpu().numpy()[0]
             b = ref.decode_solution(z, 1).cpu().numpy()[0]
             Y, X = np.meshgrid(x, x, indexing="ij")
             ue = prob.exact_u(X, Y, (z + 1) * h) if cfg.dim == 3 else prob.exact_u(X, Y)
             dmax = max(dmax, float(np.max(np.abs(a - b))))
-            umax = max(umax, float(np.max(np.abs(b))))
-            err64.append(float(np.max(np.abs(b - ue))))
-        fp32_vs_exact = {"max_rel_diff_sampled": dmax / umax,
-                         "nodal_rel_err_exact_cycle": max(err64) / max(norms)}
+            umax = max(umax, float(np.max(np.abs(a if cfg.arith else b))))
+            err_other.append(float(np.max(np.abs(b - ue))))
+        exact_ms, f32_ms = (ms_step, ref_ms) if cfg.arith == 0 else (ref_ms, ms_step)
+        e32, e64 = (max(err_other) / max(norms), nodal_rel) if cfg.arith == 0 else \
+            (nodal_rel, max(err_other) / max(norms))
+        fp32_vs_exact = {"max_rel_diff_sampled": dmax / umax, "exact_cycle_ms": exact_ms,
+                         "fp32_cycle_ms": f32_ms, "nodal_rel_err_exact_cycle": e64,
+                         "nodal_rel_err_fp32_cycle": e32,
+                         "note": "one solve of the other form after the timed region"}
         del ref
 
     if rank != 0:
@@ -518,6 +542,7 @@ def run_gpu(args, wl):
         "diffusion_vs_reference": diffusion_vs_reference,
         "roofline": roofline,
         "issue_roofline": issue,
+        "fast_kernels": solver.fast_stats(),
         "kernels_last_step": kernels,
         "storage_model": storage,
         "cpu_baseline": cpu,
@@ -678,6 +703,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the solve of the other arithmetic (binary32 cycle / exact cycle)")
     ap.add_argument("--no-h1", dest="h1", action="store_false",
                     help="skip the H1 error check against a near-lossless solve (manufactured 3-D problems)")
     ap.add_argument("--arith", default="exact", choices=["exact", "fp32"],

@@ -219,16 +219,15 @@ __device__ __forceinline__ Packer make_packer(int W) {
 // coarse nodes P_l reads) and, over the tile's own blocks, the grid range of rc
 // and of u~ (c0 / c1).  One CTA barrier at the end.
 struct TileBounds {
-  Bounds s, t;
+  Bounds s, t, t2;     // operand section, coarse temporary, second coarse temporary
   int rc_lsb, rc_msb;  // finest grid and largest exponent of rc's nonzero blocks in the tile
-  int u_lsb, u_msb;    // the same for u~
 };
 
-template <bool HAS_S, bool HAS_U>
+template <bool HAS_S, bool HAS_T2>
 __device__ __forceinline__ TileBounds tile_bounds(const Geo &g, const Geo &gc, const Tile &T, const Sec &sec,
-                                                  const Tmp &t, const Sec &rc, const Sec &u, int *sm) {
+                                                  const Tmp &t, const Tmp &t2, const Sec &rc, int *sm) {
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  if (tid < 8) sm[tid] = (tid & 1) ? MAG_NONE : GRID_NONE;  // {G, M} x {s, t, rc, u}
+  if (tid < 8) sm[tid] = (tid & 1) ? MAG_NONE : GRID_NONE;  // {G, M} x {s, t, rc, t2}
   __syncthreads();
   int G = GRID_NONE, M = MAG_NONE;
   if (HAS_S) {
@@ -253,34 +252,37 @@ __device__ __forceinline__ TileBounds tile_bounds(const Geo &g, const Geo &gc, c
     const int cb1 = imin(gc.n - 1, T.cx0 + CX - 1) >> 5;
     G = GRID_NONE;
     M = MAG_NONE;
+    int G2 = GRID_NONE, M2 = MAG_NONE;
     for (int idx = tid; idx < 18 * CR * 2; idx += NT) {
       const int kk = ck0 + idx / (CR * 2), rem = idx % (CR * 2), jj = cj0 + rem / 2, bb = cb0 + (rem & 1);
       if (kk <= ck1 && jj <= cj1 && bb <= cb1) {
-        const int gbv = __ldg(t.gb + ((long long)kk * gc.n + jj) * gc.nbx + bb);
+        const long long b = ((long long)kk * gc.n + jj) * gc.nbx + bb;
+        const int gbv = __ldg(t.gb + b);
         if (gbv & 0xff) {
           G = imin(G, gb_grid(gbv));
           M = imax(M, gb_mag(gbv));
+        }
+        if (HAS_T2) {
+          const int gb2 = __ldg(t2.gb + b);
+          if (gb2 & 0xff) {
+            G2 = imin(G2, gb_grid(gb2));
+            M2 = imax(M2, gb_mag(gb2));
+          }
         }
       }
     }
     if (G < GRID_NONE / 2) atomicMin(sm + 2, G);
     if (M > MAG_NONE / 2) atomicMax(sm + 3, M);
+    if (HAS_T2 && G2 < GRID_NONE / 2) atomicMin(sm + 6, G2);
+    if (HAS_T2 && M2 > MAG_NONE / 2) atomicMax(sm + 7, M2);
   }
-  {  // the tile's own blocks: thread (ty, lane) takes row j0 + ty of plane k0 + lane
+  {  // the tile's own blocks of rc: thread (ty, lane) takes row j0 + ty of plane k0 + lane
     const int kk = T.k0 + threadIdx.x, jj = T.j0 + threadIdx.y;
     if (kk < T.k1 && jj < g.n) {
-      const long long b = ((long long)kk * g.n + jj) * g.nbx + T.bx;
-      const int e = __ldg(rc.exps + b);
+      const int e = __ldg(rc.exps + ((long long)kk * g.n + jj) * g.nbx + T.bx);
       if (e != -128) {
         atomicMin(sm + 4, e - rc.W + 1);
         atomicMax(sm + 5, e);
-      }
-      if (HAS_U) {
-        const int eu = __ldg(u.exps + b);
-        if (eu != -128) {
-          atomicMin(sm + 6, eu - u.W + 1);
-          atomicMax(sm + 7, eu);
-        }
       }
     }
   }
@@ -292,29 +294,34 @@ __device__ __forceinline__ TileBounds tile_bounds(const Geo &g, const Geo &gc, c
   tb.t.M = sm[3];
   tb.rc_lsb = sm[4];
   tb.rc_msb = sm[5];
-  tb.u_lsb = sm[6];
-  tb.u_msb = sm[7];
+  tb.t2.G = sm[6];
+  tb.t2.M = sm[7];
   return tb;
 }
 
 // ---------------------------------------------------------------- the sweep kernels
-// MODE 0: red from y~ = 0; 1: black with the correction of u~.  WY: width of rc
-// and y~ known at compile time (0: run time); WU the same for u~; C1: the Jacobi
+// MODE 0: red from y~ = 0; 1: black with the correction of u~ (finest level);
+// 2: the same, also writing w_l = y~' + z_l and u^_l = u~_l' + P_l u^_(l-1) (the
+// levels below the finest); 3: the black half-sweep writing u^_l but no w_l (the
+// finest level of an FMG stage before the next one).  WY: width of rc and y~
+// known at compile time (0: run time); WU the same for u~; C1: the Jacobi
 // numerator is 1 (c = 2^c_exp).
 template <int MODE, int WY, int WU, bool C1>
-__global__ void __launch_bounds__(NT, MODE == 1 ? CMG_FAST_BLACK_MINB : CMG_FAST_RED_MINB)
+__global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST_RED_MINB)
     k_fast_sweep(SweepArgs a) {
-  constexpr bool BLACK = MODE == 1;
+  constexpr bool BLACK = MODE >= 1;
+  constexpr bool WW = MODE == 2, WUH = MODE >= 2;
   constexpr int WO = BLACK ? WU : WY;  // output width when known
   __shared__ int Fs[2][PLANE];
   __shared__ int ring[4 * CRX];
+  __shared__ long long ringu[WUH ? 4 * CRX : 1];  // P_l u^_(l-1), on one grid per tile
   __shared__ int cs[2][TY * CSW];
   __shared__ int ce[2][TY];
   __shared__ int smb[8];
   const Geo g = a.g, gc = a.gc;
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
   const Tile T = make_tile(g);
-  const TileBounds tb = tile_bounds<BLACK, BLACK>(g, gc, T, a.y_in, a.wc, a.rc, a.u_in, smb);
+  const TileBounds tb = tile_bounds<BLACK, WUH>(g, gc, T, a.y_in, a.wc, a.uhc, a.rc, smb);
   const Bounds bF = operand_of(tb.s, tb.t);
   const bool anyF = bF.G < GRID_NONE / 2, anyR = tb.rc_lsb < GRID_NONE / 2;
   // One output grid Gy per tile and a proof that every update fits int32:
@@ -332,11 +339,19 @@ __global__ void __launch_bounds__(NT, MODE == 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
     if (anyF) B += ldexpf(0.75f, bF.M + 4 - GF + cl + (Gcs - Gy));
     if (anyR) B += ldexpf(1.0f, tb.rc_msb + a.c_exp + cl - Gy);
     if (GY0 < GRID_NONE / 2) B += ldexpf(1.0f, tb.s.M - Gy);
-    if ((anyF && bF.M + 4 - bF.G > 30) || B >= 2147483648.0f) {  // left to the generic kernel
+    // u^_(l-1) is staged on its finest grid in the footprint: its span must fit int64
+    const bool uh_span = WUH && tb.t2.G < GRID_NONE / 2 && tb.t2.M - tb.t2.G > 61;
+    if ((anyF && bF.M + 4 - bF.G > 30) || B >= 2147483648.0f || uh_span) {  // left to the generic kernel
       if (tid == 0) tile_push(a.tiles, a.ntiles, T);
       return;
     }
   }
+  // grids of the temporaries written here: P_l w_(l-1) is exact on GPw (the
+  // coarse w grid minus one), P_l u^_(l-1) on G1u - 1
+  const int GPw = tb.t.G < GRID_NONE / 2 ? tb.t.G - 1 : GRID_NONE, MPw = tb.t.M;
+  const int G1u = (WUH && tb.t2.G < GRID_NONE / 2) ? tb.t2.G : 0, Mu = tb.t2.M;
+  const int GPu = (WUH && tb.t2.G < GRID_NONE / 2) ? G1u - 1 : GRID_NONE;
+  bool ovf = false;
   const int KS = Gcs < GRID_NONE / 2 ? Gcs - Gy : 0;  // shift of c h S onto Gy
   const int KR = a.c_exp - (WY ? WY : a.rc.W) + 1 - Gy;  // c rc of a block with exponent e: shift e + KR
   const int KY = GF - Gy;                                // y0 onto Gy
@@ -374,7 +389,7 @@ __global__ void __launch_bounds__(NT, MODE == 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
     }
     hal = make_slot(g, Ws, hi, hj, r, x, T);
   }
-  Stager st = make_stager(gc, T, tid);
+  Stager st = make_stager(gc, T, tid), stu = st;
   const CodePos cprc = code_pos(lane, Wrc), cpu = code_pos(lane, Wui);
   // the red / black colour of node (i, j, k): i + j + k + 1 even is red
   const int par = (i + j + 1) & 1, want = a.rb == 2 ? 1 : 0;
@@ -397,7 +412,7 @@ __global__ void __launch_bounds__(NT, MODE == 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
   };
 
   // output step of plane k: stage the block's codes and exponent
-  auto out_step = [&](int k, int S, int y0) {
+  auto out_step = [&](int k, int S, int y0, int F0v) {
     if (!rowok) return;  // warp-uniform
     const bool up = pt && (a.rb == 0 || ((par ^ k) & 1) == want);
     const int crc = raw_code(rc_c, cprc.boff, Wrc);
@@ -425,6 +440,34 @@ __global__ void __launch_bounds__(NT, MODE == 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
         qu = enc64(su, G2, Wout, euo);
         ovf_flush(ovf, a.err, 112);
       }
+      if constexpr (WUH) {
+        const long long p = ((long long)k * g.n + j) * g.R + i;
+        const long long blk = (long long)k * pb + bip;
+        if (WW) {  // w_l = y~' + P_l w_(l-1), the z part being F - y0 on GF
+          const int gy = e == -128 ? GRID_NONE : e - Wy + 1;  // grid of y~'s code
+          const int gw = imin(gy, GPw);
+          long long w = 0;
+          if (gw < GRID_NONE / 2) {
+            ovf |= imax(MPw, e == -128 ? MAG_NONE : e) + 1 - gw > 62;
+            const long long yv = e == -128 ? 0 : (long long)q << ((gy - gw) & 63);
+            w = yv + regrid((long long)(pt ? F0v - y0 : 0), GF, gw);  // exact: P w is a multiple of 2^GPw
+          }
+          store_tmp_on(w, gw, a.w_out.v + p, a.w_out.gb + blk, pt, ovf);
+        }
+        {  // u^_l = u~_l' + P_l u^_(l-1)
+          const int gU = euo == -128 ? GRID_NONE : euo - Wout + 1;
+          const int gu = imin(gU, GPu);
+          long long uh = 0;
+          if (gu < GRID_NONE / 2) {
+            ovf |= imax(euo == -128 ? MAG_NONE : euo, Mu) + 1 - gu > 62;
+            int za, zb;
+            zparents<3>(k, za, zb);
+            const long long pu = (GPu < GRID_NONE / 2 && pt) ? ring_p(ringu, own, za, zb) : 0;
+            uh = (euo == -128 ? 0 : (long long)qu << ((gU - gu) & 63)) + (pu << ((GPu - gu) & 63));
+          }
+          store_tmp_on(uh, gu, a.uh_out.v + p, a.uh_out.gb + blk, pt, ovf);
+        }
+      }
       q = qu;
       e = euo;
     }
@@ -437,6 +480,10 @@ __global__ void __launch_bounds__(NT, MODE == 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
   for (int c = (T.k0 - 2) >> 1; c <= (T.k0 >> 1); c++) {
     stage_load(st, a.wc, gc, c);
     stage_store<int>(st, ring, c, GF + 1, tid);
+    if (WUH) {
+      stage_load(stu, a.uhc, gc, c);
+      stage_store<long long>(stu, ringu, c, G1u, tid);
+    }
   }
   int staged_hi = T.k0 >> 1;
   const Raw rm = raw_at(own, T.k0 - 1);
@@ -456,7 +503,10 @@ __global__ void __launch_bounds__(NT, MODE == 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
   for (int k = T.k0; k < T.k1; k++) {
     const int cn = (k + 2) >> 1;
     const bool stage = cn > staged_hi && cn <= gc.nz;
-    if (stage) stage_load(st, a.wc, gc, cn);
+    if (stage) {
+      stage_load(st, a.wc, gc, cn);
+      if (WUH) stage_load(stu, a.uhc, gc, cn);
+    }
     rc_c = rc_n;
     u_c = u_n;
     if (k + 1 < T.k1) prefetch(k + 1);
@@ -474,9 +524,10 @@ __global__ void __launch_bounds__(NT, MODE == 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
     }
     const int *P = Fs[k & 1];
     const int S = 6 * F0 - Fm - Fp - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
-    out_step(k, S, s0);
+    out_step(k, S, s0, F0);
     if (stage) {
       stage_store<int>(st, ring, cn, GF + 1, tid);
+      if (WUH) stage_store<long long>(stu, ringu, cn, G1u, tid);
       staged_hi = cn;
     }
     Fm = F0;
@@ -488,6 +539,7 @@ __global__ void __launch_bounds__(NT, MODE == 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
   __syncthreads();
   pack_plane<WO>(pk, out, g, T, T.k1 - 1, cs[(T.k1 - 1) & 1], ce[(T.k1 - 1) & 1]);
   packer_flush(pk, out.meta, a.err);
+  if (WUH) ovf_flush(ovf, a.err, 113);
 }
 
 // ---------------------------------------------------------------- the residual
@@ -760,6 +812,8 @@ bool launch_sweep_fast(const SweepArgs &a, cudaStream_t st) {
   int mode;
   if (!a.has_y && a.has_z && a.write_y && !a.corr && !a.write_w && !a.write_uh) mode = 0;
   else if (a.has_y && a.has_z && !a.write_y && a.corr && !a.write_w && !a.write_uh) mode = 1;
+  else if (a.has_y && a.has_z && !a.write_y && a.corr && a.write_w && a.write_uh && a.has_uhc) mode = 2;
+  else if (a.has_y && a.has_z && !a.write_y && a.corr && !a.write_w && a.write_uh && a.has_uhc) mode = 3;
   else return false;
   const dim3 grid = fast_grid(a.g), b(32, TY);
   const bool c1 = a.c_num == 1;
@@ -773,11 +827,18 @@ bool launch_sweep_fast(const SweepArgs &a, cudaStream_t st) {
     else if (same && c1 && wy == 5) k_fast_sweep<0, 5, 0, true><<<grid, b, 0, st>>>(a);
     else if (c1) k_fast_sweep<0, 0, 0, true><<<grid, b, 0, st>>>(a);
     else k_fast_sweep<0, 0, 0, false><<<grid, b, 0, st>>>(a);
-  } else {
+  } else if (mode == 1) {
     if (same && c1 && wy == 4 && wu == 5) k_fast_sweep<1, 4, 5, true><<<grid, b, 0, st>>>(a);
     else if (same && c1 && wy == 3 && wu == 5) k_fast_sweep<1, 3, 5, true><<<grid, b, 0, st>>>(a);
     else if (c1) k_fast_sweep<1, 0, 0, true><<<grid, b, 0, st>>>(a);
     else k_fast_sweep<1, 0, 0, false><<<grid, b, 0, st>>>(a);
+  } else if (mode == 2) {
+    if (c1) k_fast_sweep<2, 0, 0, true><<<grid, b, 0, st>>>(a);
+    else k_fast_sweep<2, 0, 0, false><<<grid, b, 0, st>>>(a);
+  } else {
+    if (same && c1 && wy == 4 && wu == 5) k_fast_sweep<3, 4, 5, true><<<grid, b, 0, st>>>(a);
+    else if (c1) k_fast_sweep<3, 0, 0, true><<<grid, b, 0, st>>>(a);
+    else k_fast_sweep<3, 0, 0, false><<<grid, b, 0, st>>>(a);
   }
   launch_sweep_list(3, a, st);
   return true;

@@ -965,14 +965,17 @@ static unsigned list_grid(const Geo &g) {
 void launch_sweep_list(int dim, const SweepArgs &a, cudaStream_t st) {
   SweepArgs b = a;
   b.list_mode = 1;
-  b.rb = a.rb;
   const dim3 t(32, TY);
   int m = SW_GENERIC;
   if (!a.has_y && a.has_z && a.write_y && !a.corr && !a.write_w && !a.write_uh) m = SW_UP0;
   else if (a.has_y && a.corr && a.has_z && !a.write_y && !a.write_w && !a.write_uh) m = SW_UP_CORR;
+  else if (a.has_y && a.corr && a.has_z && !a.write_y && a.write_w && a.write_uh) m = SW_UP_CORR_W_UH;
+  else if (a.has_y && a.corr && a.has_z && !a.write_y && !a.write_w && a.write_uh) m = SW_UP_CORR_UH;
   if (dim != 3) return;
   if (m == SW_UP0) k_sweep<3, SW_UP0><<<list_grid(a.g), t, 0, st>>>(b);
   else if (m == SW_UP_CORR) k_sweep<3, SW_UP_CORR><<<list_grid(a.g), t, 0, st>>>(b);
+  else if (m == SW_UP_CORR_W_UH) k_sweep<3, SW_UP_CORR_W_UH><<<list_grid(a.g), t, 0, st>>>(b);
+  else if (m == SW_UP_CORR_UH) k_sweep<3, SW_UP_CORR_UH><<<list_grid(a.g), t, 0, st>>>(b);
   else k_sweep<3, SW_GENERIC><<<list_grid(a.g), t, 0, st>>>(b);
 }
 
