@@ -562,24 +562,34 @@ __device__ __forceinline__ long long rne_hl(long long hi, long long lo, int fsh)
   return q + ((rem > half || (rem == half && (lo != 0 || (q & 1)))) ? 1 : 0);
 }
 
-// BFP rounding of a block whose bit length bmax (on grid G) is known
-__device__ __forceinline__ int enc64b(long long v, int G, int W, int bmax, int &e, int &s, int *err) {
+// Round-to-nearest-even of v / 2^(s + dn) where v = ts 2^dn + lost, 0 <= lost < 2^dn
+// and stk says lost != 0 (a 64-bit value normalised to 32 bits once per block);
+// for s <= 0 (then dn = 0) the exact ts 2^-s.
+__device__ __forceinline__ int rne_norm(int ts, bool stk, int s) {
+  const int s1 = s > 1 ? s : 1;
+  const int t = ts >> (s1 - 1);
+  const int low = ((ts & ((1 << (s1 - 1)) - 1)) != 0) | (int)stk;
+  const int r = (t >> 1) + (t & 1 & (low | (t >> 1)));
+  return s <= 0 ? (ts << ((-s) & 31)) : r;
+}
+
+// BFP rounding at width W of a block normalised as above (bmax: bit length of the
+// block's largest |v| on grid G; dn = max(0, bmax - 31)); s gets the total drop
+// shift (the rounded value is q 2^(s + G) when s > 0, else v itself)
+__device__ __forceinline__ int enc_norm(int ts, bool stk, int bmax, int dn, int G, int W, int &e, int &s) {
   if (bmax == 0) {
     e = -128;
     s = 0;
     return 0;
   }
-  e = bmax + G;
-  s = bmax - (W - 1);
-  long long q = rne_shift_w(v, s);
+  int sl = bmax - dn - (W - 1);  // shift below the normalised value
+  int q = rne_norm(ts, stk, sl);
   const unsigned lim = 1u << (W - 1), mask = (lim << 1) - 1u;
-  if (__any_sync(FULL, (((unsigned)q + lim) & mask) == 0u)) {
-    e += 1;
-    s += 1;
-    q = rne_shift_w(v, s);
-  }
-  if ((e > 127 || e < -127) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_EXP);
-  return (int)q;
+  const bool carry = __any_sync(FULL, (((unsigned)q + lim) & mask) == 0u);
+  if (carry) q = rne_norm(ts, stk, ++sl);
+  e = bmax + G + (carry ? 1 : 0);
+  s = sl + dn;
+  return q;
 }
 
 // Algorithm 2 without pre-smoothing on level L: t = f - A (u~_L + P u^_(L-1)),
@@ -641,7 +651,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
   // the static bounds on t (|f| + |A F|) are loose by the smoothness of u; where they
   // do not prove the range, every shifted value is checked (as the generic kernel does)
   const bool fast = Mt - Gt <= 62, dfast = Mt - Gd <= 57;
-  bool ovf = false;
+  bool ovf = false, bad_exp = false;
   const int Wr = WR ? WR : a.r_out.W, Wt = a.Wt, Ws = a.u.W;
   const unsigned cmask = Wr == 32 ? FULL : (1u << Wr) - 1u;
   Packer pk = make_packer(Wr);
@@ -680,7 +690,15 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
   const int xa_off = (T.x0 + lane + 1 - ((lane + 1) & 1 ? 1 : 0)) >> 1;  // (I - sx) / 2
   const int xb_off = (T.x0 + lane + 1 + ((lane + 1) & 1 ? 1 : 0)) >> 1;  // (I + sx) / 2
   const bool Iodd = ((lane + 1) & 1) != 0;
-  unsigned long long *acc = (unsigned long long *)a.racc.v;
+  // the restriction targets of this thread: coarse rows A = (J - sy)/2 and B = (J + sy)/2,
+  // columns xa_off / xb_off (1-based); per plane only the coarse plane changes
+  const int ya = (J - sy) >> 1, yb = (J + sy) >> 1;
+  const bool okA = xa_off >= 1 && xa_off <= gc.n && ya >= 1 && ya <= gc.n;
+  const bool okB = xb_off >= 1 && xb_off <= gc.n && yb >= 1 && yb <= gc.n;
+  const bool issueB = !(lane & 1);
+  const long long cplane = (long long)gc.n * gc.R;
+  unsigned long long *accA = (unsigned long long *)a.racc.v + (okA ? (long long)(ya - 1) * gc.R + (xa_off - 1) : 0);
+  unsigned long long *accB = (unsigned long long *)a.racc.v + (okB ? (long long)(yb - 1) * gc.R + (xb_off - 1) : 0);
 
   auto out_step = [&](int k, long long S) {
     if (!rowok) return;  // warp-uniform
@@ -718,22 +736,25 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
         ck62(t, ovf);
       }
     }
+    // one normalisation of the block to 32 bits (and a sticky bit) for both roundings
     const int bmax = block_bitlen(t);
+    const int dn = bmax > 31 ? bmax - 31 : 0;
+    const int ts = (int)(t >> dn);
+    const bool stk = (t & ((1ll << dn) - 1)) != 0;
     int e, sh;
-    const int qr = enc64b(t, Gt, Wr, bmax, e, sh, a.err);
+    const int qr = enc_norm(ts, stk, bmax, dn, Gt, Wr, e, sh);
     if constexpr (WR == 4) pack_w4(qr, a.r_out.words + ((long long)k * pb + bip) * 4, lane);
     else cs[k & 1][ty * CSW + lane] = (int)((unsigned)qr & cmask);
     if (lane == 0) ce[k & 1][ty] = e;
     int et, stt;
-    const int qt = enc64b(t, Gt, Wt, bmax, et, stt, a.err);
-    const long long th = stt > 0 ? shl_fast((long long)qt, stt) : t;  // t^_L on Gt
-    long long d;  // on Gd; R t^ on Gd - 1
-    if (dfast) {
-      d = shl_fast(th, Gt - Gd);
-    } else {
-      d = shl_ck(th, Gt - Gd, ovf);
+    const int qt = enc_norm(ts, stk, bmax, dn, Gt, Wt, et, stt);
+    // t^_L on Gd (R t^ is held on Gd - 1): q 2^(stt + Gt - Gd), or t itself when nothing dropped
+    long long d = stt > 0 ? shl_fast((long long)qt, stt + Gt - Gd) : shl_fast(t, Gt - Gd);
+    if (!dfast) {  // |d| < 2^58 (a block with et - Gd > 58 has such a value, as in the generic check)
       ck58(d, ovf);
+      ovf |= et != -128 && et - Gd > 58;
     }
+    bad_exp |= et != -128 && (et > 127 || et < -127);  // t^ is not stored: its exponent checked here
     // parents of fine node (I, J, K): (I -+ s) / 2 componentwise, s the odd coordinates;
     // an all-even node has one parent (weight 1, 2d on the grid Gd - 1), others two (d each)
     const int K = k + 1, sz = K & 1;
@@ -744,11 +765,11 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     const bool issueA = (lane & 1) || lane == 0;
     const long long vA = dA + (((lane & 1) && lane < 31) ? pA : 0);
     const long long vB = dB + pB;  // row B: lanes (even, even + 1); issued by the even lane
-    const int ya = (J - sy) >> 1, za = (K - sz) >> 1, yb = (J + sy) >> 1, zb = (K + sz) >> 1;
-    if (issueA && vA && xa_off >= 1 && xa_off <= gc.n && ya >= 1 && ya <= gc.n && za >= 1 && za <= gc.nz)
-      atomicAdd(acc + ((long long)(za - 1) * gc.n + (ya - 1)) * gc.R + (xa_off - 1), (unsigned long long)vA);
-    if (!(lane & 1) && vB && xb_off >= 1 && xb_off <= gc.n && yb >= 1 && yb <= gc.n && zb >= 1 && zb <= gc.nz)
-      atomicAdd(acc + ((long long)(zb - 1) * gc.n + (yb - 1)) * gc.R + (xb_off - 1), (unsigned long long)vB);
+    const int za = (K - sz) >> 1, zb = (K + sz) >> 1;
+    if (issueA && okA && vA && za >= 1 && za <= gc.nz)
+      atomicAdd(accA + (long long)(za - 1) * cplane, (unsigned long long)vA);
+    if (issueB && okB && vB && zb >= 1 && zb <= gc.nz)
+      atomicAdd(accB + (long long)(zb - 1) * cplane, (unsigned long long)vB);
   };
 
   for (int c = (T.k0 - 2) >> 1; c <= (T.k0 >> 1); c++) {
@@ -799,6 +820,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
   pack_plane<WR>(pk, a.r_out, g, T, T.k1 - 1, cs[(T.k1 - 1) & 1], ce[(T.k1 - 1) & 1]);
   packer_flush(pk, a.r_out.meta, a.err);
   ovf_flush(ovf, a.err, 202);
+  if (__any_sync(FULL, bad_exp) && lane == 0) atomicOr(a.err, ERR_EXP);
 }
 
 dim3 fast_grid(const Geo &g) {
