@@ -50,6 +50,9 @@ WORKLOADS = {
                       "2-D Poisson 257^2 grid, u=sin(pi x)sin(pi y)(1+x^2 y)"),
 }
 DEFAULT_WORKLOAD = "poisson3d_2049"
+# cycle arithmetic: exact (int64), binary32 or binary64 V-cycle inside the exact refinement
+ARITH_NAMES = ["exact", "fp32", "fp64"]
+DTYPE_NAMES = ["int64", "f32 cycle + int64 refinement", "f64 cycle + int64 refinement"]
 
 
 def source_sha() -> str:
@@ -244,7 +247,7 @@ def run_reference(args, wl):
     import oracle
     oracle.build()
     from paper_2511_19036_gb300.cmg_config import config_for
-    cfg = config_for(prob_name, Lmax, arith=1 if args.arith == "fp32" else 0,
+    cfg = config_for(prob_name, Lmax, arith=ARITH_NAMES.index(args.arith),
                      smoother=smoother_of(args, prob_name))
     dim = cfg.dim
     Ls = pick_sample_level(prob_name, Lmax, dim)
@@ -292,7 +295,7 @@ def run_gpu(args, wl):
         dist.init_process_group("nccl")
     prob_name, Lmax, desc = WORKLOADS[wl]
     prob = cmg_problems.make_problem(prob_name, Lmax, seed=rank)
-    cfg = cmg.config_for(prob_name, Lmax, arith=1 if args.arith == "fp32" else 0,
+    cfg = cmg.config_for(prob_name, Lmax, arith=ARITH_NAMES.index(args.arith),
                          smoother=smoother_of(args, prob_name))
     diffusion = bool(getattr(prob, "coef", 0))
     stream = torch.cuda.Stream()
@@ -433,23 +436,44 @@ def run_gpu(args, wl):
             norms.append(float(np.max(np.abs(ue))))
         nodal_rel = max(errs) / max(norms)
     # diffusion (no closed form): the solution against a reference solve of the
-    # same discrete problem with wider widths and more IR iterations, on sampled planes
-    diffusion_vs_reference = None
+    # same discrete problem with the binary64 cycle, wider widths and more IR
+    # iterations (the FP64 reference on the GPU), on sampled planes
+    def sampled_diff(sa, sb):
+        dmax, umax = 0.0, 0.0
+        for z in planes:
+            a = sa.decode_solution(z, 1).cpu().numpy()[0]
+            b = sb.decode_solution(z, 1).cpu().numpy()[0]
+            dmax = max(dmax, float(np.max(np.abs(a - b))))
+            umax = max(umax, float(np.max(np.abs(b))))
+        return dmax / umax
+
+    diffusion_vs_reference, fp32_vs_fp64 = None, None
     if diffusion:
         import dataclasses
-        rcfg = dataclasses.replace(cfg, b1=14, b2=10, N_ir=16)
+        rcfg = dataclasses.replace(cfg, b1=14, b2=10, N_ir=16, arith=2)
         ref = cmg.Solver(rcfg, stream=stream)
         ref.set_rhs(prob.tables, prob.scale_exp)
         ref.set_coefficient(kfield)
         ref.fmg_solve()
-        dmax, umax = 0.0, 0.0
-        for z in planes:
-            a = solver.decode_solution(z, 1).cpu().numpy()[0]
-            b = ref.decode_solution(z, 1).cpu().numpy()[0]
-            dmax = max(dmax, float(np.max(np.abs(a - b))))
-            umax = max(umax, float(np.max(np.abs(b))))
-        diffusion_vs_reference = {"max_rel_diff_sampled": dmax / umax,
-                                  "reference": "b1=14, b2=10, N_ir=16, same binary32 cycle"}
+        diffusion_vs_reference = {"max_rel_diff_sampled": sampled_diff(solver, ref),
+                                  "reference": "b1=14, b2=10, N_ir=16, binary64 cycle"}
+        # the other floating-point cycle at the same widths, solved once after the
+        # timed region (device time by CUDA events on the solver's stream)
+        if not args.no_compare:
+            ocfg = dataclasses.replace(cfg, arith=1 if cfg.arith == 2 else 2)
+            other = cmg.Solver(ocfg, stream=stream, timing=True)
+            other.set_rhs(prob.tables, prob.scale_exp)
+            other.set_coefficient(kfield)
+            other_ms = other.fmg_solve()["solve_ms"]
+            mine = {"cycle_ms": ms_step, "rel_err_vs_reference": diffusion_vs_reference["max_rel_diff_sampled"]}
+            theirs = {"cycle_ms": other_ms, "rel_err_vs_reference": sampled_diff(other, ref)}
+            f32, f64 = (mine, theirs) if cfg.arith == 1 else (theirs, mine)
+            fp32_vs_fp64 = {"fp32_cycle_ms": f32["cycle_ms"], "fp64_cycle_ms": f64["cycle_ms"],
+                            "max_rel_diff_sampled": sampled_diff(other, solver),
+                            "rel_err_fp32_cycle_vs_reference": f32["rel_err_vs_reference"],
+                            "rel_err_fp64_cycle_vs_reference": f64["rel_err_vs_reference"],
+                            "note": "the same widths and IR; one solve of the other form after the timed region"}
+            del other
         del ref
     # Sec. 7.1 at this size: the H1 error of the solution against that of a
     # near-lossless solve of the same discrete problem (Jacobi V(2,2), b1 = b2 = 12,
@@ -470,32 +494,42 @@ def run_gpu(args, wl):
                                 "criterion": "Sec. 7.1: ratio <= 2", "met": e_cmg <= 2 * e_ref,
                                 "reference": "Jacobi V(2,2), b1=%d, b2=12, N_ir=8" % rcfg.b1}
     # the precision split (binary32 cycle inside the exact refinement) against the
-    # exact cycle, on the same GPU and problem, after the timed region: the other
-    # form is solved once (its device time by CUDA events on the solver's stream),
-    # and both solutions are compared on the sampled planes
-    fp32_vs_exact = None
+    # exact cycle and the plain binary64 cycle, on the same GPU and problem, after
+    # the timed region: each other form is solved once (its device time by CUDA
+    # events on the solver's stream) and compared on the sampled planes
+    fp32_vs_exact, precision_forms = None, None
     if not diffusion and not args.no_compare:
-        other = cmg.config_for(prob_name, Lmax, arith=0 if cfg.arith else 1, smoother=cfg.smoother)
-        ref = cmg.Solver(other, stream=stream)
-        ref.set_rhs(prob.tables, prob.scale_exp)
-        ref_ms = ref.fmg_solve()["solve_ms"]
-        dmax, umax, err_other = 0.0, 0.0, []
-        for z in planes:
-            a = solver.decode_solution(z, 1).cpu().numpy()[0]
-            b = ref.decode_solution(z, 1).cpu().numpy()[0]
-            Y, X = np.meshgrid(x, x, indexing="ij")
-            ue = prob.exact_u(X, Y, (z + 1) * h) if cfg.dim == 3 else prob.exact_u(X, Y)
-            dmax = max(dmax, float(np.max(np.abs(a - b))))
-            umax = max(umax, float(np.max(np.abs(a if cfg.arith else b))))
-            err_other.append(float(np.max(np.abs(b - ue))))
-        exact_ms, f32_ms = (ms_step, ref_ms) if cfg.arith == 0 else (ref_ms, ms_step)
-        e32, e64 = (max(err_other) / max(norms), nodal_rel) if cfg.arith == 0 else \
-            (nodal_rel, max(err_other) / max(norms))
-        fp32_vs_exact = {"max_rel_diff_sampled": dmax / umax, "exact_cycle_ms": exact_ms,
-                         "fp32_cycle_ms": f32_ms, "nodal_rel_err_exact_cycle": e64,
-                         "nodal_rel_err_fp32_cycle": e32,
-                         "note": "one solve of the other form after the timed region"}
-        del ref
+        precision_forms = {ARITH_NAMES[cfg.arith]: {"cycle_ms": ms_step, "nodal_rel_err_sampled": nodal_rel,
+                                                    "max_rel_diff_vs_timed_sampled": 0.0}}
+        for ar in (0, 1, 2):
+            if ar == cfg.arith:
+                continue
+            other = cmg.config_for(prob_name, Lmax, arith=ar, smoother=cfg.smoother)
+            if cmg.params_check(other) != cmg.OK:
+                continue
+            ref = cmg.Solver(other, stream=stream)
+            ref.set_rhs(prob.tables, prob.scale_exp)
+            ref_ms = ref.fmg_solve()["solve_ms"]
+            dmax, umax, err_other = 0.0, 0.0, []
+            for z in planes:
+                a = solver.decode_solution(z, 1).cpu().numpy()[0]
+                b = ref.decode_solution(z, 1).cpu().numpy()[0]
+                Y, X = np.meshgrid(x, x, indexing="ij")
+                ue = prob.exact_u(X, Y, (z + 1) * h) if cfg.dim == 3 else prob.exact_u(X, Y)
+                dmax = max(dmax, float(np.max(np.abs(a - b))))
+                umax = max(umax, float(np.max(np.abs(a))))
+                err_other.append(float(np.max(np.abs(b - ue))))
+            precision_forms[ARITH_NAMES[ar]] = {"cycle_ms": ref_ms, "nodal_rel_err_sampled": max(err_other) / max(norms),
+                                                "max_rel_diff_vs_timed_sampled": dmax / umax}
+            del ref
+        if "exact" in precision_forms and "fp32" in precision_forms:
+            ex, f3 = precision_forms["exact"], precision_forms["fp32"]
+            fp32_vs_exact = {"max_rel_diff_sampled": max(ex["max_rel_diff_vs_timed_sampled"],
+                                                         f3["max_rel_diff_vs_timed_sampled"]),
+                             "exact_cycle_ms": ex["cycle_ms"], "fp32_cycle_ms": f3["cycle_ms"],
+                             "nodal_rel_err_exact_cycle": ex["nodal_rel_err_sampled"],
+                             "nodal_rel_err_fp32_cycle": f3["nodal_rel_err_sampled"],
+                             "note": "one solve of the other form after the timed region"}
 
     if rank != 0:
         return 0
@@ -520,11 +554,11 @@ def run_gpu(args, wl):
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int64" if cfg.arith == 0 else "f32 cycle + int64 refinement",
+        "vs_baseline": None, "dtype": DTYPE_NAMES[cfg.arith],
         "data": "synthetic",
         "config": {"workload": wl, "description": desc, "dim": cfg.dim, "L_max": Lmax, "dofs": dofs,
                    "b1": cfg.b1, "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": cycle_name(cfg),
-                   "omega": cfg.omega, "arith": "exact" if cfg.arith == 0 else "fp32 cycle",
+                   "omega": cfg.omega, "arith": ARITH_NAMES[cfg.arith] + (" cycle" if cfg.arith else ""),
                    "l2": "working set larger than L2" if dofs > 1e8 else
                    "working set fits L2 (state per step re-read from L2)",
                    "parallelism": "replicas x%d" % world},
@@ -539,7 +573,9 @@ def run_gpu(args, wl):
         "nodal_rel_err_sampled": nodal_rel,
         "discretization_check": discretization_check,
         "fp32_vs_exact": fp32_vs_exact,
+        "precision_forms": precision_forms,
         "diffusion_vs_reference": diffusion_vs_reference,
+        "fp32_vs_fp64": fp32_vs_fp64,
         "roofline": roofline,
         "issue_roofline": issue,
         "fast_kernels": solver.fast_stats(),
@@ -593,10 +629,10 @@ def run_adjoint(args, wl):
     with torch.no_grad():
         u_obs = diffusion_solve(k_obs, g, cfg).reshape(-1)
 
-    def step():
+    def step(c=cfg):
         kt = k.clone().requires_grad_(True)
         gt = g.clone().requires_grad_(True)
-        u = diffusion_solve(kt, gt, cfg).reshape(-1)
+        u = diffusion_solve(kt, gt, c).reshape(-1)
         J = 0.5 * torch.sum((u - u_obs) ** 2)
         dk, dg = torch.autograd.grad(J, (kt, gt))
         return J, dk * kt.detach(), dg  # dJ/dm = k dJ/dk for k = exp(m)
@@ -632,6 +668,25 @@ def run_adjoint(args, wl):
         barrier()
         e2e.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(statistics.median(e2e), dist, "cuda")
+    # the same gradient with the plain binary64 cycle (same widths and IR), timed
+    # once after the timed region, and the difference of the two gradients
+    fp32_vs_fp64 = None
+    if not args.no_compare:
+        import dataclasses
+        c64 = dataclasses.replace(cfg, arith=2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record()
+        J64, dm64, dg64 = step(c64)
+        e1.record()
+        barrier()
+
+        def rel(a, b):
+            return float(torch.max(torch.abs(a - b)) / torch.max(torch.abs(b)))
+        fp32_vs_fp64 = {"fp32_step_ms": ms_step, "fp64_step_ms": e0.elapsed_time(e1),
+                        "rel_diff_J": abs(float(J) - float(J64)) / abs(float(J64)),
+                        "max_rel_diff_dJ_dm": rel(dm, dm64), "max_rel_diff_dJ_df": rel(dg, dg64),
+                        "note": "forward + adjoint + gradient with the binary64 cycle, once after the timed region"}
     # the dominant kernel, from one timed forward solve of the same problem
     solver = cmg.Solver(cfg, timing=True)
     solver.set_coefficient(k)
@@ -678,6 +733,7 @@ def run_adjoint(args, wl):
                    "b2": cfg.b2, "N_ir": cfg.N_ir, "cycle": cycle_name(cfg),
                    "l2": "working set larger than L2", "parallelism": "replicas x%d" % world},
         "J": float(J.detach()),
+        "fp32_vs_fp64": fp32_vs_fp64,
         "roofline": {"kernel": "k_sweep_f32<3> finest level (forward solve)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": None,
                      "coefficient_bytes_per_launch": coef_bytes, "peak_kind": peak_kind},
@@ -707,8 +763,8 @@ def main():
                     help="skip the solve of the other arithmetic (binary32 cycle / exact cycle)")
     ap.add_argument("--no-h1", dest="h1", action="store_false",
                     help="skip the H1 error check against a near-lossless solve (manufactured 3-D problems)")
-    ap.add_argument("--arith", default="exact", choices=["exact", "fp32"],
-                    help="exact V-cycle, or the binary32 V-cycle inside exact iterative refinement")
+    ap.add_argument("--arith", default="exact", choices=["exact", "fp32", "fp64"],
+                    help="exact V-cycle, or the binary32 / binary64 V-cycle inside exact iterative refinement")
     ap.add_argument("--smoother", default="rbgs", choices=["rbgs", "jacobi"],
                     help="V(0,1) red-black Gauss-Seidel (Algorithm 1's cycle), or V(2,2) weighted Jacobi; "
                          "diffusion and adjoint workloads always use Jacobi V(2,2)")

@@ -55,7 +55,7 @@ typedef enum {
 /* Parameters of Algorithm 3 with the precisions of Table 1 (P1: p = 1, m = 1).
  * Intermediate arithmetic is exact (fixed-point integers on the GPU); values are
  * rounded only where they are stored, as the paper's rounding rules prescribe. */
-enum { CMG_ARITH_EXACT = 0, CMG_ARITH_FP32 = 1 };
+enum { CMG_ARITH_EXACT = 0, CMG_ARITH_FP32 = 1, CMG_ARITH_FP64 = 2 };
 enum { CMG_COEF_POISSON = 0, CMG_COEF_DIFFUSION = 1 };
 enum { CMG_SMOOTHER_JACOBI = 0, CMG_SMOOTHER_RBGS = 1 };
 
@@ -76,12 +76,15 @@ typedef struct {
                           prolongated corrections) in binary32, round to nearest,
                           in a fixed order, inside the exact iterative refinement
                           (outer residual, level-1 solve and u~ correction exact);
-                          needs k_r (L_max - 1) + b2 + bitlen(Jacobi numerator) <= 24 */
+                          needs k_r (L_max - 1) + b2 + bitlen(Jacobi numerator) <= 24;
+                          CMG_ARITH_FP64 (2): the same cycle in binary64, the plain
+                          FP64 form of the precision split of Table 1 */
   int coef;            /* CMG_COEF_POISSON (0): -Lap u = f; CMG_COEF_DIFFUSION (1):
                           -div(k grad u) = f with the nodal coefficient set by
-                          cmg_set_coefficient; needs arith = CMG_ARITH_FP32 and
-                          nu1 >= 1 (the outer residual and level-1 solve in FP64,
-                          the cycle in binary32, each in a fixed order) */
+                          cmg_set_coefficient; needs arith = CMG_ARITH_FP32 or
+                          CMG_ARITH_FP64 and nu1 >= 1 (the outer residual and
+                          level-1 solve in FP64, the cycle in binary32 or binary64,
+                          each in a fixed order) */
   int smoother;        /* CMG_SMOOTHER_JACOBI (0): weighted Jacobi sweeps;
                           CMG_SMOOTHER_RBGS (1): red-black Gauss-Seidel post-
                           smoothing (Algorithm 1 as the V(0,1) cycle of Sec. 7):

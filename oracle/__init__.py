@@ -24,6 +24,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cmg_oracle.c")
 _HDR = os.path.join(_HERE, "cmg_oracle.h")
+_INC = os.path.join(_HERE, "cycle_real.inc")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -35,7 +36,7 @@ OK, EINVAL, ENOMEM, ERANGE, ECORRUPT = 0, 1, 2, 3, 5
 def build(force: bool = False) -> str:
     """Compile liboracle.so next to its source (gcc, OpenMP when available)."""
     stale = (not os.path.exists(_LIB) or
-             os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+             os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in (_SRC, _HDR, _INC)))
     if not (force or stale):
         return _LIB
     base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",

@@ -180,11 +180,12 @@ void cmgo_restrict(int dim, int level, const double *fine, double *coarse) {
 }
 
 /* ------------------------------------------------------------------------- */
-/* FP32 V-cycle (the precision split of Table 1: the cycle works in            */
+/* floating-point V-cycles (the precision split of Table 1: the cycle works in  */
 /* progressive(+m, b4) precision, the residual of fmgResidual in                */
-/* progressive(+p+m+1, b3); here the cycle runs in IEEE binary32, round to     */
-/* nearest, no fused multiply-add, in the fixed order below, while the outer    */
-/* residual, the level-1 solve and the correction of u~ stay exact)             */
+/* progressive(+p+m+1, b3)).  arith = 1 runs the cycle in IEEE binary32,        */
+/* arith = 2 in IEEE binary64 (the plain FP64 form), both round to nearest with */
+/* no fused multiply-add, in the one fixed order of cycle_real.inc, while the   */
+/* outer residual, the level-1 solve and the correction of u~ stay exact.       */
 /* ------------------------------------------------------------------------- */
 
 /* x as binary32; flags *bad when x is not exactly a normal-range float or 0 */
@@ -194,40 +195,10 @@ static inline float to_f32(double x, int *bad) {
   return f;
 }
 
-static inline float get0f(const float *x, const lev *g, int i, int j, int k) {
-  if (i < 0 || i >= g->n || j < 0 || j >= g->n || k < 0 || k >= g->nz) return 0.0f;
-  return x[idx(g, i, j, k)];
-}
-
-/* (A_l x) in binary32: (2d) x_p, then minus the neighbours -x,+x,-y,+y,-z,+z,
- * each operation rounded, then times h^(d-2) (a power of two) */
-static float A_at_f32(const float *x, const lev *g, int i, int j, int k) {
-  volatile float acc = (float)(2 * g->dim) * x[idx(g, i, j, k)];
-  acc = acc - get0f(x, g, i - 1, j, k);
-  acc = acc - get0f(x, g, i + 1, j, k);
-  acc = acc - get0f(x, g, i, j - 1, k);
-  acc = acc - get0f(x, g, i, j + 1, k);
-  if (g->dim == 3) {
-    acc = acc - get0f(x, g, i, j, k - 1);
-    acc = acc - get0f(x, g, i, j, k + 1);
-  }
-  return acc * ldexpf(1.0f, -(g->dim - 2) * g->l);
-}
-
-/* (P_l xc) in binary32: a copy, or (a + b) rounded, then halved */
-/* value at 1-based node (I, J, K); zero on the boundary.  K ignored in 2-D. */
-static inline float nodef(const float *x, const lev *g, int I, int J, int K) {
-  if (g->dim == 2) K = 1;
-  return get0f(x, g, I - 1, J - 1, K - 1);
-}
-
-static float P_at_f32(const float *xc, const lev *gc, int I, int J, int K) {
-  int sx = I & 1, sy = J & 1, sz = gc->dim == 3 ? (K & 1) : 0;
-  if (!sx && !sy && !sz) return nodef(xc, gc, I / 2, J / 2, K / 2);
-  volatile float a = nodef(xc, gc, (I - sx) / 2, (J - sy) / 2, (K - sz) / 2);
-  volatile float b = nodef(xc, gc, (I + sx) / 2, (J + sy) / 2, (K + sz) / 2);
-  volatile float s = a + b;
-  return s * 0.5f;
+/* x as binary64: every stored value is one already */
+static inline double to_f64(double x, int *bad) {
+  (void)bad;
+  return x;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -403,8 +374,8 @@ static int Wt(const cmgo_ctx *c) { return c->P.b1 == 0 ? 0 : c->P.ku * c->L + c-
 /* flux between neighbours p, q uses the face value (k_p + k_q) / 2, so         */
 /*   (A_l u)_p = h^(d-2) sum over the 2d neighbours q of (k_p+k_q)/2 (u_p - u_q) */
 /* with u = 0 on the boundary (k = 1 gives the Poisson stencil).  The outer     */
-/* residual evaluates it in FP64 and the cycle in binary32, each in the fixed   */
-/* order below (face sums are exact in FP64; products and sums round).          */
+/* residual evaluates it in FP64 and the cycle in binary32 or binary64, each   */
+/* in a fixed order (face sums are exact in FP64; products and sums round).     */
 /* ------------------------------------------------------------------------- */
 
 static const int NBR[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
@@ -444,41 +415,6 @@ static double diag1_diff64(const cmgo_ctx *c) {
   return acc * ldexp(1.0, -(c->P.dim - 2));
 }
 
-/* binary32 (A_l F)_p and diagonal D_p: kf = fl(fl(k_q + k_p) * 0.5),
- * acc = fl(acc + fl(kf * fl(F_p - F_q))), dsum = fl(dsum + kf) in the neighbour
- * order; S = fl(acc h^(d-2)), D = fl(dsum h^(d-2)) */
-static void A_at_diff32(const cmgo_ctx *c, const float *F, const lev *g, int i, int j, int k, float *S,
-                        float *D) {
-  const int I = i + 1, J = j + 1, K = k + 1, nn = 2 * g->dim;
-  const float kp = kcoef(c, g->l, I, J, K), Fp = F[idx(g, i, j, k)];
-  volatile float acc = 0.0f, dsum = 0.0f;
-  for (int e = 0; e < nn; e++) {
-    const int Iq = I + NBR[e][0], Jq = J + NBR[e][1], Kq = K + NBR[e][2];
-    volatile float ks = kcoef(c, g->l, Iq, Jq, Kq) + kp;
-    volatile float kf = ks * 0.5f;
-    volatile float du = Fp - get0f(F, g, Iq - 1, Jq - 1, Kq - 1);
-    volatile float pr = kf * du;
-    acc = acc + pr;
-    dsum = dsum + kf;
-  }
-  const float hs = ldexpf(1.0f, -(g->dim - 2) * g->l);
-  *S = acc * hs;
-  *D = dsum * hs;
-}
-
-/* binary32 restriction (R_l d) at coarse node (Ic, Jc, Kc) in the order of R_at */
-static float R_at_f32(const float *df, const lev *gf, int Ic, int Jc, int Kc) {
-  int I = 2 * Ic, J = 2 * Jc, K = 2 * Kc;
-  int ns = gf->dim == 3 ? 7 : 3;
-  volatile float sum = 0.0f;
-  for (int s = 0; s < ns; s++) {
-    int ex = ODDSET[s][0], ey = ODDSET[s][1], ez = ODDSET[s][2];
-    sum = sum + nodef(df, gf, I - ex, J - ey, K - ez);
-    sum = sum + nodef(df, gf, I + ex, J + ey, K + ez);
-  }
-  volatile float half = sum * 0.5f;
-  return nodef(df, gf, I, J, K) + half;
-}
 
 int cmgo_width(const cmgo_ctx *c, int which, int level) {
   return which == CMGO_U ? Wu(c, level) : Wr(c, level);
@@ -497,7 +433,8 @@ cmgo_ctx *cmgo_create(const cmgo_params *p, int nterms, const int32_t *tables, i
   if (!p || p->dim < 2 || p->dim > 3 || p->Lmax < 1 || p->Lmax > MAXL || p->N < 1 ||
       p->nu1 < 0 || p->nu2 < 1 || p->b1 < 0 || p->b2 < 0 || nterms < 1 || !tables)
     return NULL;
-  if (p->coef != 0 && (p->coef != 1 || p->arith != 1 || p->nu1 < 1)) return NULL;
+  if (p->arith < 0 || p->arith > 2) return NULL;
+  if (p->coef != 0 && (p->coef != 1 || p->arith == 0 || p->nu1 < 1)) return NULL;
   if (p->smoother != 0 && (p->smoother != 1 || p->nu1 != 0)) return NULL;
   cmgo_ctx *c = (cmgo_ctx *)calloc(1, sizeof(cmgo_ctx));
   if (!c) return NULL;
@@ -878,58 +815,27 @@ static int jacobi(cmgo_ctx *c, int l, const double *z, long long *cnt, int colou
   return st;
 }
 
-/* The same sweep with binary32 arithmetic (FP32 V-cycle): F = fl(y + z) (or y),
- * S = A F as in A_at_f32, res = fl(rc - S), y' = fl(y + fl(c res)); y' is then
- * rounded into the BFP section like the exact sweep.  Every stored value the
- * cycle reads must be an exact normal-range binary32 number (else ERANGE). */
-static int jacobi_f32(cmgo_ctx *c, int l, const float *z, long long *cnt, int colour) {
-  lev g = mklev(c->P.dim, l);
-  int bad = 0;
-  const float cl = to_f32(cjac(c, l, cnt), &bad);
-  float *F = (float *)malloc((size_t)g.np * sizeof(float));
-  float *yf = (float *)malloc((size_t)g.np * sizeof(float));
-  double *yn = (double *)malloc((size_t)g.np * sizeof(double));
-  if (!F || !yf || !yn) {
-    free(F);
-    free(yf);
-    free(yn);
-    return CMGO_ENOMEM;
-  }
-  for (int64_t p = 0; p < g.np; p++) {
-    yf[p] = to_f32(c->y[l].v[p], &bad);
-    volatile float f = yf[p];
-    if (z) f = f + z[p];
-    F[p] = f;
-  }
-  const float omega_f = (float)c->P.omega;
-#pragma omp parallel for collapse(2) reduction(| : bad) schedule(static)
-  for (int k = 0; k < g.nz; k++)
-    for (int j = 0; j < g.n; j++)
-      for (int i = 0; i < g.n; i++) {
-        int64_t p = idx(&g, i, j, k);
-        if (colour >= 0 && node_colour(g.dim, i, j, k) != colour) {  /* other colour: kept */
-          yn[p] = c->y[l].v[p];
-          continue;
-        }
-        volatile float S, cp = cl;
-        if (c->P.coef) {  /* diffusion: the Jacobi factor omega / D_p per node */
-          float Sd, Dd;
-          A_at_diff32(c, F, &g, i, j, k, &Sd, &Dd);
-          S = Sd;
-          cp = omega_f / Dd;
-        } else {
-          S = A_at_f32(F, &g, i, j, k);
-        }
-        volatile float res = to_f32(c->rc[l].v[p], &bad) - S;
-        volatile float cres = cp * res;
-        volatile float y2 = yf[p] + cres;
-        yn[p] = (double)y2;
-      }
-  int st = round_dense(&g, yn, Wr(c, l), &c->y[l]);
-  free(F);
-  free(yf);
-  free(yn);
-  return bad ? CMGO_ERANGE : st;
+/* the binary32 and binary64 cycles: sweep, down-leg right-hand side, up-leg */
+#define REAL float
+#define CYC(name) name##_f32
+#define TO_REAL to_f32
+#include "cycle_real.inc"
+#undef REAL
+#undef CYC
+#undef TO_REAL
+#define REAL double
+#define CYC(name) name##_f64
+#define TO_REAL to_f64
+#include "cycle_real.inc"
+#undef REAL
+#undef CYC
+#undef TO_REAL
+
+/* the sweep of the configured cycle arithmetic */
+static int sweep_any(cmgo_ctx *c, int l, long long *cnt, int colour) {
+  if (c->P.arith == 1) return jacobi_f32(c, l, NULL, cnt, colour);
+  if (c->P.arith == 2) return jacobi_f64(c, l, NULL, cnt, colour);
+  return jacobi(c, l, NULL, cnt, colour);
 }
 
 /* Down-leg on level l >= 2: y~_l = 0, nu1 sweeps on A y = rc_l (the coarser
@@ -944,60 +850,10 @@ int cmgo_down(cmgo_ctx *c, int l) {
   if (l == c->L) sec_copy(&c->rc[l], &c->r[l], &g);
   sec_zero(&c->y[l], &g, Wr(c, l));
   for (int s = 0; s < c->P.nu1 && st == CMGO_OK; s++)
-    st = c->P.arith ? jacobi_f32(c, l, NULL, &cnt, -1) : jacobi(c, l, NULL, &cnt, -1);
+    st = sweep_any(c, l, &cnt, -1);
   if (st == CMGO_OK && c->P.arith && c->P.nu1 > 0) {
-    /* FP32 cycle: d = fl(rc - A y) in binary32; R d is then formed exactly
-     * (binary32 rounding never leaves the grid of its inputs, so the exact sum
-     * of these d is what both implementations round into rc_(l-1)) */
-    float *yf = (float *)malloc((size_t)g.np * sizeof(float));
-    double *dd = (double *)malloc((size_t)g.np * sizeof(double));
-    double *rcc = (double *)malloc((size_t)gc.np * sizeof(double));
-    int bad = 0;
-    if (!yf || !dd || !rcc) {
-      free(yf);
-      free(dd);
-      free(rcc);
-      return setst(c, CMGO_ENOMEM);
-    }
-    for (int64_t p = 0; p < g.np; p++) yf[p] = to_f32(c->y[l].v[p], &bad);
-#pragma omp parallel for collapse(2) reduction(| : bad) schedule(static)
-    for (int k = 0; k < g.nz; k++)
-      for (int j = 0; j < g.n; j++)
-        for (int i = 0; i < g.n; i++) {
-          int64_t p = idx(&g, i, j, k);
-          volatile float S;
-          if (c->P.coef) {
-            float Sd, Dd;
-            A_at_diff32(c, yf, &g, i, j, k, &Sd, &Dd);
-            S = Sd;
-          } else {
-            S = A_at_f32(yf, &g, i, j, k);
-          }
-          volatile float d = to_f32(c->rc[l].v[p], &bad) - S;
-          dd[p] = (double)d;
-        }
-    if (c->P.coef) {
-      /* diffusion: the products k_f (F_p - F_q) leave d on no common grid, so R d
-       * is formed in binary32 too, in the order of R_at */
-      float *df = (float *)malloc((size_t)g.np * sizeof(float));
-      if (!df) {
-        free(yf);
-        free(dd);
-        free(rcc);
-        return setst(c, CMGO_ENOMEM);
-      }
-      for (int64_t p = 0; p < g.np; p++) df[p] = (float)dd[p];
-      for (int k = 0; k < gc.nz; k++)
-        for (int j = 0; j < gc.n; j++)
-          for (int i = 0; i < gc.n; i++) rcc[idx(&gc, i, j, k)] = (double)R_at_f32(df, &g, i + 1, j + 1, k + 1);
-      free(df);
-    } else {
-      restrict_(&g, &gc, dd, rcc, &cnt);
-    }
-    st = bad ? CMGO_ERANGE : round_dense(&gc, rcc, Wr(c, l - 1), &c->rc[l - 1]);
-    free(yf);
-    free(dd);
-    free(rcc);
+    /* floating-point cycle: rc_(l-1) from d = fl(rc - A y) (cycle_real.inc) */
+    st = c->P.arith == 1 ? down_rhs_f32(c, l, &cnt) : down_rhs_f64(c, l, &cnt);
   } else if (st == CMGO_OK) {
     if (c->P.nu1 > 0) {
       double *Ay = (double *)malloc((size_t)g.np * sizeof(double));
@@ -1045,36 +901,10 @@ int cmgo_up(cmgo_ctx *c, int l) {
   lev g = mklev(c->P.dim, l), gc = mklev(c->P.dim, l - 1);
   long long cnt = 0;
   int st = CMGO_OK;
-  if (c->P.arith) {
-    /* FP32 cycle: z = P w_(l-1) and w_l = fl(y~_l + z) in binary32 */
-    float *wc = (float *)malloc((size_t)gc.np * sizeof(float));
-    float *zf = (float *)malloc((size_t)g.np * sizeof(float));
-    int bad = 0;
-    if (!wc || !zf) {
-      free(wc);
-      free(zf);
-      return setst(c, CMGO_ENOMEM);
-    }
-    for (int64_t p = 0; p < gc.np; p++) wc[p] = to_f32(c->w[l - 1][p], &bad);
-    for (int k = 0; k < g.nz; k++)
-      for (int j = 0; j < g.n; j++)
-        for (int i = 0; i < g.n; i++) zf[idx(&g, i, j, k)] = P_at_f32(wc, &gc, i + 1, j + 1, k + 1);
-    for (int s = 0; s < c->P.nu2 && st == CMGO_OK; s++) {
-      if (c->P.smoother) { /* red-black Gauss-Seidel: red, then black */
-        st = jacobi_f32(c, l, zf, &cnt, 0);
-        if (st == CMGO_OK) st = jacobi_f32(c, l, zf, &cnt, 1);
-      } else {
-        st = jacobi_f32(c, l, zf, &cnt, -1);
-      }
-    }
-    for (int64_t p = 0; p < g.np; p++) {
-      volatile float w = to_f32(c->y[l].v[p], &bad) + zf[p];
-      c->w[l][p] = (double)w;
-    }
-    free(wc);
-    free(zf);
+  if (c->P.arith) { /* floating-point cycle: z = P w_(l-1), w_l = y~_l + z (cycle_real.inc) */
+    st = c->P.arith == 1 ? up_f32(c, l, &cnt) : up_f64(c, l, &cnt);
     c->inexact += cnt;
-    return setst(c, bad ? CMGO_ERANGE : st);
+    return setst(c, st);
   }
   double *z = (double *)malloc((size_t)g.np * sizeof(double));
   if (!z) return setst(c, CMGO_ENOMEM);

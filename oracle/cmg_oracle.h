@@ -57,11 +57,11 @@ typedef struct {
   int N;        /* IR iterations per FMG level */
   int nu1, nu2; /* pre- and post-smoothing sweeps per level, nu2 >= 1 */
   double omega; /* Jacobi weight */
-  int arith;    /* 0: exact V-cycle; 1: FP32 V-cycle inside exact iterative
-                   refinement (see cmg_oracle.c, "FP32 V-cycle") */
+  int arith;    /* 0: exact V-cycle; 1: binary32 V-cycle, 2: binary64 V-cycle,
+                   each inside exact iterative refinement (cycle_real.inc) */
   int coef;     /* 0: Poisson; 1: diffusion -div(k grad u) with a nodal binary32
-                   coefficient field (cmgo_set_coefficient); needs arith = 1 and
-                   nu1 >= 1 (see cmg_oracle.c, "diffusion") */
+                   coefficient field (cmgo_set_coefficient); needs arith = 1 or 2
+                   and nu1 >= 1 (see cmg_oracle.c, "diffusion") */
   int smoother; /* 0: weighted Jacobi; 1: red-black Gauss-Seidel (each sweep a red
                    then a black half-sweep; needs nu1 = 0, the paper's V(0,1)) */
 } cmgo_params;

@@ -8,7 +8,7 @@ import tempfile
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcmg.so")
-SOURCES = ["cmg_stencil.cu", "cmg_stencil_f32.cu", "cmg_fast.cu", "cmg_kernels.cu", "cmg_capi.cu", "cmg_noalloc.cu"]
+SOURCES = ["cmg_stencil.cu", "cmg_stencil_fp.cu", "cmg_fast.cu", "cmg_kernels.cu", "cmg_capi.cu", "cmg_noalloc.cu"]
 HEADERS = ["cmg_device.cuh", "cmg_kernels.h", "cmg_stencil_common.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

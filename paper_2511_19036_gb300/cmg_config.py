@@ -17,8 +17,8 @@ class SolverConfig:
     omega_log2den: int = 2
     k_u: int = 2
     k_r: int = 1
-    arith: int = 0  # 0: exact V-cycle; 1: binary32 V-cycle inside exact iterative refinement
-    coef: int = 0   # 0: Poisson; 1: diffusion -div(k grad u) (needs arith = 1)
+    arith: int = 0  # 0: exact V-cycle; 1 / 2: binary32 / binary64 V-cycle inside exact iterative refinement
+    coef: int = 0   # 0: Poisson; 1: diffusion -div(k grad u) (needs arith = 1 or 2)
     smoother: int = 0  # 0: weighted Jacobi; 1: red-black Gauss-Seidel (needs nu1 = 0)
 
     @property
@@ -51,8 +51,9 @@ def config_for(name: str, L_max: int, arith: int = 0, smoother: int = 0) -> Solv
     if name.startswith("diffusion"):
         # rough coefficient (k over e^-3..e^3): Jacobi V(2,2) contracts by about
         # 1/2 per iteration, so more IR iterations than for Poisson
+        # (a floating-point cycle: binary32 unless binary64 is asked for)
         return SolverConfig(dim=dim, L_max=L_max, b1=6, b2=4, N_ir=8, nu1=2, nu2=2, omega_num=3,
-                            omega_log2den=2, arith=1, coef=1)
+                            omega_log2den=2, arith=arith if arith else 1, coef=1)
     if dim == 2:
         return SolverConfig(dim=2, L_max=L_max, b1=4, b2=4, N_ir=3, nu1=2, nu2=2, omega_num=3, omega_log2den=2,
                             arith=arith)

@@ -74,7 +74,7 @@ struct cmg_ctx {
   const float *kfield = nullptr;  // diffusion: borrowed nodal coefficient
   const double *grhs = nullptr;   // diffusion: borrowed nodal right-hand side, or null
   int grhs_log2 = 0;              // its power-of-two scale: f_L = h_L^d 2^grhs_log2 g
-  float *dbuf = nullptr;          // diffusion: d = rc - A y~ of the finest level in binary32
+  void *dbuf = nullptr;           // diffusion: d = rc - A y~ of the finest level in the cycle's type
   KStat stats[CMG_KIND_COUNT][2];  // per kernel kind; [1] = launches on level L_max
   long long launches = 0;
   double alg_bytes = 0;
@@ -223,9 +223,9 @@ extern "C" cmg_status cmg_params_check(const cmg_params *p) {
   // without pre-smoothing the restriction chain carries t^ at (p+1)L + b1 bits
   if (p->nu1 == 0 && p->k_u * p->L_max + p->b1 > 32) return CMG_ERANGE;
   if (p->omega_num <= 0 || p->omega_log2den < 0 || p->omega_log2den > 30) return CMG_EINVAL;
-  if (p->arith != CMG_ARITH_EXACT && p->arith != CMG_ARITH_FP32) return CMG_EINVAL;
+  if (p->arith != CMG_ARITH_EXACT && p->arith != CMG_ARITH_FP32 && p->arith != CMG_ARITH_FP64) return CMG_EINVAL;
   if (p->coef != CMG_COEF_POISSON && p->coef != CMG_COEF_DIFFUSION) return CMG_EINVAL;
-  if (p->coef == CMG_COEF_DIFFUSION && (p->arith != CMG_ARITH_FP32 || p->nu1 < 1)) return CMG_EINVAL;
+  if (p->coef == CMG_COEF_DIFFUSION && (p->arith == CMG_ARITH_EXACT || p->nu1 < 1)) return CMG_EINVAL;
   if (p->smoother != CMG_SMOOTHER_JACOBI &&
       (p->smoother != CMG_SMOOTHER_RBGS || p->nu1 != 0 || p->coef != CMG_COEF_POISSON))
     return CMG_EINVAL;
@@ -435,7 +435,8 @@ extern "C" cmg_status cmg_set_coefficient(cmg_ctx *ctx, const float *k_dev, int6
   ctx->kfield = k_dev;
   if (!ctx->dbuf) {
     const Geo g = make_geo(ctx->P.dim, ctx->P.L_max);
-    CU(cudaMalloc(&ctx->dbuf, (size_t)g.nz * g.n * g.R * sizeof(float)));
+    const size_t es = ctx->P.arith == CMG_ARITH_FP64 ? sizeof(double) : sizeof(float);
+    CU(cudaMalloc(&ctx->dbuf, (size_t)g.nz * g.n * g.R * es));
   }
   return CMG_OK;
 }
@@ -733,9 +734,9 @@ static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
     v.u.W = un.W;
   }
   if (o.has_z) a.wc = tmp_of(LV(ctx, l - 1).w, LV(ctx, l - 1).wg, nullptr);
-  if (ctx->P.arith == CMG_ARITH_FP32) {  // binary32 w temporaries in the same buffers
-    if (o.has_z) a.wc_f = (const float *)LV(ctx, l - 1).w;
-    if (o.write_w) a.w_out_f = (float *)v.w;
+  if (ctx->P.arith != CMG_ARITH_EXACT) {  // floating-point w temporaries in the same buffers
+    if (o.has_z) a.wc_r = LV(ctx, l - 1).w;
+    if (o.write_w) a.w_out_r = v.w;
   }
   if (ctx->P.coef == CMG_COEF_DIFFUSION) {
     a.kfield = ctx->kfield;
@@ -755,12 +756,12 @@ static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
   if (ctx->P.arith == CMG_ARITH_FP32)  // binary32 w: half the bytes
     bytes -= 0.5 * ((o.has_z ? tmp_bytes(a.gc) : 0) + (o.write_w ? tmp_bytes(v.g) : 0));
   bool fast = false;
-  if (ctx->P.arith != CMG_ARITH_FP32 && ctx->fast && ctx->fb_tiles) {
+  if (ctx->P.arith == CMG_ARITH_EXACT && ctx->fast && ctx->fb_tiles) {
     a.tiles = ctx->fb_tiles;
     if ((s = fb_slot(ctx, l, &a.ntiles))) return s;
   }
   ev_begin(ctx, kstat(ctx, CMG_KIND_SWEEP, l));
-  if (ctx->P.arith == CMG_ARITH_FP32) launch_sweep_f32(d, a, ctx->st);
+  if (ctx->P.arith != CMG_ARITH_EXACT) launch_sweep_fp(d, ctx->P.arith == CMG_ARITH_FP64, a, ctx->st);
   else if (!(fast = a.tiles && launch_sweep_fast(a, ctx->st))) launch_sweep(d, a, ctx->st);
   ev_end(ctx, kstat(ctx, CMG_KIND_SWEEP, l), bytes);
   if (fast) {
@@ -792,14 +793,15 @@ static cmg_status do_restrict(cmg_ctx *ctx, int l, bool first_sweep_below) {
   a.acc = tmp_of(c.acc, nullptr, c.accmeta);
   a.err = ctx->err;
   if (ctx->P.coef == CMG_COEF_DIFFUSION) {
-    // d = fl(rc - A y~) in binary32 on level l, then rc_(l-1) = round(R d) in R's order
+    // d = fl(rc - A y~) in the cycle's type on level l, then rc_(l-1) = round(R d) in R's order
     a.d_out = ctx->dbuf;
     a.kfield = ctx->kfield;
     a.kN = (1 << ctx->P.L_max) + 1;
     a.kstride = 1 << (ctx->P.L_max - l);
-    const double bytes = sec_bytes(v.g, a.y.W) + sec_bytes(v.g, a.rc.W) + 8.0 * v.g.nz * v.g.n * v.g.n;
+    const double es = ctx->P.arith == CMG_ARITH_FP64 ? 8.0 : 4.0;  // d written, then read by the gather
+    const double bytes = sec_bytes(v.g, a.y.W) + sec_bytes(v.g, a.rc.W) + 2 * es * v.g.nz * v.g.n * v.g.n;
     ev_begin(ctx, kstat(ctx, CMG_KIND_RESTRICT, l));
-    launch_dvec_diffusion(d, a, ctx->st);
+    launch_dvec_diffusion(d, ctx->P.arith == CMG_ARITH_FP64, a, ctx->st);
     GatherArgs ga{};
     ga.g = v.g;
     ga.gc = c.g;
@@ -809,13 +811,13 @@ static cmg_status do_restrict(cmg_ctx *ctx, int l, bool first_sweep_below) {
     if (s2) return s2;
     ga.rc_out = sec_of(c.rc);
     ga.err = ctx->err;
-    launch_gather_restrict_f32(d, ga, ctx->st);
+    launch_gather_restrict_fp(d, ctx->P.arith == CMG_ARITH_FP64, ga, ctx->st);
     ev_end(ctx, kstat(ctx, CMG_KIND_RESTRICT, l), bytes + sec_bytes(c.g, c.rc.W));
     LV(ctx, l - 1).y_zero = true;
     return launched(ctx, bytes + sec_bytes(c.g, c.rc.W));
   }
   ev_begin(ctx, kstat(ctx, CMG_KIND_RESTRICT, l));
-  if (ctx->P.arith == CMG_ARITH_FP32) launch_restrict_f32(d, a, ctx->st);
+  if (ctx->P.arith != CMG_ARITH_EXACT) launch_restrict_fp(d, ctx->P.arith == CMG_ARITH_FP64, a, ctx->st);
   else launch_restrict(d, a, ctx->st);
   ev_end(ctx, kstat(ctx, CMG_KIND_RESTRICT, l), sec_bytes(v.g, a.y.W) + sec_bytes(v.g, a.rc.W) + 2 * tmp_bytes(c.g));
   cmg_status s = launched(ctx, sec_bytes(v.g, a.y.W) + sec_bytes(v.g, a.rc.W) + 2 * tmp_bytes(c.g));
@@ -876,7 +878,10 @@ static cmg_status do_coarse(cmg_ctx *ctx, bool start, bool corr) {
       a.u_out = sec_of(ua);
     }
     a.w_out = tmp_of(v.w, v.wg, nullptr);
-    if (ctx->P.arith == CMG_ARITH_FP32) a.w_out_f = (float *)v.w;
+    if (ctx->P.arith != CMG_ARITH_EXACT) {
+      a.w_out_r = v.w;
+      a.w_f64 = ctx->P.arith == CMG_ARITH_FP64;
+    }
     if (corr) a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
   }
   if (ctx->P.coef == CMG_COEF_DIFFUSION) {

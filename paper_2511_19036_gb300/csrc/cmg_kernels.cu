@@ -3,7 +3,7 @@
 // Every kernel reads its operands in the compact BFP form (Sec. 6.1.3 of the
 // paper), computes exactly in int64 fixed point on locally chosen grids (see
 // cmg_device.cuh), and writes BFP sections rounded to nearest-even (Sec. 4).
-// The stencil kernels (cmg_stencil.cu, cmg_stencil_f32.cu) march a CTA through
+// The stencil kernels (cmg_stencil.cu, cmg_stencil_fp.cu) march a CTA through
 // z, keeping the planes k-1, k, k+1 of each column's decoded operand in
 // registers and the in-plane neighbours in two shared-memory plane buffers
 // (one x-block of 32 plus a one-node halo, by TY rows plus halo); one warp owns
@@ -219,8 +219,9 @@ __global__ void k_coarse(CoarseArgs a) {
     set_tmp1(a.uh_out, q, yG);
     return;
   }
-  if (a.w_out_f) {  // w_1 = y~_1 in binary32 (exact: W <= 24, normal range checked by the cycle)
-    a.w_out_f[0] = e == -128 ? 0.0f : ldexpf((float)q, yG);
+  if (a.w_out_r) {  // w_1 = y~_1 in the cycle's type (exact: binary32 needs W <= 24, checked at setup)
+    if (a.w_f64) ((double *)a.w_out_r)[0] = e == -128 ? 0.0 : ldexp((double)q, yG);
+    else ((float *)a.w_out_r)[0] = e == -128 ? 0.0f : ldexpf((float)q, yG);
   } else {
     set_tmp1(a.w_out, q, yG);  // w_1 = y~_1 (z_1 = 0)
   }

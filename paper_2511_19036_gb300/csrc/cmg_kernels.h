@@ -21,9 +21,9 @@ struct SweepArgs {
   Sec y_in, rc, y_out, u_in, u_out;
   Tmp wc, w_out, uhc, uh_out;
   int c_num, c_exp, cbits;  // Jacobi factor c_l = c_num 2^c_exp, cbits = bitlen(c_num)
-  const float *wc_f;   // FP32 cycle: w_(l-1) in binary32 (padded level layout)
-  float *w_out_f;      // FP32 cycle: w_l in binary32
-  const float *kfield; // diffusion (FP32 cycle): nodal k, boundary included
+  const void *wc_r;    // floating-point cycle: w_(l-1) in the cycle's type (padded level layout)
+  void *w_out_r;       // floating-point cycle: w_l in the cycle's type
+  const float *kfield; // diffusion (floating-point cycle): nodal binary32 k, boundary included
   int kN, kstride;     // 2^Lmax + 1, and the level's stride 2^(Lmax - l) in it
   float omega;         // diffusion: Jacobi weight (factor omega / D_p per node)
   int rb;              // 0: every node; 1 / 2: only the red / black nodes (red: the
@@ -73,7 +73,7 @@ struct RestrictArgs {
   int has_y;           // d = rc - A y~ (else d = rc)
   Sec y, rc;
   Tmp acc;             // exact R_l d on one global grid
-  float *d_out;        // diffusion: d = fl(rc - A y~) in binary32 (padded level layout)
+  void *d_out;         // diffusion: d = fl(rc - A y~) in the cycle's type (padded level layout)
   const float *kfield; // diffusion: nodal k, boundary included
   int kN, kstride;
   int *err;
@@ -82,7 +82,7 @@ struct RestrictArgs {
 // diffusion: rc_(l-1) = round(R_l d) with R_l d in binary32 in the fixed order
 struct GatherArgs {
   Geo g, gc;           // fine level l, coarse level l - 1
-  const float *d;      // d on level l (padded layout)
+  const void *d;       // d on level l in the cycle's type (padded layout)
   Sec rc_out;
   int *err;
 };
@@ -107,7 +107,8 @@ struct CoarseArgs {
   Sec rc, y_out, u_in, u_out;
   int corr;            // fused u~_1 += y~_1 (cycle mode)
   Tmp w_out, uh_out;
-  float *w_out_f;      // FP32 cycle: w_1 = y~_1 in binary32 (else w_out)
+  void *w_out_r;       // floating-point cycle: w_1 = y~_1 in its type (else w_out)
+  int w_f64;           // ... binary64 (else binary32)
   const float *kfield; // diffusion: the level-1 diagonal from k (FP64 division)
   int kN, kstride;
   const double *grhs;  // diffusion start mode: f_1 = 2^(grhs_log2 - d) g[gidx] (else f1 on Gf1)
@@ -176,10 +177,11 @@ struct GradArgs {
   double *dg;          // dJ/dg = h^d lam on the interior, or null
 };
 void launch_gradient(const GradArgs &a, cudaStream_t st);
-void launch_sweep_f32(int dim, const SweepArgs &a, cudaStream_t st);
-void launch_restrict_f32(int dim, const RestrictArgs &a, cudaStream_t st);
-void launch_dvec_diffusion(int dim, const RestrictArgs &a, cudaStream_t st);
-void launch_gather_restrict_f32(int dim, const GatherArgs &a, cudaStream_t st);
+// the floating-point cycle, binary64 (f64) or binary32
+void launch_sweep_fp(int dim, bool f64, const SweepArgs &a, cudaStream_t st);
+void launch_restrict_fp(int dim, bool f64, const RestrictArgs &a, cudaStream_t st);
+void launch_dvec_diffusion(int dim, bool f64, const RestrictArgs &a, cudaStream_t st);
+void launch_gather_restrict_fp(int dim, bool f64, const GatherArgs &a, cudaStream_t st);
 void launch_acc_encode(int dim, const AccArgs &a, cudaStream_t st);
 void launch_coarse(const CoarseArgs &a, cudaStream_t st);
 void launch_repack(const RepackArgs &a, cudaStream_t st);

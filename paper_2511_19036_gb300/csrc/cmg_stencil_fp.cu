@@ -1,23 +1,24 @@
-// FP32 V-cycle kernels (sm_103a): the smoothing sweep (weighted Jacobi, or a
-// red-black Gauss-Seidel half-sweep) and the restriction of the compact cycle
-// with binary32 arithmetic, inside the exact
-// iterative refinement (the precision split of Table 1: the cycle needs only
-// progressive(+m, b4) precision, the fmgResidual progressive(+p+m+1, b3)).
+// Floating-point V-cycle kernels (sm_103a): the smoothing sweep (weighted
+// Jacobi, or a red-black Gauss-Seidel half-sweep) and the restriction of the
+// compact cycle in IEEE binary32 (float) or binary64 (double) arithmetic, inside
+// the exact iterative refinement (the precision split of Table 1: the cycle needs
+// only progressive(+m, b4) precision, the fmgResidual progressive(+p+m+1, b3)).
+// The binary64 instantiation is the plain FP64 form of the same cycle.
 //
-// Every operation of the cycle rounds to nearest binary32 in one fixed order,
-// with no fused multiply-add (explicit __f*_rn intrinsics):
+// Every operation of the cycle rounds to nearest in its type, in one fixed
+// order, with no fused multiply-add (explicit round-to-nearest intrinsics):
 //   F   = fl(y + z) with z = P_l w_(l-1) = fl(fl(w_a + w_b) / 2) (or a copy)
 //   S   = fl(fl(...fl(fl((2d) F_p) - F_-x) - F_+x ... - F_+z) * h^(d-2))
 //   y'  = fl(y + fl(c fl(rc - S)))        (stored as RNE into the BFP section)
-//   w_l = fl(y'_stored + z)               (binary32 temporary for level l + 1)
+//   w_l = fl(y'_stored + z)               (temporary of the cycle's type for level l + 1)
 //   d   = fl(rc - S)                      (restriction input; R_l d is exact)
 // The stored sections (y~, rc, u~) keep their BFP format; the correction of u~
 // and u^_l = u~_l + P_l u^_(l-1) stay exact (int64), as in the exact kernels.
-// Binary32 rounding never produces bits below the grid of its inputs, so the
+// Rounding never produces bits below the grid of its inputs, so the
 // restriction's integer scatter of d on the exact path's grid stays exact.
 //
 // The tile, prefetch and ring machinery is that of cmg_stencil.cu with
-// binary32 operands (half the registers and shared memory per value).
+// floating-point operands.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -101,74 +102,164 @@ __device__ __forceinline__ long long f32_on_grid(float x, int G, bool &bad) {
   return bits < 0 ? -v : v;
 }
 
-struct SmemF {
-  float Fs[2][PLANE];        // in-plane operand, double-buffered
-  float ring[4 * CRX];       // coarse ring of w_(l-1) (binary32)
+// 2^k as binary64 (k in the normal range)
+__device__ __forceinline__ double pow2_f64(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+// binary64 x exactly as an integer on grid G (x is a multiple of 2^G and
+// |x| < 2^(G + 58), else *bad)
+__device__ __forceinline__ long long f64_on_grid(double x, int G, bool &bad) {
+  if (x == 0.0) return 0;
+  const long long bits = __double_as_longlong(x);
+  const int ef = (int)((bits >> 52) & 0x7ff);
+  if (ef == 0x7ff) {
+    bad = true;
+    return 0;
+  }
+  const long long m = ef ? ((bits & 0xfffffffffffffll) | (1ll << 52)) : (bits & 0xfffffffffffffll);
+  const int sh = imax(ef, 1) - 1075 - G;  // x = m 2^(max(ef, 1) - 1075)
+  long long v;
+  if (sh >= 0) {
+    if (sh > 5) bad = true;  // m < 2^53: |x| may reach 2^(G + 58)
+    v = m << imin(sh, 63);
+  } else {
+    const int r = imin(-sh, 63);
+    if (m & ((1ll << r) - 1)) bad = true;  // x not on grid G
+    v = m >> r;
+  }
+  return bits < 0 ? -v : v;
+}
+
+// The arithmetic of one cycle type: round-to-nearest operations, BFP values,
+// the warp-collective BFP rounding of one block (code q, block exponent e, and
+// the rounded value yr on grid Gy) and the exact conversion onto a grid.
+template <class R>
+struct RT;
+
+template <>
+struct RT<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ float pow2(int k) { return __int_as_float((k + 127) << 23); }
+  static __device__ __forceinline__ float raw(const Raw &r, int boff, int W, bool &bad) {
+    return raw_f32(r, boff, W, bad);
+  }
+  static __device__ __forceinline__ float code(int q, int e, int W, bool &bad) { return code_f32(q, e, W, bad); }
+  static __device__ __forceinline__ int encode(float x, int W, int &e, long long &yr, int &Gy, bool &bad,
+                                               int *err) {
+    const long long v = f32_block_to_grid(x, Gy, bad);
+    int sh;
+    const int q = encode_block(v, Gy, W, e, sh, err);
+    yr = rounded_value(v, q, sh);
+    return q;
+  }
+  static __device__ __forceinline__ long long on_grid(float x, int G, bool &bad) { return f32_on_grid(x, G, bad); }
+};
+
+template <>
+struct RT<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double pow2(int k) { return pow2_f64(k); }
+  // every BFP value (a code of at most 32 bits, a block exponent in [-127, 127]) is exact
+  static __device__ __forceinline__ double raw(const Raw &r, int boff, int W, bool &) {
+    if (r.e == -128) return 0.0;
+    return __dmul_rn((double)raw_code(r, boff, W), pow2_f64(r.e - W + 1));
+  }
+  static __device__ __forceinline__ double code(int q, int e, int W, bool &) {
+    return e == -128 ? 0.0 : __dmul_rn((double)q, pow2_f64(e - W + 1));
+  }
+  // RNE of the binary64 values of one block, as the oracle rounds doubles; the
+  // rounded value is the code itself on the block grid e - W + 1
+  static __device__ __forceinline__ int encode(double x, int W, int &e, long long &yr, int &Gy, bool &,
+                                               int *err) {
+    const int q = encode_block_f64(x, W, e, err);
+    yr = q;
+    Gy = e == -128 ? GRID_NONE : e - W + 1;
+    return q;
+  }
+  static __device__ __forceinline__ long long on_grid(double x, int G, bool &bad) { return f64_on_grid(x, G, bad); }
+};
+
+template <class R>
+struct SmemR {
+  R Fs[2][PLANE];            // in-plane operand, double-buffered
+  R ring[4 * CRX];           // coarse ring of w_(l-1) (the cycle's type)
   long long ringu[4 * CRX];  // coarse ring of u^_(l-1) (exact, grid G1u)
 };
 
-// one ring entry per thread of a binary32 coarse temporary
-struct StagerF {
+// one ring entry per thread of a floating-point coarse temporary
+template <class R>
+struct StagerR {
   bool on, ok;
   int cj, ci;
-  float v;
+  R v;
 };
 
-__device__ __forceinline__ StagerF make_stager_f(const Geo &gc, const Tile &T, int tid) {
-  StagerF s;
+template <class R>
+__device__ __forceinline__ StagerR<R> make_stager_r(const Geo &gc, const Tile &T, int tid) {
+  StagerR<R> s;
   s.on = tid < CRX;
   const int r = tid / CX, x = tid - (tid / CX) * CX;
   const int cj = T.cr0 + r, ci = T.cx0 + x;
   s.ok = s.on && (unsigned)ci < (unsigned)gc.n && (unsigned)cj < (unsigned)gc.n;
   s.cj = s.ok ? cj : 0;
   s.ci = s.ok ? ci : 0;
-  s.v = 0.0f;
+  s.v = (R)0;
   return s;
 }
 
-__device__ __forceinline__ void stage_load_f(StagerF &s, const float *w, const Geo &gc, int c) {
-  s.v = 0.0f;
+template <class R>
+__device__ __forceinline__ void stage_load_r(StagerR<R> &s, const R *w, const Geo &gc, int c) {
+  s.v = (R)0;
   if (s.ok && (unsigned)c < (unsigned)gc.nz) s.v = __ldg(w + (long long)(c * gc.n + s.cj) * gc.R + s.ci);
 }
 
-__device__ __forceinline__ void stage_store_f(const StagerF &s, float *ring, int c, int tid) {
+template <class R>
+__device__ __forceinline__ void stage_store_r(const StagerR<R> &s, R *ring, int c, int tid) {
   if (s.on) ring[(c & 3) * CRX + tid] = s.v;
 }
 
 // z = P_l w at a slot: the copy for a single parent, else fl(fl(a + b) / 2)
-__device__ __forceinline__ float ring_pf(const float *ring, const Slot &s, int za, int zb) {
-  const float a = ring[(za & 3) * CRX + s.oa];
+template <class R>
+__device__ __forceinline__ R ring_pr(const R *ring, const Slot &s, int za, int zb) {
+  const R a = ring[(za & 3) * CRX + s.oa];
   if (s.oa == s.ob && za == zb) return a;
-  return __fmul_rn(__fadd_rn(a, ring[(zb & 3) * CRX + s.ob]), 0.5f);
+  return RT<R>::mul(RT<R>::add(a, ring[(zb & 3) * CRX + s.ob]), (R)0.5);
 }
 
-struct MarchF {
+template <class R>
+struct MarchR {
   Sec s;        // y~ (if has_s)
   bool has_s;
-  const float *w;  // w_(l-1) (if has_z)
+  const R *w;   // w_(l-1) (if has_z)
   bool has_z;
   Tmp u;        // u^_(l-1) ring (if has_u)
   bool has_u;
   int G1u;
-  float c2d, hscale;  // 2d and h^(d-2)
-  float cjac;         // Poisson: the Jacobi factor c_l
-  // diffusion: nodal k on the finest grid (boundary included, kN^dim), read at
-  // stride 2^(Lmax - l); the Jacobi factor is omega / D_p per node
+  R c2d, hscale;  // 2d and h^(d-2)
+  R cjac;         // Poisson: the Jacobi factor c_l
+  // diffusion: nodal binary32 k on the finest grid (boundary included, kN^dim),
+  // read at stride 2^(Lmax - l); the Jacobi factor is omega / D_p per node
   const float *kfield;
   int kN, kstride;
-  float omega_f;
+  R omega;
 };
 
-// The binary32 z-march: as march() in cmg_stencil.cu, with
-// body.out(k, S, y, F, z, Pu, c) at every plane k (S, y, F, z binary32 at the
+// The floating-point z-march: as march() in cmg_stencil.cu, with
+// body.out(k, S, y, F, z, Pu, c) at every plane k (S, y, F, z of type R at the
 // thread's node; Pu = (P_l u^)(node) exact on grid G1u - 1; c the Jacobi
 // factor at the node).  COEF selects the diffusion operator: for the
 // neighbours -x, +x, -y, +y, -z, +z, kf = fl(fl(k_q + k_p) * 0.5),
 // acc = fl(acc + fl(kf fl(F_p - F_q))), dsum = fl(dsum + kf); S = fl(acc h^(d-2)),
 // D = fl(dsum h^(d-2)), c = fl(omega / D) (nodes outside the level get S = c = 0).
-template <int DIM, bool COEF, class Body>
-__device__ __forceinline__ void march_f32(const Geo &g, const Geo &gc, const Tile &T, const MarchF &in, SmemF &sm,
-                                          Body &body, bool &bad) {
+template <class R, int DIM, bool COEF, class Body>
+__device__ __forceinline__ void march_fp(const Geo &g, const Geo &gc, const Tile &T, const MarchR<R> &in,
+                                         SmemR<R> &sm, Body &body, bool &bad) {
+  using O = RT<R>;
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
   const int Ws = in.has_s ? in.s.W : 1;
   const Slot own = make_slot(g, Ws, T.x0 + lane, T.j0 + ty, ty + 1, lane + 1, T);
@@ -190,20 +281,20 @@ __device__ __forceinline__ void march_f32(const Geo &g, const Geo &gc, const Til
   }
   const int pb = g.n * g.nbx;
   const bool rings = in.has_z || in.has_u;
-  StagerF stw = make_stager_f(gc, T, tid);
+  StagerR<R> stw = make_stager_r<R>(gc, T, tid);
   Stager stu = make_stager(gc, T, tid);
   auto raw_at = [&](const Slot &sl, int kf) -> Raw {
     return raw_load(in.s, kf * pb + sl.bip, sl.cp, in.has_s && sl.ok && (unsigned)kf < (unsigned)g.nz);
   };
   // operand at a slot: F = fl(y + z) (y alone without z); y and z returned too
-  auto F_at = [&](const Slot &sl, const Raw &r, int kf, float &y, float &z) -> float {
-    y = in.has_s ? raw_f32(r, sl.cp.boff, Ws, bad) : 0.0f;
-    z = 0.0f;
+  auto F_at = [&](const Slot &sl, const Raw &r, int kf, R &y, R &z) -> R {
+    y = in.has_s ? O::raw(r, sl.cp.boff, Ws, bad) : (R)0;
+    z = (R)0;
     if (!in.has_z) return y;
     int za, zb;
     zparents<DIM>(kf, za, zb);
-    z = ring_pf(sm.ring, sl, za, zb);
-    return in.has_s ? __fadd_rn(y, z) : z;
+    z = ring_pr(sm.ring, sl, za, zb);
+    return in.has_s ? O::add(y, z) : z;
   };
   auto pu_at = [&](int kf) -> long long {
     if (!in.has_u) return 0;
@@ -211,47 +302,47 @@ __device__ __forceinline__ void march_f32(const Geo &g, const Geo &gc, const Til
     zparents<DIM>(kf, za, zb);
     return ring_p(sm.ringu, own, za, zb);
   };
-  auto kat = [&](int I, int J, int K) -> float {
-    return __ldg(in.kfield + ((long long)(DIM == 3 ? K * in.kstride : 0) * in.kN + J * in.kstride) * in.kN +
+  auto kat = [&](int I, int J, int K) -> R {
+    return (R)__ldg(in.kfield + ((long long)(DIM == 3 ? K * in.kstride : 0) * in.kN + J * in.kstride) * in.kN +
                  I * in.kstride);
   };
-  auto stencil = [&](const float *P, float Fm, float F0, float Fp, int k, float &cp) -> float {
+  auto stencil = [&](const R *P, R Fm, R F0, R Fp, int k, R &cp) -> R {
     if constexpr (COEF) {
-      cp = 0.0f;
-      if (!own.ok) return 0.0f;
+      cp = (R)0;
+      if (!own.ok) return (R)0;
       const int I = T.x0 + lane + 1, J = T.j0 + ty + 1, K = k + 1;
-      const float kp = kat(I, J, K);
-      const float nb[6] = {P[own.sm - 1], P[own.sm + 1], P[own.sm - PW], P[own.sm + PW], Fm, Fp};
-      float acc = 0.0f, dsum = 0.0f;
+      const R kp = kat(I, J, K);
+      const R nb[6] = {P[own.sm - 1], P[own.sm + 1], P[own.sm - PW], P[own.sm + PW], Fm, Fp};
+      R acc = (R)0, dsum = (R)0;
 #pragma unroll
       for (int e = 0; e < 2 * DIM; e++) {
         const int Iq = I + (e == 0 ? -1 : e == 1 ? 1 : 0), Jq = J + (e == 2 ? -1 : e == 3 ? 1 : 0);
         const int Kq = K + (e == 4 ? -1 : e == 5 ? 1 : 0);
-        const float kf = __fmul_rn(__fadd_rn(kat(Iq, Jq, Kq), kp), 0.5f);
-        acc = __fadd_rn(acc, __fmul_rn(kf, __fsub_rn(F0, nb[e])));
-        dsum = __fadd_rn(dsum, kf);
+        const R kf = O::mul(O::add(kat(Iq, Jq, Kq), kp), (R)0.5);
+        acc = O::add(acc, O::mul(kf, O::sub(F0, nb[e])));
+        dsum = O::add(dsum, kf);
       }
-      cp = __fdiv_rn(in.omega_f, __fmul_rn(dsum, in.hscale));
-      return __fmul_rn(acc, in.hscale);
+      cp = O::div(in.omega, O::mul(dsum, in.hscale));
+      return O::mul(acc, in.hscale);
     }
     cp = in.cjac;
-    float acc = __fmul_rn(in.c2d, F0);
-    acc = __fsub_rn(acc, P[own.sm - 1]);
-    acc = __fsub_rn(acc, P[own.sm + 1]);
-    acc = __fsub_rn(acc, P[own.sm - PW]);
-    acc = __fsub_rn(acc, P[own.sm + PW]);
+    R acc = O::mul(in.c2d, F0);
+    acc = O::sub(acc, P[own.sm - 1]);
+    acc = O::sub(acc, P[own.sm + 1]);
+    acc = O::sub(acc, P[own.sm - PW]);
+    acc = O::sub(acc, P[own.sm + PW]);
     if (DIM == 3) {
-      acc = __fsub_rn(acc, Fm);
-      acc = __fsub_rn(acc, Fp);
+      acc = O::sub(acc, Fm);
+      acc = O::sub(acc, Fp);
     }
-    return __fmul_rn(acc, in.hscale);
+    return O::mul(acc, in.hscale);
   };
   auto stage = [&](int c, bool load) {
     if (load) {
-      if (in.has_z) stage_load_f(stw, in.w, gc, c);
+      if (in.has_z) stage_load_r(stw, in.w, gc, c);
       if (in.has_u) stage_load(stu, in.u, gc, c);
     } else {
-      if (in.has_z) stage_store_f(stw, sm.ring, c, tid);
+      if (in.has_z) stage_store_r(stw, sm.ring, c, tid);
       if (in.has_u) stage_store(stu, sm.ringu, c, in.G1u, tid);
     }
   };
@@ -266,13 +357,13 @@ __device__ __forceinline__ void march_f32(const Geo &g, const Geo &gc, const Til
     Raw h0 = r0;
     if (has_h) h0 = raw_at(hal, 0);
     __syncthreads();
-    float y0, z0, yh, zh;
-    const float F0 = F_at(own, r0, 0, y0, z0);
+    R y0, z0, yh, zh;
+    const R F0 = F_at(own, r0, 0, y0, z0);
     sm.Fs[0][own.sm] = F0;
     if (has_h) sm.Fs[0][hal.sm] = F_at(hal, h0, 0, yh, zh);
     __syncthreads();
-    float cp;
-    const float S = stencil(sm.Fs[0], 0.0f, F0, 0.0f, 0, cp);
+    R cp;
+    const R S = stencil(sm.Fs[0], (R)0, F0, (R)0, 0, cp);
     body.advance();
     body.out(0, S, y0, F0, z0, pu_at(0), cp);
     return;
@@ -294,9 +385,9 @@ __device__ __forceinline__ void march_f32(const Geo &g, const Geo &gc, const Til
   if (has_h) hn = raw_at(hal, T.k0 + 1);
   body.prefetch(T.k0);
   __syncthreads();
-  float yx, zx, y0, z0;
-  float Fm = F_at(own, rm, T.k0 - 1, yx, zx);
-  float F0 = F_at(own, r0, T.k0, y0, z0);
+  R yx, zx, y0, z0;
+  R Fm = F_at(own, rm, T.k0 - 1, yx, zx);
+  R F0 = F_at(own, r0, T.k0, y0, z0);
   sm.Fs[T.k0 & 1][own.sm] = F0;
   if (has_h) sm.Fs[T.k0 & 1][hal.sm] = F_at(hal, h0, T.k0, yx, zx);
 
@@ -310,15 +401,15 @@ __device__ __forceinline__ void march_f32(const Geo &g, const Geo &gc, const Til
     if (k + 2 <= T.k1) rn2 = raw_at(own, k + 2);
     if (has_h && k + 2 < T.k1) hn2 = raw_at(hal, k + 2);
     __syncthreads();  // plane k complete in Fs[k & 1]; ring planes for k + 1 staged
-    float yp, zp;
-    const float Fp = F_at(own, rn, k + 1, yp, zp);
+    R yp, zp;
+    const R Fp = F_at(own, rn, k + 1, yp, zp);
     if (k + 1 < T.k1) {
-      float *nxt = sm.Fs[(k + 1) & 1];
+      R *nxt = sm.Fs[(k + 1) & 1];
       nxt[own.sm] = Fp;
       if (has_h) nxt[hal.sm] = F_at(hal, hn, k + 1, yx, zx);
     }
-    float cp;
-    const float S = stencil(sm.Fs[k & 1], Fm, F0, Fp, k, cp);
+    R cp;
+    const R S = stencil(sm.Fs[k & 1], Fm, F0, Fp, k, cp);
     body.out(k, S, y0, F0, z0, pu_at(k), cp);
     if (stg) {
       stage(cs, false);
@@ -355,11 +446,12 @@ struct SfF {
   static constexpr bool w = M == SF_UP_CORR_W_UH;
 };
 
-template <int DIM, int M>
-struct SweepBodyF {
+template <class R, int DIM, int M>
+struct SweepBodyR {
+  using O = RT<R>;
   const SweepArgs &a;
   const Geo &g;
-  float c_f;
+  R c_f;
   bool ring_u;
   int G1u, Mu;
   int bip, lane, i, j;
@@ -392,25 +484,23 @@ struct SweepBodyF {
     u_c = u_n;
   }
 
-  __device__ __forceinline__ void out(int k, float S, float y, float F0, float z, long long Pu, float cp) {
+  __device__ __forceinline__ void out(int k, R S, R y, R F0, R z, long long Pu, R cp) {
     if (!rowok) return;  // warp-uniform: one warp per row
     const int blk = k * g.n * g.nbx + bip;
     // y' = fl(y + fl(c fl(rc - S))); padding lanes carry 0; a node left out by a
     // half-sweep keeps y
-    float ynew = 0.0f;
+    R ynew = (R)0;
     if (pt) {
       if (upd(k)) {
-        const float rc = raw_f32(rc_c, cprc.boff, a.rc.W, bad);
-        ynew = __fadd_rn(y, __fmul_rn(cp, __fsub_rn(rc, S)));
+        const R rc = O::raw(rc_c, cprc.boff, a.rc.W, bad);
+        ynew = O::add(y, O::mul(cp, O::sub(rc, S)));
       } else {
         ynew = y;
       }
     }
-    int Gy;
-    const long long vy = f32_block_to_grid(ynew, Gy, bad);
-    int e, sh;
-    const int q = encode_block(vy, Gy, a.Wy, e, sh, a.err);
-    const long long yr = rounded_value(vy, q, sh);
+    int Gy, e;
+    long long yr;
+    const int q = O::encode(ynew, a.Wy, e, yr, Gy, bad, a.err);
     if (WY()) {
       pack_block(q, a.Wy, pk, a.y_out.words + (long long)blk * a.Wy);
       if (lane == 0) {
@@ -439,9 +529,9 @@ struct SweepBodyF {
       }
     }
     const long long p = (long long)(k * g.n + j) * g.R + i;
-    if (WW()) {  // w_l = fl(y~'_stored + z), binary32; the stored value is q 2^(e - W + 1)
-      const float ys = code_f32(q, e, a.Wy, bad);
-      if (pt) a.w_out_f[p] = __fadd_rn(ys, z);
+    if (WW()) {  // w_l = fl(y~'_stored + z) in R; the stored value is q 2^(e - W + 1)
+      const R ys = O::code(q, e, a.Wy, bad);
+      if (pt) ((R *)a.w_out_r)[p] = O::add(ys, z);
     }
     if (WUH()) {  // u^_l = u~_l' + P u^_(l-1), exact
       if (ring_u || !a.has_uhc) {
@@ -472,13 +562,13 @@ struct SweepBodyF {
   }
 };
 
-template <int DIM, int M, bool COEF>
-__global__ void __launch_bounds__(NT, CMG_SWEEP_F32_MINB) k_sweep_f32(SweepArgs a) {
+template <class R, int DIM, int M, bool COEF>
+__global__ void __launch_bounds__(NT, CMG_SWEEP_F32_MINB) k_sweep_fp(SweepArgs a) {
   using F = SfF<M>;
   const bool has_y = F::fixed ? F::y : (bool)a.has_y, has_z = F::fixed ? F::z : (bool)a.has_z;
   const bool write_y = F::fixed ? F::wy : (bool)a.write_y, corr = F::fixed ? F::corr : (bool)a.corr;
   const bool write_uh = F::fixed ? F::uh : (bool)a.write_uh;
-  __shared__ SmemF sm;
+  __shared__ SmemR<R> sm;
   __shared__ uint32_t pk[TY][33];
   __shared__ int smy[2], smu[2], smb[6];
   const Geo g = a.g;
@@ -488,8 +578,8 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_F32_MINB) k_sweep_f32(SweepArgs 
   const bool uring_wanted = write_uh && a.has_uhc;
   Bounds bs, bt, bu;
   footprint_bounds<DIM>(g, a.gc, T, a.y_in, false, a.uhc, false, a.uhc, uring_wanted, smb, bs, bt, bu);
-  SweepBodyF<DIM, M> b{a, g};
-  b.c_f = __fmul_rn((float)a.c_num, __int_as_float((a.c_exp + 127) << 23));
+  SweepBodyR<R, DIM, M> b{a, g};
+  b.c_f = RT<R>::mul((R)a.c_num, RT<R>::pow2(a.c_exp));
   b.ring_u = uring_wanted && (bu.G >= GRID_NONE / 2 || bu.M - bu.G <= 61);
   b.G1u = bu.G < GRID_NONE / 2 ? bu.G : 0;
   b.Mu = bu.M;
@@ -506,22 +596,22 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_F32_MINB) k_sweep_f32(SweepArgs 
   b.my.init();
   b.mu.init();
   b.pk = pk[ty];
-  MarchF in;
+  MarchR<R> in;
   in.s = a.y_in;
   in.has_s = has_y;
-  in.w = a.wc_f;
+  in.w = (const R *)a.wc_r;
   in.has_z = has_z;
   in.u = a.uhc;
   in.has_u = b.ring_u;
   in.G1u = b.G1u;
-  in.c2d = (float)(2 * DIM);
-  in.hscale = __int_as_float((127 - (DIM - 2) * g.l) << 23);
+  in.c2d = (R)(2 * DIM);
+  in.hscale = RT<R>::pow2(-(DIM - 2) * g.l);
   in.cjac = b.c_f;
   in.kfield = a.kfield;
   in.kN = a.kN;
   in.kstride = a.kstride;
-  in.omega_f = a.omega;
-  march_f32<DIM, COEF>(g, a.gc, T, in, sm, b, b.bad);
+  in.omega = (R)a.omega;
+  march_fp<R, DIM, COEF>(g, a.gc, T, in, sm, b, b.bad);
   ovf_flush(b.ovf, a.err, 111);
   ovf_flush(b.bad, a.err, 112);
   if (write_y) meta_flush(b.my, a.y_out.meta, smy);
@@ -529,8 +619,9 @@ __global__ void __launch_bounds__(NT, CMG_SWEEP_F32_MINB) k_sweep_f32(SweepArgs 
 }
 
 // ------------------------------------------------------------------ restriction
-template <int DIM>
-struct RestrictBodyF {
+template <class R, int DIM>
+struct RestrictBodyR {
+  using O = RT<R>;
   const RestrictArgs &a;
   const Geo &g;
   int Gd;
@@ -546,26 +637,26 @@ struct RestrictBodyF {
   }
   __device__ __forceinline__ void advance() { rc_c = rc_n; }
 
-  __device__ __forceinline__ void out(int k, float S, float, float, float, long long, float) {
+  __device__ __forceinline__ void out(int k, R S, R, R, R, long long, R) {
     if (!rowok || !pt) return;
-    const float d = __fsub_rn(raw_f32(rc_c, cprc.boff, a.rc.W, bad), S);
-    const long long v = f32_on_grid(d, Gd, bad);
+    const R d = O::sub(O::raw(rc_c, cprc.boff, a.rc.W, bad), S);
+    const long long v = O::on_grid(d, Gd, bad);
     if (v) scatter_restrict<DIM>((unsigned long long *)a.acc.v, a.gc, i + 1, j + 1, k + 1, v);
   }
 };
 
-template <int DIM>
-__global__ void __launch_bounds__(NT, 2) k_restrict_f32(RestrictArgs a) {
-  __shared__ SmemF sm;
+template <class R, int DIM>
+__global__ void __launch_bounds__(NT, 2) k_restrict_fp(RestrictArgs a) {
+  __shared__ SmemR<R> sm;
   const Geo g = a.g;
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
   const Tile T = make_tile(g);
-  // the grid of every d = fl(rc - A y): that of the exact d (binary32 rounding
-  // keeps its result on the grid of its inputs); the accumulator holds R d on Gd - 1
+  // the grid of every d = fl(rc - A y): that of the exact d (rounding keeps its
+  // result on the grid of its inputs); the accumulator holds R d on Gd - 1
   const int sA = (DIM - 2) * g.l;
   const int Gd = imin(sec_lsb(a.rc), a.has_y ? sec_lsb(a.y) - sA : GRID_NONE);
   if (tid == 0 && first_cta()) a.acc.meta[0] = Gd - 1;
-  RestrictBodyF<DIM> b{a, g};
+  RestrictBodyR<R, DIM> b{a, g};
   b.Gd = Gd;
   b.i = T.x0 + lane;
   b.j = T.j0 + ty;
@@ -575,7 +666,7 @@ __global__ void __launch_bounds__(NT, 2) k_restrict_f32(RestrictArgs a) {
   b.cprc = code_pos(lane, a.rc.W);
   b.ovf = false;
   b.bad = false;
-  MarchF in;
+  MarchR<R> in;
   in.s = a.y;
   in.has_s = a.has_y;
   in.w = nullptr;
@@ -583,18 +674,18 @@ __global__ void __launch_bounds__(NT, 2) k_restrict_f32(RestrictArgs a) {
   in.u = a.acc;
   in.has_u = false;
   in.G1u = 0;
-  in.c2d = (float)(2 * DIM);
-  in.hscale = __int_as_float((127 - (DIM - 2) * g.l) << 23);
-  in.cjac = 0.0f;
+  in.c2d = (R)(2 * DIM);
+  in.hscale = RT<R>::pow2(-(DIM - 2) * g.l);
+  in.cjac = (R)0;
   in.kfield = nullptr;
-  march_f32<DIM, false>(g, a.gc, T, in, sm, b, b.bad);
+  march_fp<R, DIM, false>(g, a.gc, T, in, sm, b, b.bad);
   ovf_flush(b.bad, a.err, 312);
 }
 
 // ------------------------------------------------------------------ diffusion restriction
-// d = fl(rc - A y~) of the diffusion operator, stored in binary32 on level l
-template <int DIM>
-struct DBodyF {
+// d = fl(rc - A y~) of the diffusion operator, stored in the cycle's type on level l
+template <class R, int DIM>
+struct DBodyR {
   const RestrictArgs &a;
   const Geo &g;
   int bip, i, j;
@@ -608,19 +699,19 @@ struct DBodyF {
     rc_n = raw_load(a.rc, k * g.n * g.nbx + bip, cprc, true);
   }
   __device__ __forceinline__ void advance() { rc_c = rc_n; }
-  __device__ __forceinline__ void out(int k, float S, float, float, float, long long, float) {
+  __device__ __forceinline__ void out(int k, R S, R, R, R, long long, R) {
     if (!rowok || !pt) return;
-    a.d_out[(long long)(k * g.n + j) * g.R + i] = __fsub_rn(raw_f32(rc_c, cprc.boff, a.rc.W, bad), S);
+    ((R *)a.d_out)[(long long)(k * g.n + j) * g.R + i] = RT<R>::sub(RT<R>::raw(rc_c, cprc.boff, a.rc.W, bad), S);
   }
 };
 
-template <int DIM>
+template <class R, int DIM>
 __global__ void __launch_bounds__(NT, 3) k_dvec_diff(RestrictArgs a) {
-  __shared__ SmemF sm;
+  __shared__ SmemR<R> sm;
   const Geo g = a.g;
   const int lane = threadIdx.x, ty = threadIdx.y;
   const Tile T = make_tile(g);
-  DBodyF<DIM> b{a, g};
+  DBodyR<R, DIM> b{a, g};
   b.i = T.x0 + lane;
   b.j = T.j0 + ty;
   b.rowok = b.j < g.n;
@@ -628,7 +719,7 @@ __global__ void __launch_bounds__(NT, 3) k_dvec_diff(RestrictArgs a) {
   b.bip = b.rowok ? b.j * g.nbx + T.bx : 0;
   b.cprc = code_pos(lane, a.rc.W);
   b.bad = false;
-  MarchF in;
+  MarchR<R> in;
   in.s = a.y;
   in.has_s = a.has_y;
   in.w = nullptr;
@@ -636,22 +727,23 @@ __global__ void __launch_bounds__(NT, 3) k_dvec_diff(RestrictArgs a) {
   in.u = a.acc;
   in.has_u = false;
   in.G1u = 0;
-  in.c2d = (float)(2 * DIM);
-  in.hscale = __int_as_float((127 - (DIM - 2) * g.l) << 23);
-  in.cjac = 0.0f;
+  in.c2d = (R)(2 * DIM);
+  in.hscale = RT<R>::pow2(-(DIM - 2) * g.l);
+  in.cjac = (R)0;
   in.kfield = a.kfield;
   in.kN = a.kN;
   in.kstride = a.kstride;
-  in.omega_f = 1.0f;
-  march_f32<DIM, true>(g, a.gc, T, in, sm, b, b.bad);
+  in.omega = (R)1;
+  march_fp<R, DIM, true>(g, a.gc, T, in, sm, b, b.bad);
   ovf_flush(b.bad, a.err, 313);
 }
 
-// rc_(l-1) = round(R_l d): per coarse node, in binary32, the fine node 2J plus
+// rc_(l-1) = round(R_l d): per coarse node, in the cycle's type, the fine node 2J plus
 // half the sum over the odd sets {x},{y},{x,y},{z},{x,z},{y,z},{x,y,z} of
 // d(2J - e_S) then d(2J + e_S); one warp per coarse block row
-template <int DIM>
-__global__ void __launch_bounds__(NT) k_gather_restrict_f32(GatherArgs a) {
+template <class R, int DIM>
+__global__ void __launch_bounds__(NT) k_gather_restrict_fp(GatherArgs a) {
+  using O = RT<R>;
   __shared__ uint32_t pk[TY][33];
   __shared__ int smr[2];
   const Geo gc = a.gc, g = a.g;
@@ -667,29 +759,28 @@ __global__ void __launch_bounds__(NT) k_gather_restrict_f32(GatherArgs a) {
     const int bx = (int)(blk - row * gc.nbx);
     const int ci = bx * 32 + lane;
     const int cj = (int)(row % gc.n), ck = (int)(row / gc.n);
-    float r = 0.0f;
+    R r = (R)0;
     if (ci < gc.n) {
       const int I = 2 * (ci + 1), J = 2 * (cj + 1), K = DIM == 3 ? 2 * (ck + 1) : 0;
-      auto at = [&](int Ii, int Jj, int Kk) -> float {  // 1-based fine node, zero outside
-        if (Ii < 1 || Ii > g.n || Jj < 1 || Jj > g.n) return 0.0f;
-        if (DIM == 3 && (Kk < 1 || Kk > g.nz)) return 0.0f;
+      auto at = [&](int Ii, int Jj, int Kk) -> R {  // 1-based fine node, zero outside
+        if (Ii < 1 || Ii > g.n || Jj < 1 || Jj > g.n) return (R)0;
+        if (DIM == 3 && (Kk < 1 || Kk > g.nz)) return (R)0;
         const int kk = DIM == 3 ? Kk - 1 : 0;
-        return __ldg(a.d + (long long)(kk * g.n + Jj - 1) * g.R + Ii - 1);
+        return __ldg((const R *)a.d + (long long)(kk * g.n + Jj - 1) * g.R + Ii - 1);
       };
       const int ns = DIM == 3 ? 7 : 3;
       const int ox[7] = {1, 0, 1, 0, 1, 0, 1}, oy[7] = {0, 1, 1, 0, 0, 1, 1}, oz[7] = {0, 0, 0, 1, 1, 1, 1};
-      float sum = 0.0f;
+      R sum = (R)0;
 #pragma unroll
       for (int s = 0; s < ns; s++) {
-        sum = __fadd_rn(sum, at(I - ox[s], J - oy[s], K - oz[s]));
-        sum = __fadd_rn(sum, at(I + ox[s], J + oy[s], K + oz[s]));
+        sum = O::add(sum, at(I - ox[s], J - oy[s], K - oz[s]));
+        sum = O::add(sum, at(I + ox[s], J + oy[s], K + oz[s]));
       }
-      r = __fadd_rn(at(I, J, K), __fmul_rn(sum, 0.5f));
+      r = O::add(at(I, J, K), O::mul(sum, (R)0.5));
     }
-    int G;
-    const long long v = f32_block_to_grid(r, G, bad);
-    int e, sh;
-    const int q = encode_block(v, G, a.rc_out.W, e, sh, a.err);
+    int G, e;
+    long long rr;
+    const int q = O::encode(r, a.rc_out.W, e, rr, G, bad, a.err);
     pack_block(q, a.rc_out.W, pk[ty], a.rc_out.words + blk * a.rc_out.W);
     if (lane == 0) {
       a.rc_out.exps[blk] = (int8_t)e;
@@ -704,8 +795,8 @@ dim3 stencil_grid_f(const Geo &g) {
   return dim3((unsigned)g.nbx, (unsigned)((g.n + TY - 1) / TY), (unsigned)((g.nz + ZC - 1) / ZC));
 }
 
-template <int DIM, bool COEF>
-void launch_sweep_f32_dim(const SweepArgs &a, cudaStream_t st) {
+template <class R, int DIM, bool COEF>
+void launch_sweep_fp_dim(const SweepArgs &a, cudaStream_t st) {
   const dim3 grid = stencil_grid_f(a.g), b(32, TY);
   int m = SF_GENERIC;
   if (a.has_y) {
@@ -717,49 +808,70 @@ void launch_sweep_f32_dim(const SweepArgs &a, cudaStream_t st) {
   }
   if constexpr (!COEF) {
     if (m == SF_UP0) {
-      k_sweep_f32<DIM, SF_UP0, COEF><<<grid, b, 0, st>>>(a);
+      k_sweep_fp<R, DIM, SF_UP0, COEF><<<grid, b, 0, st>>>(a);
       return;
     }
   }
   switch (m) {
-    case SF_DOWN: k_sweep_f32<DIM, SF_DOWN, COEF><<<grid, b, 0, st>>>(a); break;
-    case SF_UP: k_sweep_f32<DIM, SF_UP, COEF><<<grid, b, 0, st>>>(a); break;
-    case SF_UP_CORR: k_sweep_f32<DIM, SF_UP_CORR, COEF><<<grid, b, 0, st>>>(a); break;
-    case SF_UP_CORR_UH: k_sweep_f32<DIM, SF_UP_CORR_UH, COEF><<<grid, b, 0, st>>>(a); break;
-    case SF_UP_CORR_W_UH: k_sweep_f32<DIM, SF_UP_CORR_W_UH, COEF><<<grid, b, 0, st>>>(a); break;
-    default: k_sweep_f32<DIM, SF_GENERIC, COEF><<<grid, b, 0, st>>>(a); break;
+    case SF_DOWN: k_sweep_fp<R, DIM, SF_DOWN, COEF><<<grid, b, 0, st>>>(a); break;
+    case SF_UP: k_sweep_fp<R, DIM, SF_UP, COEF><<<grid, b, 0, st>>>(a); break;
+    case SF_UP_CORR: k_sweep_fp<R, DIM, SF_UP_CORR, COEF><<<grid, b, 0, st>>>(a); break;
+    case SF_UP_CORR_UH: k_sweep_fp<R, DIM, SF_UP_CORR_UH, COEF><<<grid, b, 0, st>>>(a); break;
+    case SF_UP_CORR_W_UH: k_sweep_fp<R, DIM, SF_UP_CORR_W_UH, COEF><<<grid, b, 0, st>>>(a); break;
+    default: k_sweep_fp<R, DIM, SF_GENERIC, COEF><<<grid, b, 0, st>>>(a); break;
+  }
+}
+
+template <class R>
+void launch_sweep_r(int dim, const SweepArgs &a, cudaStream_t st) {
+  if (a.kfield) {
+    if (dim == 3) launch_sweep_fp_dim<R, 3, true>(a, st);
+    else launch_sweep_fp_dim<R, 2, true>(a, st);
+  } else {
+    if (dim == 3) launch_sweep_fp_dim<R, 3, false>(a, st);
+    else launch_sweep_fp_dim<R, 2, false>(a, st);
   }
 }
 
 }  // namespace
 
-void launch_sweep_f32(int dim, const SweepArgs &a, cudaStream_t st) {
-  if (a.kfield) {
-    if (dim == 3) launch_sweep_f32_dim<3, true>(a, st);
-    else launch_sweep_f32_dim<2, true>(a, st);
+void launch_sweep_fp(int dim, bool f64, const SweepArgs &a, cudaStream_t st) {
+  if (f64) launch_sweep_r<double>(dim, a, st);
+  else launch_sweep_r<float>(dim, a, st);
+}
+
+void launch_dvec_diffusion(int dim, bool f64, const RestrictArgs &a, cudaStream_t st) {
+  const dim3 grid = stencil_grid_f(a.g), b(32, TY);
+  if (f64) {
+    if (dim == 3) k_dvec_diff<double, 3><<<grid, b, 0, st>>>(a);
+    else k_dvec_diff<double, 2><<<grid, b, 0, st>>>(a);
   } else {
-    if (dim == 3) launch_sweep_f32_dim<3, false>(a, st);
-    else launch_sweep_f32_dim<2, false>(a, st);
+    if (dim == 3) k_dvec_diff<float, 3><<<grid, b, 0, st>>>(a);
+    else k_dvec_diff<float, 2><<<grid, b, 0, st>>>(a);
   }
 }
 
-void launch_dvec_diffusion(int dim, const RestrictArgs &a, cudaStream_t st) {
-  const dim3 grid = stencil_grid_f(a.g), b(32, TY);
-  if (dim == 3) k_dvec_diff<3><<<grid, b, 0, st>>>(a);
-  else k_dvec_diff<2><<<grid, b, 0, st>>>(a);
-}
-
-void launch_gather_restrict_f32(int dim, const GatherArgs &a, cudaStream_t st) {
+void launch_gather_restrict_fp(int dim, bool f64, const GatherArgs &a, cudaStream_t st) {
   const dim3 b(32, TY);
   const unsigned nb = (unsigned)((a.gc.nblocks + TY - 1) / TY);
-  if (dim == 3) k_gather_restrict_f32<3><<<nb, b, 0, st>>>(a);
-  else k_gather_restrict_f32<2><<<nb, b, 0, st>>>(a);
+  if (f64) {
+    if (dim == 3) k_gather_restrict_fp<double, 3><<<nb, b, 0, st>>>(a);
+    else k_gather_restrict_fp<double, 2><<<nb, b, 0, st>>>(a);
+  } else {
+    if (dim == 3) k_gather_restrict_fp<float, 3><<<nb, b, 0, st>>>(a);
+    else k_gather_restrict_fp<float, 2><<<nb, b, 0, st>>>(a);
+  }
 }
 
-void launch_restrict_f32(int dim, const RestrictArgs &a, cudaStream_t st) {
+void launch_restrict_fp(int dim, bool f64, const RestrictArgs &a, cudaStream_t st) {
   const dim3 grid = stencil_grid_f(a.g), b(32, TY);
-  if (dim == 3) k_restrict_f32<3><<<grid, b, 0, st>>>(a);
-  else k_restrict_f32<2><<<grid, b, 0, st>>>(a);
+  if (f64) {
+    if (dim == 3) k_restrict_fp<double, 3><<<grid, b, 0, st>>>(a);
+    else k_restrict_fp<double, 2><<<grid, b, 0, st>>>(a);
+  } else {
+    if (dim == 3) k_restrict_fp<float, 3><<<grid, b, 0, st>>>(a);
+    else k_restrict_fp<float, 2><<<grid, b, 0, st>>>(a);
+  }
 }
 
 }  // namespace cmg

@@ -91,11 +91,13 @@ def test_host_side_parameter_validation_edges(libpath):
     # binary32 cycle: every r~ / y~ code must be exact in binary32
     assert check("poisson3d_manufactured", 11, arith=1) == cmg.OK
     assert check("poisson3d_manufactured", 11, arith=1, b2=14) == cmg.ERANGE
-    # diffusion runs only as the binary32 cycle, with pre-smoothing
+    # diffusion runs only with a floating-point cycle (binary32 or binary64), with pre-smoothing
     assert check("diffusion3d_grf", 8) == cmg.OK
+    assert check("diffusion3d_grf", 8, arith=2) == cmg.OK
+    assert check("poisson3d_manufactured", 11, arith=2, b2=14) == cmg.OK
     assert check("diffusion3d_grf", 8, arith=0) == cmg.EINVAL
     assert check("diffusion3d_grf", 8, nu1=0) == cmg.EINVAL
-    for k, v in [("arith", 2), ("coef", 2), ("omega_log2den", 31), ("omega_log2den", -1), ("N_ir", 0),
+    for k, v in [("arith", 3), ("coef", 2), ("omega_log2den", 31), ("omega_log2den", -1), ("N_ir", 0),
                  ("nu1", 65), ("b1", 1), ("k_u", -1)]:
         assert check("poisson3d_fourier", 8, **{k: v}) == cmg.EINVAL, k
     # without pre-smoothing t^ carries (p+1) L + b1 bits, at most 32

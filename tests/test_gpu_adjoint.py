@@ -2,7 +2,8 @@
 
 * the gradient kernel is bit-exact against the oracle's node formula;
 * forward and adjoint compact solves with a nodal right-hand side are bit-exact
-  against the oracle, and so are the resulting gradients;
+  against the oracle, and so are the resulting gradients, with the binary32
+  cycle and with the plain binary64 cycle;
 * the torch.autograd path (compact checkpoint, adjoint CMG solve, gradient
   kernel) agrees with central finite differences of J on the exact discrete
   system (dense FP64 solves), to the accuracy of the compact solves.
@@ -25,7 +26,7 @@ def cmg():
 
 def make_oracle(prob, cfg, k):
     return oracle.Oracle(prob.dim, prob.Lmax, prob.tables, prob.scale_exp, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir,
-                         nu1=cfg.nu1, nu2=cfg.nu2, omega=cfg.omega, arith=1, coef=1, kfield=k)
+                         nu1=cfg.nu1, nu2=cfg.nu2, omega=cfg.omega, arith=cfg.arith, coef=1, kfield=k)
 
 
 @pytest.mark.parametrize("dim,L", [(3, 4), (2, 6)])
@@ -45,11 +46,11 @@ def test_gradient_kernel_matches_oracle(cmg, dim, L):
     assert np.array_equal(dg.cpu().numpy(), np.ldexp(lam, -dim * L))
 
 
-@pytest.mark.parametrize("dim,L", [(3, 5), (2, 6)])
-def test_forward_adjoint_and_gradients_match_oracle(cmg, dim, L):
+@pytest.mark.parametrize("dim,L,arith", [(3, 5, 1), (2, 6, 1), (3, 5, 2), (2, 6, 2)])
+def test_forward_adjoint_and_gradients_match_oracle(cmg, dim, L, arith):
     prob = P.make_problem("diffusion%dd_grf" % dim, L)
     k = np.ascontiguousarray(prob.kfield().ravel())
-    cfg = cmg.config_for(prob.name, L)
+    cfg = cmg.config_for(prob.name, L, arith=arith)
     n = ((1 << L) - 1) ** dim
     rng = np.random.default_rng(8)
     g = np.ones(n)

@@ -1,9 +1,10 @@
-"""GPU parity of the FP32 V-cycle (binary32 cycle inside exact iterative refinement).
+"""GPU parity of the floating-point V-cycles inside exact iterative refinement.
 
-The CUDA path with arith = CMG_ARITH_FP32 against the oracle with arith = 1:
-bit-exact sections after every step, including inputs on which binary32
-operations round (a residual whose rows span about 32 binary orders), and
-whole solves at sizes where the binary32 cycle departs from the exact one.
+The CUDA path with arith = CMG_ARITH_FP32 / CMG_ARITH_FP64 against the oracle
+with arith = 1 / 2: bit-exact sections after every step, including inputs on
+which binary32 operations round (a residual whose rows span about 32 binary
+orders), and whole solves at sizes where the binary32 cycle departs from the
+exact one (where the binary64 cycle does not).
 """
 import numpy as np
 import pytest
@@ -22,15 +23,15 @@ def cmg():
     return m
 
 
-def make_pair(cmg, name, Lmax, **over):
+def make_pair(cmg, name, Lmax, arith=1, **over):
     prob = P.make_problem(name, Lmax)
-    cfg = cmg.config_for(name, Lmax, arith=1)
+    cfg = cmg.config_for(name, Lmax, arith=arith)
     for k, v in over.items():
         setattr(cfg, k, v)
     s = cmg.Solver(cfg)
     s.set_rhs(prob.tables, prob.scale_exp)
     o = oracle.Oracle.for_problem(prob, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1, nu2=cfg.nu2,
-                                  omega=cfg.omega, arith=1)
+                                  omega=cfg.omega, arith=arith)
     return prob, cfg, s, o
 
 
@@ -43,16 +44,19 @@ def same_section(cmg, s, o, which_g, which_o, level, what=""):
     assert np.array_equal(gw, ow), "words differ: %s level %d (%d words)" % (what, level, int(np.sum(gw != ow)))
 
 
-FMG_CASES = [("poisson2d_manufactured", 8, {}),
-             ("poisson2d_manufactured", 10, {}),   # the binary32 cycle rounds here
-             ("poisson3d_fourier", 6, {}),
-             ("poisson3d_manufactured", 6, {"nu1": 1, "nu2": 1}),
-             ("poisson2d_fourier", 7, {"nu1": 0, "nu2": 1})]
+FMG_CASES = [("poisson2d_manufactured", 8, 1, {}),
+             ("poisson2d_manufactured", 10, 1, {}),   # the binary32 cycle rounds here
+             ("poisson3d_fourier", 6, 1, {}),
+             ("poisson3d_manufactured", 6, 1, {"nu1": 1, "nu2": 1}),
+             ("poisson2d_fourier", 7, 1, {"nu1": 0, "nu2": 1}),
+             ("poisson2d_manufactured", 10, 2, {}),
+             ("poisson3d_fourier", 6, 2, {}),
+             ("poisson3d_manufactured", 6, 2, {"nu1": 1, "nu2": 1, "b2": 12})]
 
 
-@pytest.mark.parametrize("name,Lmax,over", FMG_CASES)
-def test_fmg_parity_fp32(cmg, name, Lmax, over):
-    prob, cfg, s, o = make_pair(cmg, name, Lmax, **over)
+@pytest.mark.parametrize("name,Lmax,arith,over", FMG_CASES)
+def test_fmg_parity_fp(cmg, name, Lmax, arith, over):
+    prob, cfg, s, o = make_pair(cmg, name, Lmax, arith, **over)
     s.fmg_solve()
     o.fmg()
     assert o.status == 0 and o.inexact == 0
@@ -70,9 +74,10 @@ def _rows_encode(dim, L, vals, W):
     return w, e
 
 
-@pytest.mark.parametrize("name,L", [("poisson3d_manufactured", 5), ("poisson2d_manufactured", 6)])
-def test_cycle_steps_where_binary32_rounds(cmg, name, L):
-    prob, cfg, s, o = make_pair(cmg, name, L)
+@pytest.mark.parametrize("name,L,arith", [("poisson3d_manufactured", 5, 1), ("poisson2d_manufactured", 6, 1),
+                                          ("poisson3d_manufactured", 5, 2), ("poisson2d_manufactured", 6, 2)])
+def test_cycle_steps_where_binary32_rounds(cmg, name, L, arith):
+    prob, cfg, s, o = make_pair(cmg, name, L, arith)
     s.start()
     o.start()
     for _ in range(L - 1):
@@ -103,8 +108,8 @@ def test_cycle_steps_where_binary32_rounds(cmg, name, L):
         o.down(l)
         same_section(cmg, s, o, cmg.SEC_Y, oracle.Y, l, "down")
         same_section(cmg, s, o, cmg.SEC_RC, oracle.RC, l - 1, "restrict")
-        if l == L and prob.dim == 3:
-            assert not np.array_equal(o.get_section(oracle.RC, l - 1, words=False)[2],
+        if l == L and prob.dim == 3:  # binary32 rounds; binary64 holds these spans
+            assert (arith == 1) != np.array_equal(o.get_section(oracle.RC, l - 1, words=False)[2],
                                       o64.get_section(oracle.RC, l - 1, words=False)[2])
     s.coarse()
     o.coarse()
@@ -121,5 +126,8 @@ def test_fp32_needs_widths_within_binary32(cmg):
     cfg.b2 = 12  # r / y~ on level 1 would need 13 + 12 bits plus the Jacobi numerator
     assert cmg.params_check(cfg) == cmg.ERANGE
     assert cmg.params_check(cmg.config_for("poisson3d_fourier", 11, arith=1)) == cmg.OK
-    bad = cmg.config_for("poisson3d_fourier", 5, arith=2)
+    bad = cmg.config_for("poisson3d_fourier", 5, arith=3)
     assert cmg.params_check(bad) == cmg.EINVAL
+    cfg = cmg.config_for("poisson3d_fourier", 14, arith=2)
+    cfg.b2 = 12  # binary64 holds these widths
+    assert cmg.params_check(cfg) == cmg.OK

@@ -46,7 +46,8 @@ def same_section(cmg, s, o, which_g, which_o, level, what=""):
 
 STEP_CASES = [("poisson2d_manufactured", 6, 0, {}), ("poisson3d_fourier", 5, 0, {}),
               ("poisson3d_manufactured", 4, 0, {"nu2": 2}), ("poisson2d_fourier", 7, 1, {}),
-              ("poisson3d_fourier", 5, 1, {"nu2": 2})]
+              ("poisson3d_fourier", 5, 1, {"nu2": 2}), ("poisson3d_fourier", 5, 2, {}),
+              ("poisson2d_manufactured", 6, 2, {})]
 
 
 @pytest.mark.parametrize("name,Lmax,arith,over", STEP_CASES)
@@ -84,7 +85,9 @@ FMG_CASES = [("poisson2d_manufactured", 8, 0, {}),   # Table 2's 2-D constants, 
              ("poisson3d_fourier", 6, 0, {}),
              ("poisson3d_manufactured", 5, 0, {"nu2": 2, "N_ir": 4}),
              ("poisson2d_manufactured", 10, 1, {}),  # binary32 rounds in the cycle
-             ("poisson3d_fourier", 6, 1, {})]
+             ("poisson3d_fourier", 6, 1, {}),
+             ("poisson2d_manufactured", 10, 2, {}),  # binary64 cycle
+             ("poisson3d_fourier", 6, 2, {})]
 
 
 @pytest.mark.parametrize("name,Lmax,arith,over", FMG_CASES)
