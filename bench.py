@@ -338,8 +338,13 @@ def run_gpu(args, wl):
     sw_bytes = sum(r["sweep_alg_bytes"] for r in reports) + sw_n * coef_bytes
     peak, peak_kind = measured_peak_hbm()
     achieved = (sw_bytes / sw_n) / (sw_ms / sw_n * 1e-3) / 1e9 if sw_n and sw_ms > 0 else None
-    traffic_per_dof = read_traffic("k_sweep", wl + ("_rbgs" if cfg.smoother else "_jacobi"))
-    roofline = {"kernel": "%s<%d> finest level" % ("k_sweep_f32" if cfg.arith else "k_sweep", cfg.dim),
+    # the finest-level sweep kernel: the specialised 3-D red / black half-sweeps on
+    # the exact red-black path, else the generic (or floating-point) sweep
+    sweep_kernel = ("k_sweep_fp" if cfg.arith else
+                    "k_fast_sweep" if (cfg.smoother and cfg.dim == 3) else "k_sweep")
+    prof_wl = wl + ("_rbgs" if cfg.smoother else "_jacobi")
+    traffic_per_dof = read_traffic(sweep_kernel, prof_wl)
+    roofline = {"kernel": "%s<%d> finest level" % (sweep_kernel, cfg.dim),
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
                 "traffic": traffic_per_dof * dofs if traffic_per_dof else None,
@@ -365,8 +370,7 @@ def run_gpu(args, wl):
         roofline["frac_survey"] = ach_s / peak
     # the bound that holds: instruction issue (4 warp-instructions per SM and clock)
     # with the ncu instruction count per 32-value row of the same kernels
-    prof_wl = wl + ("_rbgs" if cfg.smoother else "_jacobi")
-    inst_row = read_profile("k_sweep", prof_wl, "warp_inst_per_row")
+    inst_row = read_profile(sweep_kernel, prof_wl, "warp_inst_per_row")
     issue = None
     if inst_row and sw_n and sw_ms > 0:
         nsm = torch.cuda.get_device_properties(local).multi_processor_count
@@ -734,7 +738,7 @@ def run_adjoint(args, wl):
                    "l2": "working set larger than L2", "parallelism": "replicas x%d" % world},
         "J": float(J.detach()),
         "fp32_vs_fp64": fp32_vs_fp64,
-        "roofline": {"kernel": "k_sweep_f32<3> finest level (forward solve)", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": "k_sweep_fp<float, 3> finest level (forward solve)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": None,
                      "coefficient_bytes_per_launch": coef_bytes, "peak_kind": peak_kind},
         "cpu_baseline": cpu,

@@ -68,6 +68,10 @@ struct cmg_ctx {
   std::vector<int32_t> tables_host;
   bool have_rhs = false;
   int uh_upto = 0;  // u^_1 .. u^_uh_upto agree with the current u~
+  // exact Poisson path: on the finest FMG level (L = L_max) the level-(L-1)
+  // sources w and u^ are read in two levels (section + P of level L-2), so that
+  // level L_max - 1 holds no int64 copy of them
+  bool tl = false;
   int c_num2 = 0, c_exp2 = 0;  // omega / (2d) = c_num2 2^c_exp2 (level-free part)
   std::string msg;
   bool timing = false;
@@ -299,6 +303,7 @@ extern "C" cmg_status cmg_create(const cmg_params *p, void *stream, cmg_ctx **ou
   if (!ctx) return CMG_ENOMEM;
   ctx->P = *p;
   ctx->st = (cudaStream_t)stream;
+  ctx->tl = p->arith == CMG_ARITH_EXACT && p->coef == CMG_COEF_POISSON && p->L_max >= 3;
   {
     int num = p->dim == 3 ? p->omega_num / 3 : p->omega_num;
     int ex = -p->omega_log2den - (p->dim == 3 ? 1 : 2);  // 2-D: /4; 3-D: /6 = /3 /2
@@ -344,15 +349,21 @@ extern "C" cmg_status cmg_create(const cmg_params *p, void *stream, cmg_ctx **ou
     if (p->nu1 == 0 && l < p->L_max && (r = alloc_sec(ctx, v.t, g, p->k_u * p->L_max + p->b1)) != CMG_OK) break;
     if (l < p->L_max || l == 1) {
       size_t nt = (size_t)g.nz * g.n * g.R;
-      chk(cudaMalloc(&v.uh, nt * 8));
-      chk(cudaMalloc(&v.w, nt * 8));
+      // level L_max - 1 of the two-level path keeps its restriction accumulator only
+      const bool temps = !(ctx->tl && l == p->L_max - 1);
+      if (temps) {
+        chk(cudaMalloc(&v.uh, nt * 8));
+        chk(cudaMalloc(&v.w, nt * 8));
+        chk(cudaMalloc(&v.uhg, (size_t)g.nblocks * sizeof(int)));
+        chk(cudaMalloc(&v.wg, (size_t)g.nblocks * sizeof(int)));
+      }
       chk(cudaMalloc(&v.acc, nt * 8));
-      chk(cudaMalloc(&v.uhg, (size_t)g.nblocks * sizeof(int)));
-      chk(cudaMalloc(&v.wg, (size_t)g.nblocks * sizeof(int)));
       if (r == CMG_OK) {
         chk(cudaMemsetAsync(v.acc, 0, nt * 8, ctx->st));
-        chk(cudaMemsetAsync(v.uh, 0, nt * 8, ctx->st));
-        chk(cudaMemsetAsync(v.w, 0, nt * 8, ctx->st));
+        if (temps) {
+          chk(cudaMemsetAsync(v.uh, 0, nt * 8, ctx->st));
+          chk(cudaMemsetAsync(v.w, 0, nt * 8, ctx->st));
+        }
       }
     }
   }
@@ -550,6 +561,8 @@ static cmg_status fresh_meta(cmg_ctx *ctx, SecBuf &b) {
 }
 
 static cmg_status run_chain(cmg_ctx *ctx, int upto) {
+  if (ctx->tl && upto >= ctx->P.L_max - 1)  // that level has no u^ buffer on the two-level path
+    return fail(ctx, CMG_EINVAL, "u^ of level %d is formed on the fly", upto);
   for (int l = 1; l <= upto; l++) {
     Level &v = ctx->lv[l];
     ChainArgs a{};
@@ -571,6 +584,19 @@ static cmg_status run_chain(cmg_ctx *ctx, int upto) {
 
 static Level &LV(cmg_ctx *c, int l) { return c->lv[l]; }
 
+// the two-level sources are in use at the current FMG level
+static bool tl_on(const cmg_ctx *c) { return c->tl && c->L == c->P.L_max; }
+
+// w_(L-1) = y~_(L-1) + P w_(L-2) and u^_(L-1) = u~_(L-1) + P u^_(L-2) in two levels
+static Tmp2 two_level(cmg_ctx *ctx, const SecBuf &s, bool w) {
+  const Level &b = LV(ctx, ctx->L - 2);
+  Tmp2 t{};
+  t.s = sec_of(s);
+  t.b = w ? tmp_of(b.w, b.wg, nullptr) : tmp_of(b.uh, b.uhg, nullptr);
+  t.gb = b.g;
+  return t;
+}
+
 // rc section of level l at the current FMG level
 static SecBuf &rc_of(cmg_ctx *c, int l) {
   if (l == c->L) return c->lv[l].r;
@@ -580,10 +606,12 @@ static SecBuf &rc_of(cmg_ctx *c, int l) {
 
 static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
   const int L = ctx->L, d = ctx->P.dim;
-  if (ctx->uh_upto < L - 1) {
-    cmg_status s = run_chain(ctx, L - 1);
+  const bool two = tl_on(ctx);  // u^_(L-1) = u~_(L-1) + P u^_(L-2) on the fly
+  const int need = two ? L - 2 : L - 1;
+  if (ctx->uh_upto < need) {
+    cmg_status s = run_chain(ctx, need);
     if (s) return s;
-    ctx->uh_upto = L - 1;
+    ctx->uh_upto = need;
   }
   Level &v = LV(ctx, L);
   ResidArgs a{};
@@ -591,7 +619,12 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
   a.gc = L > 1 ? LV(ctx, L - 1).g : v.g;
   a.u = sec_of(v.u);
   a.has_uhc = L > 1;
-  if (L > 1) a.uhc = tmp_of(LV(ctx, L - 1).uh, LV(ctx, L - 1).uhg, nullptr);
+  if (two) {
+    a.tl = 1;
+    a.uhc2 = two_level(ctx, LV(ctx, L - 1).u, false);
+  } else if (L > 1) {
+    a.uhc = tmp_of(LV(ctx, L - 1).uh, LV(ctx, L - 1).uhg, nullptr);
+  }
   a.tables = ctx->tables;
   a.nterms = ctx->nterms;
   a.n1max = (1 << ctx->P.L_max) - 1;
@@ -638,7 +671,9 @@ static cmg_status do_residual(cmg_ctx *ctx, bool first_sweep) {
     }
   }
   a.err = ctx->err;
-  double bytes = sec_bytes(v.g, v.u.W) + (L > 1 ? tmp_bytes(a.gc) : 0) + sec_bytes(v.g, v.r.W) +
+  // the coarse source: u^_(L-1), or in two levels u~_(L-1) and u^_(L-2)
+  const double src = two ? sec_bytes(a.gc, a.uhc2.s.W) + tmp_bytes(LV(ctx, L - 2).g) : (L > 1 ? tmp_bytes(a.gc) : 0);
+  double bytes = sec_bytes(v.g, v.u.W) + src + sec_bytes(v.g, v.r.W) +
                  (first_sweep ? sec_bytes(v.g, v.r.W) : 0) + (chain ? 2 * tmp_bytes(a.gc) : 0);
   if (!diff && ctx->fast && ctx->fb_tiles) {
     a.tiles = ctx->fb_tiles;
@@ -700,9 +735,21 @@ struct SweepOpts {
   int rb = 0;  // red-black half-sweep: 1 red nodes only, 2 black nodes only
 };
 
-static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
+static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o_in) {
   const int L = ctx->L, d = ctx->P.dim;
   Level &v = LV(ctx, l);
+  SweepOpts o = o_in;
+  if (tl_on(ctx) && l == L - 1 && (o.write_w || o.write_uh)) {
+    // level L-1 keeps y~' (the finest level reads w_(L-1) = y~' + P w_(L-2)) and no w, u^
+    o.write_y = true;
+    o.write_w = false;
+    o.write_uh = false;
+  }
+  const bool two = tl_on(ctx) && l == L && o.has_z;  // z_L = P (y~_(L-1) + P w_(L-2))
+  if (two && LV(ctx, L - 1).y_zero)
+    return fail(ctx, CMG_EINVAL, "the finest up-sweep needs the level-%d up-sweep of the same cycle", L - 1);
+  if ((o.write_w && !v.w) || (o.write_uh && !v.uh))  // level L_max - 1 of the two-level path
+    return fail(ctx, CMG_EINVAL, "level %d keeps no int64 w or u^", l);
   SweepArgs a{};
   a.g = v.g;
   a.gc = l > 1 ? LV(ctx, l - 1).g : v.g;
@@ -733,7 +780,12 @@ static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
     v.u.meta = un.meta;
     v.u.W = un.W;
   }
-  if (o.has_z) a.wc = tmp_of(LV(ctx, l - 1).w, LV(ctx, l - 1).wg, nullptr);
+  if (two) {
+    a.tl = 1;
+    a.wc2 = two_level(ctx, LV(ctx, L - 1).y[LV(ctx, L - 1).ycur], true);
+  } else if (o.has_z) {
+    a.wc = tmp_of(LV(ctx, l - 1).w, LV(ctx, l - 1).wg, nullptr);
+  }
   if (ctx->P.arith != CMG_ARITH_EXACT) {  // floating-point w temporaries in the same buffers
     if (o.has_z) a.wc_r = LV(ctx, l - 1).w;
     if (o.write_w) a.w_out_r = v.w;
@@ -744,13 +796,15 @@ static cmg_status do_sweep(cmg_ctx *ctx, int l, const SweepOpts &o) {
     a.kstride = 1 << (ctx->P.L_max - l);
     a.omega = (float)ctx->P.omega_num / (float)(1 << ctx->P.omega_log2den);
   }
-  if (l > 1) a.uhc = tmp_of(LV(ctx, l - 1).uh, LV(ctx, l - 1).uhg, nullptr);
+  if (l > 1 && !two) a.uhc = tmp_of(LV(ctx, l - 1).uh, LV(ctx, l - 1).uhg, nullptr);
   if (o.write_w) a.w_out = tmp_of(v.w, v.wg, nullptr);
   if (o.write_uh) a.uh_out = tmp_of(v.uh, v.uhg, nullptr);
   jacobi_factor(ctx, l, a.c_num, a.c_exp, a.cbits);
   a.err = ctx->err;
+  // the coarse source: w_(l-1), or in two levels y~_(L-1) and w_(L-2)
+  const double zsrc = two ? sec_bytes(a.gc, a.wc2.s.W) + tmp_bytes(LV(ctx, L - 2).g) : (o.has_z ? tmp_bytes(a.gc) : 0);
   double bytes = (a.has_y ? sec_bytes(v.g, a.Wy) : 0) + sec_bytes(v.g, a.rc.W) +
-                 (o.has_z ? tmp_bytes(a.gc) : 0) + (o.write_y ? sec_bytes(v.g, a.Wy) : 0) +
+                 zsrc + (o.write_y ? sec_bytes(v.g, a.Wy) : 0) +
                  (o.corr ? 2 * sec_bytes(v.g, a.u_out.W) : 0) + (o.write_w ? tmp_bytes(v.g) : 0) +
                  (o.write_uh ? tmp_bytes(v.g) + tmp_bytes(a.gc) : 0);
   if (ctx->P.arith == CMG_ARITH_FP32)  // binary32 w: half the bytes
@@ -1017,9 +1071,9 @@ extern "C" cmg_status cmg_smooth(cmg_ctx *ctx, int l, int sweeps, int with_z) {
     return CMG_OK;
   }
   for (int k = 0; k < sweeps; k++) {  // post-smoothing with z_l = P_l w_(l-1); the last sweep writes w_l
-    SweepOpts o;
+    SweepOpts o;                        // for the next finer level of this FMG level
     o.has_z = true;
-    o.write_w = (k == sweeps - 1) && l < ctx->P.L_max;
+    o.write_w = (k == sweeps - 1) && l < ctx->L;
     if ((s = post_sweep(ctx, l, o))) return s;
   }
   return CMG_OK;
@@ -1041,7 +1095,7 @@ extern "C" cmg_status cmg_up(cmg_ctx *ctx, int l) {
   for (int k = 0; k < ctx->P.nu2; k++) {
     SweepOpts o;
     o.has_z = true;
-    o.write_w = (k == ctx->P.nu2 - 1) && l < ctx->P.L_max;
+    o.write_w = (k == ctx->P.nu2 - 1) && l < ctx->L;  // w_l feeds the next finer level only
     if ((s = post_sweep(ctx, l, o))) return s;
   }
   return CMG_OK;
@@ -1079,6 +1133,12 @@ extern "C" cmg_status cmg_vcycle(cmg_ctx *ctx) {
   return s;
 }
 
+// u^_L is written by the last IR iteration of an FMG level when the next level
+// reads it materialized (not on the two-level path into L_max)
+static bool need_uh_top(const cmg_ctx *ctx) {
+  return ctx->L < ctx->P.L_max && !(ctx->tl && ctx->L == ctx->P.L_max - 1);
+}
+
 // the production IR iteration: residual with the first sweep fused, restriction
 // with the next level's first sweep fused, corrections fused into the last up
 // sweep of every level, u^ refreshed on the way up.
@@ -1113,13 +1173,14 @@ static cmg_status ir_fused(cmg_ctx *ctx, bool need_uh_top) {
       if ((s = post_sweep(ctx, l, o))) return s;
     }
   }
-  ctx->uh_upto = (need_uh_top && L < ctx->P.L_max) ? L : L - 1;
+  // (on the two-level path level L - 1 keeps no u^: it is formed on the fly)
+  ctx->uh_upto = tl_on(ctx) ? L - 2 : (need_uh_top && L < ctx->P.L_max) ? L : L - 1;
   return CMG_OK;
 }
 
 extern "C" cmg_status cmg_ir_iteration(cmg_ctx *ctx) {
   if (!ctx || ctx->L < 2) return ctx ? fail(ctx, CMG_EINVAL, "IR needs L >= 2") : CMG_EINVAL;
-  return ir_fused(ctx, ctx->L < ctx->P.L_max);
+  return ir_fused(ctx, need_uh_top(ctx));
 }
 
 extern "C" cmg_status cmg_sync(cmg_ctx *ctx) {
@@ -1150,7 +1211,7 @@ extern "C" cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *rep) {
   cmg_status s = cmg_start(ctx);
   for (int L = 2; L <= ctx->P.L_max && !s; L++) {
     s = cmg_prolongate(ctx);
-    for (int it = 0; it < ctx->P.N_ir && !s; it++) s = ir_fused(ctx, it == ctx->P.N_ir - 1 && L < ctx->P.L_max);
+    for (int it = 0; it < ctx->P.N_ir && !s; it++) s = ir_fused(ctx, it == ctx->P.N_ir - 1 && need_uh_top(ctx));
   }
   CU(cudaEventRecord(e1, ctx->st));
   cmg_status s2 = cmg_sync(ctx);
@@ -1171,7 +1232,8 @@ extern "C" cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *rep) {
     for (int l = 1; l <= Lm; l++) {
       Geo g = make_geo(d, l);
       bits += (double)g.nblocks * (32.0 * (Wu(ctx, l, Lm) + 3 * Wr(ctx, l, Lm)) + 8.0 * 4);
-      if (l < Lm) tb += 3.0 * 8.0 * g.nz * g.n * g.R;
+      // u^, w and the restriction accumulator (two-level path: level L_max - 1 only the last)
+      if (l < Lm) tb += (ctx->tl && l == Lm - 1 ? 1.0 : 3.0) * 8.0 * g.nz * g.n * g.R;
       // without pre-smoothing: the restriction chain's t^ section on every level
       if (ctx->P.nu1 == 0 && l < Lm) tb += (double)g.nblocks * (4.0 * (ctx->P.k_u * Lm + ctx->P.b1) + 1.0);
     }
@@ -1270,16 +1332,23 @@ extern "C" cmg_status cmg_decode_solution(cmg_ctx *ctx, int64_t z0, int64_t nz, 
   const Geo &g = LV(ctx, L).g;
   if (z0 < 0 || nz < 0 || z0 + nz > g.nz) return CMG_EINVAL;
   cmg_status s;
-  if (ctx->uh_upto < L - 1) {
-    if ((s = run_chain(ctx, L - 1))) return s;
-    ctx->uh_upto = L - 1;
+  const bool two = tl_on(ctx);  // u^_(L-1) = u~_(L-1) + P u^_(L-2) on the fly
+  const int need = two ? L - 2 : L - 1;
+  if (ctx->uh_upto < need) {
+    if ((s = run_chain(ctx, need))) return s;
+    ctx->uh_upto = need;
   }
   DecodeSolArgs a{};
   a.g = g;
   a.gc = L > 1 ? LV(ctx, L - 1).g : g;
   a.u = sec_of(LV(ctx, L).u);
   a.has_uhc = L > 1;
-  if (L > 1) a.uhc = tmp_of(LV(ctx, L - 1).uh, LV(ctx, L - 1).uhg, nullptr);
+  if (two) {
+    a.tl = 1;
+    a.uhc2 = two_level(ctx, LV(ctx, L - 1).u, false);
+  } else if (L > 1) {
+    a.uhc = tmp_of(LV(ctx, L - 1).uh, LV(ctx, L - 1).uhg, nullptr);
+  }
   a.z0 = z0;
   a.nz = nz;
   a.out = out;

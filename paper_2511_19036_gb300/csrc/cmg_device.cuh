@@ -65,6 +65,16 @@ struct Tmp {
   int *meta;        // accumulators: {G, unused}
 };
 
+// A temporary of level lc held in two levels instead of materialized (the
+// finest level's coarse sources, decoded on the fly): x_lc = s_lc + P_lc x_(lc-1)
+// with s the BFP section of level lc (y~ or u~) and x_(lc-1) the materialized
+// temporary of level lc - 1 (w or u^).
+struct Tmp2 {
+  Sec s;   // level lc section
+  Tmp b;   // level lc - 1 temporary
+  Geo gb;  // level lc - 1 geometry
+};
+
 __host__ __device__ inline int imin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }
 
@@ -211,6 +221,64 @@ __device__ __forceinline__ int prolong_grid(const Tmp &c, const Geo &gc, int I, 
   if (!p.two) return G;
   if (inside(gc, p.ib, p.jb, p.kb)) G = imin(G, gb_grid(__ldg(c.gb + blk_index(gc, p.ib, p.jb, p.kb))));
   return G >= GRID_NONE / 2 ? G : G - 1;
+}
+
+// value and grid of a two-level temporary at 0-based (i, j, k) of its level g:
+// the section's code on its block grid plus P of the lower temporary, exact on
+// the returned grid G (GRID_NONE: zero); zero outside the interior.  bad: the
+// invalid code -2^(W-1).
+template <int DIM>
+__device__ __forceinline__ long long tmp2_raw(const Tmp2 &t, const Geo &g, int i, int j, int k, int &G, bool &ovf,
+                                              bool &bad) {
+  G = GRID_NONE;
+  if (!inside(g, i, j, k)) return 0;
+  const long long blk = blk_index(g, i, j, k);
+  const int e = __ldg(t.s.exps + blk);
+  long long vs = 0;
+  int Gs = GRID_NONE;
+  if (e != -128) {
+    const int q = code_at(t.s.words + blk * t.s.W, t.s.W, i & 31);
+    bad |= (unsigned)q == (0xffffffffu << (t.s.W - 1));
+    vs = q;
+    Gs = e - t.s.W + 1;
+  }
+  Parents<DIM> p(i + 1, j + 1, k + 1);
+  int ga, gb2 = GRID_NONE;
+  const long long a = tmp_raw(t.b, t.gb, p.ia, p.ja, p.ka, ga);
+  const long long b = p.two ? tmp_raw(t.b, t.gb, p.ib, p.jb, p.kb, gb2) : 0;
+  // P x_(lc-1): a copy on ga, or (a + b) / 2 on min(ga, gb) - 1
+  const int Gp = p.two ? imin(ga, gb2) - 1 : ga;
+  G = imin(Gs, Gp);
+  if (G >= GRID_NONE / 2) {
+    G = GRID_NONE;
+    return 0;
+  }
+  long long v = vs ? shl_ck(vs, Gs - G, ovf) : 0;
+  if (p.two) {
+    if (a) v += shl_ck(a, ga - 1 - G, ovf);
+    if (b) v += shl_ck(b, gb2 - 1 - G, ovf);
+  } else if (a) {
+    v += shl_ck(a, ga - G, ovf);
+  }
+  return v;
+}
+
+// (P_l x)(I, J, K) of a two-level temporary x of level l - 1 (geometry gc),
+// exact on the returned grid G (GRID_NONE: zero)
+template <int DIM>
+__device__ __forceinline__ long long prolong2(const Tmp2 &t, const Geo &gc, int I, int J, int K, int &G, bool &ovf,
+                                              bool &bad) {
+  Parents<DIM> p(I, J, K);
+  int ga, gb2 = GRID_NONE;
+  const long long a = tmp2_raw<DIM>(t, gc, p.ia, p.ja, p.ka, ga, ovf, bad);
+  const long long b = p.two ? tmp2_raw<DIM>(t, gc, p.ib, p.jb, p.kb, gb2, ovf, bad) : 0;
+  G = p.two ? imin(ga, gb2) - 1 : ga;
+  if (G >= GRID_NONE / 2) {
+    G = GRID_NONE;
+    return 0;
+  }
+  if (!p.two) return a;
+  return (a ? shl_ck(a, ga - 1 - G, ovf) : 0) + (b ? shl_ck(b, gb2 - 1 - G, ovf) : 0);
 }
 
 // ---------------------------------------------------------------- rounding

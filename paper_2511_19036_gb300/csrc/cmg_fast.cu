@@ -223,9 +223,11 @@ struct TileBounds {
   int rc_lsb, rc_msb;  // finest grid and largest exponent of rc's nonzero blocks in the tile
 };
 
+// tl: the coarse temporary t is held in two levels (t2l) instead.
 template <bool HAS_S, bool HAS_T2>
 __device__ __forceinline__ TileBounds tile_bounds(const Geo &g, const Geo &gc, const Tile &T, const Sec &sec,
-                                                  const Tmp &t, const Tmp &t2, const Sec &rc, int *sm) {
+                                                  const Tmp &t, const Tmp &t2, const Sec &rc, int *sm,
+                                                  bool tl = false, const Tmp2 *t2l = nullptr) {
   const int tid = threadIdx.y * 32 + threadIdx.x;
   if (tid < 8) sm[tid] = (tid & 1) ? MAG_NONE : GRID_NONE;  // {G, M} x {s, t, rc, t2}
   __syncthreads();
@@ -253,11 +255,12 @@ __device__ __forceinline__ TileBounds tile_bounds(const Geo &g, const Geo &gc, c
     G = GRID_NONE;
     M = MAG_NONE;
     int G2 = GRID_NONE, M2 = MAG_NONE;
+    if (tl) bounds2_scan(*t2l, gc, ck0, ck1, cj0, cj1, cb0, cb1, sm + 2, tid);
     for (int idx = tid; idx < 18 * CR * 2; idx += NT) {
       const int kk = ck0 + idx / (CR * 2), rem = idx % (CR * 2), jj = cj0 + rem / 2, bb = cb0 + (rem & 1);
       if (kk <= ck1 && jj <= cj1 && bb <= cb1) {
         const long long b = ((long long)kk * gc.n + jj) * gc.nbx + bb;
-        const int gbv = __ldg(t.gb + b);
+        const int gbv = tl ? 0 : __ldg(t.gb + b);
         if (gbv & 0xff) {
           G = imin(G, gb_grid(gbv));
           M = imax(M, gb_mag(gbv));
@@ -303,25 +306,30 @@ __device__ __forceinline__ TileBounds tile_bounds(const Geo &g, const Geo &gc, c
 // MODE 0: red from y~ = 0; 1: black with the correction of u~ (finest level);
 // 2: the same, also writing w_l = y~' + z_l and u^_l = u~_l' + P_l u^_(l-1) (the
 // levels below the finest); 3: the black half-sweep writing u^_l but no w_l (the
-// finest level of an FMG stage before the next one).  WY: width of rc and y~
+// finest level of an FMG stage before the next one); 4: mode 1 also storing y~'
+// (the level below the finest on the two-level path: the finest level reads
+// w_(L-1) = y~' + P w_(L-2) from it).  WY: width of rc and y~
 // known at compile time (0: run time); WU the same for u~; C1: the Jacobi
 // numerator is 1 (c = 2^c_exp).
 template <int MODE, int WY, int WU, bool C1>
 __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST_RED_MINB)
     k_fast_sweep(SweepArgs a) {
   constexpr bool BLACK = MODE >= 1;
-  constexpr bool WW = MODE == 2, WUH = MODE >= 2;
+  constexpr bool WW = MODE == 2, WUH = MODE == 2 || MODE == 3;
+  constexpr bool WYO = MODE == 4;  // y~' stored besides u~'
   constexpr int WO = BLACK ? WU : WY;  // output width when known
   __shared__ int Fs[2][PLANE];
   __shared__ int ring[4 * CRX];
   __shared__ long long ringu[WUH ? 4 * CRX : 1];  // P_l u^_(l-1), on one grid per tile
   __shared__ int cs[2][TY * CSW];
   __shared__ int ce[2][TY];
+  __shared__ int cs2[WYO ? 2 : 1][WYO ? TY * CSW : 1];  // the y~' codes and exponents (mode 4)
+  __shared__ int ce2[WYO ? 2 : 1][WYO ? TY : 1];
   __shared__ int smb[8];
   const Geo g = a.g, gc = a.gc;
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
   const Tile T = make_tile(g);
-  const TileBounds tb = tile_bounds<BLACK, WUH>(g, gc, T, a.y_in, a.wc, a.uhc, a.rc, smb);
+  const TileBounds tb = tile_bounds<BLACK, WUH>(g, gc, T, a.y_in, a.wc, a.uhc, a.rc, smb, a.tl, &a.wc2);
   const Bounds bF = operand_of(tb.s, tb.t);
   const bool anyF = bF.G < GRID_NONE / 2, anyR = tb.rc_lsb < GRID_NONE / 2;
   // One output grid Gy per tile and a proof that every update fits int32:
@@ -363,6 +371,8 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
   const int Wy = WY ? WY : a.Wy;
   const unsigned cmask = Wout == 32 ? FULL : (1u << Wout) - 1u;
   Packer pk = make_packer(Wout);
+  const unsigned ymask = Wy == 32 ? FULL : (1u << Wy) - 1u;
+  Packer pk2 = make_packer(WYO ? Wy : 1);
 
   const int i = T.x0 + lane, j = T.j0 + ty;
   const bool rowok = j < g.n, pt = rowok && i < g.n;
@@ -390,6 +400,11 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
     hal = make_slot(g, Ws, hi, hj, r, x, T);
   }
   Stager st = make_stager(gc, T, tid), stu = st;
+  bool sov = false, sbad = false;  // two-level staging of w_(l-1): range and invalid-code flags
+  auto load_w = [&](int c) {
+    if (a.tl) stage_load2<3>(st, a.wc2, gc, c, sov, sbad);
+    else stage_load(st, a.wc, gc, c);
+  };
   const CodePos cprc = code_pos(lane, Wrc), cpu = code_pos(lane, Wui);
   // the red / black colour of node (i, j, k): i + j + k + 1 even is red
   const int par = (i + j + 1) & 1, want = a.rb == 2 ? 1 : 0;
@@ -422,6 +437,10 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
     if (BLACK) v += shl32(y0, KY);
     int e;
     int q = enc32<WY>(v, Gy, Wy, e);
+    if constexpr (WYO) {
+      cs2[k & 1][ty * CSW + lane] = (int)((unsigned)q & ymask);
+      if (lane == 0) ce2[k & 1][ty] = e;
+    }
     if (BLACK) {  // u~' = round(u~ + y~'), y~' = q 2^(e - Wy + 1)
       const int eu = u_c.e;
       const int cu = raw_code(u_c, cpu.boff, Wui);
@@ -478,7 +497,7 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
 
   // ring planes (k0 - 2)/2 .. k0/2 before the first decode
   for (int c = (T.k0 - 2) >> 1; c <= (T.k0 >> 1); c++) {
-    stage_load(st, a.wc, gc, c);
+    load_w(c);
     stage_store<int>(st, ring, c, GF + 1, tid);
     if (WUH) {
       stage_load(stu, a.uhc, gc, c);
@@ -504,7 +523,7 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
     const int cn = (k + 2) >> 1;
     const bool stage = cn > staged_hi && cn <= gc.nz;
     if (stage) {
-      stage_load(st, a.wc, gc, cn);
+      load_w(cn);
       if (WUH) stage_load(stu, a.uhc, gc, cn);
     }
     rc_c = rc_n;
@@ -514,7 +533,10 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
     if (k + 2 <= T.k1) rn2 = raw_at(own, k + 2);
     if (has_h && k + 2 < T.k1) hn2 = raw_at(hal, k + 2);
     __syncthreads();  // plane k complete in Fs[k & 1]; codes of plane k - 1 staged
-    if (k > T.k0) pack_plane<WO>(pk, out, g, T, k - 1, cs[(k - 1) & 1], ce[(k - 1) & 1]);
+    if (k > T.k0) {
+      pack_plane<WO>(pk, out, g, T, k - 1, cs[(k - 1) & 1], ce[(k - 1) & 1]);
+      if (WYO) pack_plane<0>(pk2, a.y_out, g, T, k - 1, cs2[(k - 1) & 1], ce2[(k - 1) & 1]);
+    }
     int sp;
     const int Fp = F_at(own, rn, k + 1, sp);
     if (k + 1 < T.k1) {
@@ -539,7 +561,15 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
   __syncthreads();
   pack_plane<WO>(pk, out, g, T, T.k1 - 1, cs[(T.k1 - 1) & 1], ce[(T.k1 - 1) & 1]);
   packer_flush(pk, out.meta, a.err);
+  if (WYO) {
+    pack_plane<0>(pk2, a.y_out, g, T, T.k1 - 1, cs2[(T.k1 - 1) & 1], ce2[(T.k1 - 1) & 1]);
+    packer_flush(pk2, a.y_out.meta, a.err);
+  }
   if (WUH) ovf_flush(ovf, a.err, 113);
+  if (a.tl) {
+    ovf_flush(sov, a.err, 122);
+    corrupt_flush(sbad, a.err);
+  }
 }
 
 // ---------------------------------------------------------------- the residual
@@ -627,7 +657,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     }
   }
   Bounds bs, bt, bu;
-  footprint_bounds<3>(g, gc, T, a.u, true, a.uhc, true, a.uhc, false, smb, bs, bt, bu);
+  footprint_bounds<3>(g, gc, T, a.u, true, a.uhc, true, a.uhc, false, smb, bs, bt, bu, a.tl ? &a.uhc2 : nullptr);
   const Bounds bF = operand_of(bs, bt);
   const bool anyF = bF.G < GRID_NONE / 2;
   const int GF = anyF ? bF.G : 0;
@@ -677,6 +707,11 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     hal = make_slot(g, Ws, hi, hj, r, x, T);
   }
   Stager st = make_stager(gc, T, tid);
+  bool sov = false, sbad = false;  // two-level staging of u^_(L-1): range and invalid-code flags
+  auto load_u = [&](int c) {
+    if (a.tl) stage_load2<3>(st, a.uhc2, gc, c, sov, sbad);
+    else stage_load(st, a.uhc, gc, c);
+  };
   auto raw_at = [&](const Slot &sl, int kf) -> Raw {
     return raw_load(a.u, kf * pb + sl.bip, sl.cp, sl.ok && (unsigned)kf < (unsigned)g.nz);
   };
@@ -773,7 +808,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
   };
 
   for (int c = (T.k0 - 2) >> 1; c <= (T.k0 >> 1); c++) {
-    stage_load(st, a.uhc, gc, c);
+    load_u(c);
     stage_store<long long>(st, ring, c, GF + 1, tid);
   }
   int staged_hi = T.k0 >> 1;
@@ -792,7 +827,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
   for (int k = T.k0; k < T.k1; k++) {
     const int cn = (k + 2) >> 1;
     const bool stage = cn > staged_hi && cn <= gc.nz;
-    if (stage) stage_load(st, a.uhc, gc, cn);
+    if (stage) load_u(cn);
     Raw rn2 = rm, hn2 = rm;
     if (k + 2 <= T.k1) rn2 = raw_at(own, k + 2);
     if (has_h && k + 2 < T.k1) hn2 = raw_at(hal, k + 2);
@@ -821,6 +856,10 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
   packer_flush(pk, a.r_out.meta, a.err);
   ovf_flush(ovf, a.err, 202);
   if (__any_sync(FULL, bad_exp) && lane == 0) atomicOr(a.err, ERR_EXP);
+  if (a.tl) {
+    ovf_flush(sov, a.err, 123);
+    corrupt_flush(sbad, a.err);
+  }
 }
 
 dim3 fast_grid(const Geo &g) {
@@ -836,7 +875,9 @@ bool launch_sweep_fast(const SweepArgs &a, cudaStream_t st) {
   else if (a.has_y && a.has_z && !a.write_y && a.corr && !a.write_w && !a.write_uh) mode = 1;
   else if (a.has_y && a.has_z && !a.write_y && a.corr && a.write_w && a.write_uh && a.has_uhc) mode = 2;
   else if (a.has_y && a.has_z && !a.write_y && a.corr && !a.write_w && a.write_uh && a.has_uhc) mode = 3;
+  else if (a.has_y && a.has_z && a.write_y && a.corr && !a.write_w && !a.write_uh) mode = 4;
   else return false;
+  if (a.tl && mode >= 2) return false;  // the two-level source feeds the finest level only
   const dim3 grid = fast_grid(a.g), b(32, TY);
   const bool c1 = a.c_num == 1;
   // compile-time widths for the finest-level shapes of the red-black and Jacobi
@@ -857,10 +898,13 @@ bool launch_sweep_fast(const SweepArgs &a, cudaStream_t st) {
   } else if (mode == 2) {
     if (c1) k_fast_sweep<2, 0, 0, true><<<grid, b, 0, st>>>(a);
     else k_fast_sweep<2, 0, 0, false><<<grid, b, 0, st>>>(a);
-  } else {
+  } else if (mode == 3) {
     if (same && c1 && wy == 4 && wu == 5) k_fast_sweep<3, 4, 5, true><<<grid, b, 0, st>>>(a);
     else if (c1) k_fast_sweep<3, 0, 0, true><<<grid, b, 0, st>>>(a);
     else k_fast_sweep<3, 0, 0, false><<<grid, b, 0, st>>>(a);
+  } else {
+    if (c1) k_fast_sweep<4, 0, 0, true><<<grid, b, 0, st>>>(a);
+    else k_fast_sweep<4, 0, 0, false><<<grid, b, 0, st>>>(a);
   }
   launch_sweep_list(3, a, st);
   return true;

@@ -337,11 +337,22 @@ __global__ void k_decode_solution(DecodeSolArgs a) {
     const long long row = p / g.n;
     const int j = (int)(row % g.n), k = (int)(row / g.n) + (int)a.z0;
     int G = blk_lsb(__ldg(a.u.exps + blk_index(g, i, j, k)), a.u.W);
-    if (a.has_uhc) G = imin(G, prolong_grid<DIM>(a.uhc, a.gc, i + 1, j + 1, k + 1));
+    long long p2 = 0;  // two-level u^_(L-1): P of it on its own grid G2
+    int G2 = GRID_NONE;
+    if (a.tl) {
+      p2 = prolong2<DIM>(a.uhc2, a.gc, i + 1, j + 1, k + 1, G2, ovf, bad);
+      G = imin(G, G2);
+    } else if (a.has_uhc) {
+      G = imin(G, prolong_grid<DIM>(a.uhc, a.gc, i + 1, j + 1, k + 1));
+    }
     long long v = 0;
     if (G < GRID_NONE / 2) {
       v = sec_val_ck(a.u, g, i, j, k, G, ovf, bad);
-      if (a.has_uhc) v += prolong_tmp<DIM>(a.uhc, a.gc, i + 1, j + 1, k + 1, G, ovf);
+      if (a.tl) {
+        if (p2) v += shl_ck(p2, G2 - G, ovf);
+      } else if (a.has_uhc) {
+        v += prolong_tmp<DIM>(a.uhc, a.gc, i + 1, j + 1, k + 1, G, ovf);
+      }
     }
     a.out[p] = v == 0 ? 0.0 : scalbn(__ll2double_rn(v), G);
   }

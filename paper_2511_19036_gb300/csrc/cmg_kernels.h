@@ -20,6 +20,8 @@ struct SweepArgs {
   int Wy;              // width of y~'
   Sec y_in, rc, y_out, u_in, u_out;
   Tmp wc, w_out, uhc, uh_out;
+  int tl;              // w_(l-1) held in two levels (wc2) instead of wc
+  Tmp2 wc2;
   int c_num, c_exp, cbits;  // Jacobi factor c_l = c_num 2^c_exp, cbits = bitlen(c_num)
   const void *wc_r;    // floating-point cycle: w_(l-1) in the cycle's type (padded level layout)
   void *w_out_r;       // floating-point cycle: w_l in the cycle's type
@@ -41,6 +43,8 @@ struct ResidArgs {
   Sec u;               // u~_L
   int has_uhc;
   Tmp uhc;             // u^_(L-1)
+  int tl;              // u^_(L-1) held in two levels (uhc2) instead of uhc
+  Tmp2 uhc2;
   const int32_t *tables;
   int nterms, n1max, Lmax, fsh;
   int rhs_bits;        // bit length of the bound sum_t prod_a max|T| on |F_q| before the shift
@@ -141,6 +145,8 @@ struct DecodeSolArgs {
   Sec u;
   int has_uhc;
   Tmp uhc;
+  int tl;              // u^_(L-1) held in two levels (uhc2) instead of uhc
+  Tmp2 uhc2;
   long long z0, nz;
   double *out;
   int *err;

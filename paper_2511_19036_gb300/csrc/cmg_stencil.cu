@@ -74,6 +74,8 @@ struct MarchIn {
   bool has_s, has_t, has_u;
   int GF;        // operand grid
   int G1t, G1u;  // staging grids of the rings
+  const Tmp2 *t2 = nullptr;  // the operand temporary held in two levels instead of t
+  int *err = nullptr;        // flags of the two-level staging
 };
 
 // Calls, for every plane k of the tile in order, body.advance() (what
@@ -111,6 +113,17 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
   const int pb = g.n * g.nbx;  // blocks per plane (block indices fit in int)
   const bool rings = in.has_t || in.has_u;
   Stager st0 = make_stager(gc, T, tid), st1 = st0;
+  bool sov = false, sbad = false;  // two-level staging: range and invalid-code flags
+  auto load_t = [&](int c) {
+    if (in.t2) stage_load2<DIM>(st0, *in.t2, gc, c, sov, sbad);
+    else stage_load(st0, in.t, gc, c);
+  };
+  auto staging_flush = [&]() {
+    if (in.t2) {
+      ovf_flush(sov, in.err, 121);
+      corrupt_flush(sbad, in.err);
+    }
+  };
   const bool has_s = in.has_s;
   auto raw_at = [&](const Slot &sl, int kf) -> Raw {
     return raw_load(in.s, kf * pb + sl.bip, sl.cp, has_s && sl.ok && (unsigned)kf < (unsigned)g.nz);
@@ -131,7 +144,7 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
 
   if (DIM == 2) {
     if (rings) {
-      if (in.has_t) stage_load(st0, in.t, gc, 0);
+      if (in.has_t) load_t(0);
       if (in.has_u) stage_load(st1, in.u, gc, 0);
       if (in.has_t) stage_store(st0, sm.ring, 0, in.G1t, tid);
       if (in.has_u) stage_store(st1, sm.ringu, 0, in.G1u, tid);
@@ -154,6 +167,7 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
       const V S = 4 * F0 - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
       body.out(0, (long long)S, (long long)s0, (long long)F0, pu_at(0));
     }
+    staging_flush();
     return;
   }
 
@@ -161,7 +175,7 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
   int staged_hi = -2;
   if (rings) {
     for (int c = (T.k0 - 2) >> 1; c <= (T.k0 >> 1); c++) {
-      if (in.has_t) stage_load(st0, in.t, gc, c);
+      if (in.has_t) load_t(c);
       if (in.has_u) stage_load(st1, in.u, gc, c);
       if (in.has_t) stage_store(st0, sm.ring, c, in.G1t, tid);
       if (in.has_u) stage_store(st1, sm.ringu, c, in.G1u, tid);
@@ -186,7 +200,7 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
     const int cs = (k + 2) >> 1;
     const bool stage = rings && cs > staged_hi && cs <= gc.nz;
     if (stage) {
-      if (in.has_t) stage_load(st0, in.t, gc, cs);
+      if (in.has_t) load_t(cs);
       if (in.has_u) stage_load(st1, in.u, gc, cs);
     }
     body.advance();
@@ -220,6 +234,7 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
     rn = rn2;
     hn = hn2;
   }
+  staging_flush();
 }
 
 // March without an operand (F = 0): the body still sees every plane.
@@ -413,7 +428,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const Tile &T) {
   if (tid == 0) smy[0] = smy[1] = smu[0] = smu[1] = 0;
   const bool uring_wanted = write_uh && a.has_uhc;
   Bounds bs, bt, bu;
-  footprint_bounds<DIM>(g, a.gc, T, a.y_in, has_y, a.wc, has_z, a.uhc, uring_wanted, smb, bs, bt, bu);
+  footprint_bounds<DIM>(g, a.gc, T, a.y_in, has_y, a.wc, has_z, a.uhc, uring_wanted, smb, bs, bt, bu,
+                        a.tl ? &a.wc2 : nullptr);
   const Bounds bF = operand_of(bs, bt);
   const int GF = bF.G, MF = bF.M;
   const int sA = (DIM - 2) * g.l;
@@ -452,6 +468,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const Tile &T) {
   in.GF = GF;
   in.G1t = GF + 1;
   in.G1u = b.G1u;
+  if (a.tl) in.t2 = &a.wc2;
+  in.err = a.err;
   if (in.has_s || in.has_t || in.has_u) {
     if (narrow_operand(GF, MF)) march<DIM>(g, a.gc, T, in, sm.w32, b);
     else march<DIM>(g, a.gc, T, in, sm.w64, b);
@@ -644,7 +662,8 @@ __device__ __forceinline__ void residual_tile(const ResidArgs &a, const Tile &T)
     }
   }
   Bounds bs, bt, bu;
-  footprint_bounds<DIM>(g, a.gc, T, a.u, true, a.uhc, has_uhc, a.uhc, false, smb, bs, bt, bu);
+  footprint_bounds<DIM>(g, a.gc, T, a.u, true, a.uhc, has_uhc, a.uhc, false, smb, bs, bt, bu,
+                        a.tl ? &a.uhc2 : nullptr);
   const Bounds bF = operand_of(bs, bt);
   const int GF = bF.G, MF = bF.M;
   const int sA = (DIM - 2) * g.l;
@@ -699,6 +718,8 @@ __device__ __forceinline__ void residual_tile(const ResidArgs &a, const Tile &T)
   in.GF = GF;
   in.G1t = GF + 1;
   in.G1u = 0;
+  if (a.tl) in.t2 = &a.uhc2;
+  in.err = a.err;
   if (narrow_operand(GF, MF)) march<DIM>(g, a.gc, T, in, sm.w32, b);
   else march<DIM>(g, a.gc, T, in, sm.w64, b);
   ovf_flush(b.ovf, a.err, 202);

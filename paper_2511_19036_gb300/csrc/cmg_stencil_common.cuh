@@ -202,6 +202,19 @@ __device__ __forceinline__ void stage_load(Stager &s, const Tmp &t, const Geo &g
   }
 }
 
+// the same from a two-level temporary (x = s + P x_(l-2), see Tmp2): the value
+// and its grid as a descriptor with a nonzero bits field
+template <int DIM>
+__device__ __forceinline__ void stage_load2(Stager &s, const Tmp2 &t, const Geo &gc, int c, bool &ovf, bool &bad) {
+  s.v = 0;
+  s.gb = 0;
+  if (s.ok && (unsigned)c < (unsigned)gc.nz) {
+    int G;
+    s.v = tmp2_raw<DIM>(t, gc, s.ci, s.cj, c, G, ovf, bad);
+    s.gb = s.v ? (G << 8) | 1 : 0;
+  }
+}
+
 // the staged value on the ring's grid G1 (a 32-bit ring only where the caller
 // proved every value below 2^31 on G1)
 template <class V>
@@ -210,6 +223,48 @@ __device__ __forceinline__ void stage_store(const Stager &s, V *ring, int c, int
 }
 
 // ------------------------------------------------------------------ footprint bounds
+// Bounds of a two-level temporary over the coarse footprint planes ck0..ck1,
+// rows cj0..cj1, blocks cb0..cb1 of its level (all inside it): the section's
+// block exponents there and the lower temporary's descriptors over their
+// parents; G = min(G_s, G_b - 1), |x| < 2^(max(M_s, M_b) + 1).  CTA-cooperative:
+// atomics into sm[0] (G) and sm[1] (M), which the caller has initialised.
+__device__ __forceinline__ void bounds2_scan(const Tmp2 &t, const Geo &gc, int ck0, int ck1, int cj0, int cj1,
+                                             int cb0, int cb1, int *sm, int tid) {
+  int G = GRID_NONE, M = MAG_NONE;
+  {
+    const int nb = cb1 - cb0 + 1, nr = cj1 - cj0 + 1, np = ck1 - ck0 + 1, cnt = nb * nr * np;
+    for (int idx = tid; idx < cnt; idx += NT) {
+      const int kk = ck0 + idx / (nb * nr), rem = idx % (nb * nr);
+      const int e = __ldg(t.s.exps + ((long long)kk * gc.n + cj0 + rem / nb) * gc.nbx + cb0 + rem % nb);
+      if (e != -128) {
+        G = imin(G, e - t.s.W + 1);
+        M = imax(M, e);
+      }
+    }
+  }
+  {  // parents of coarse index c lie in c / 2 - 1 .. c / 2 of the level below
+    const Geo &gb = t.gb;
+    const int k0 = gc.nz > 1 ? imax(0, ck0 / 2 - 1) : 0, k1 = gc.nz > 1 ? imin(gb.nz - 1, ck1 / 2) : 0;
+    const int j0 = imax(0, cj0 / 2 - 1), j1 = imin(gb.n - 1, cj1 / 2);
+    const int i0 = imax(0, (cb0 * 32) / 2 - 1), i1 = imin(gb.n - 1, imin(gc.n - 1, cb1 * 32 + 31) / 2);
+    const int b0 = i0 >> 5, b1 = i1 >> 5;
+    const int nb = b1 - b0 + 1, nr = j1 - j0 + 1, np = k1 - k0 + 1;
+    if (nb > 0 && nr > 0 && np > 0) {
+      const int cnt = nb * nr * np;
+      for (int idx = tid; idx < cnt; idx += NT) {
+        const int kk = k0 + idx / (nb * nr), rem = idx % (nb * nr);
+        const int gbv = __ldg(t.b.gb + ((long long)kk * gb.n + j0 + rem / nb) * gb.nbx + b0 + rem % nb);
+        if (gbv & 0xff) {
+          G = imin(G, gb_grid(gbv) - 1);
+          M = imax(M, gb_mag(gbv));
+        }
+      }
+    }
+  }
+  if (G < GRID_NONE / 2) atomicMin(sm, G);
+  if (M > MAG_NONE / 2) atomicMax(sm + 1, M + 1);
+}
+
 struct Bounds {
   int G;  // finest grid (GRID_NONE: all zero)
   int M;  // |v| < 2^M (MAG_NONE: all zero)
@@ -219,10 +274,12 @@ struct Bounds {
 // rows j0-1..j0+TY and blocks bx-1..bx+1, and the descriptors of the coarse
 // temporaries t and u over the coarse planes, rows and blocks P_l reads.
 // sm: 6 ints; ends with a CTA barrier.
+// t2 / u2 (if not null): t / u are two-level temporaries (Tmp2) instead.
 template <int DIM>
 __device__ __forceinline__ void footprint_bounds(const Geo &g, const Geo &gc, const Tile &T, const Sec &s,
                                                  bool has_s, const Tmp &t, bool has_t, const Tmp &u, bool has_u,
-                                                 int *sm, Bounds &bs, Bounds &bt, Bounds &bu) {
+                                                 int *sm, Bounds &bs, Bounds &bt, Bounds &bu,
+                                                 const Tmp2 *t2 = nullptr, const Tmp2 *u2 = nullptr) {
   const int tid = threadIdx.y * 32 + threadIdx.x;
   if (tid == 0) {
     sm[0] = sm[2] = sm[4] = GRID_NONE;
@@ -257,6 +314,11 @@ __device__ __forceinline__ void footprint_bounds(const Geo &g, const Geo &gc, co
       const int cnt = nb * nr * np;
       for (int which = 0; which < 2; which++) {
         if (!(which ? has_u : has_t)) continue;
+        const Tmp2 *x2 = which ? u2 : t2;
+        if (x2) {
+          bounds2_scan(*x2, gc, ck0, ck1, cj0, cj1, cb0, cb1, sm + 2 + 2 * which, tid);
+          continue;
+        }
         const int *xgb = which ? u.gb : t.gb;
         int G = GRID_NONE, M = MAG_NONE;
         for (int idx = tid; idx < cnt; idx += NT) {

@@ -128,6 +128,7 @@ def test_fp32_needs_widths_within_binary32(cmg):
     assert cmg.params_check(cmg.config_for("poisson3d_fourier", 11, arith=1)) == cmg.OK
     bad = cmg.config_for("poisson3d_fourier", 5, arith=3)
     assert cmg.params_check(bad) == cmg.EINVAL
-    cfg = cmg.config_for("poisson3d_fourier", 14, arith=2)
-    cfg.b2 = 12  # binary64 holds these widths
-    assert cmg.params_check(cfg) == cmg.OK
+    for arith, want in ((1, cmg.ERANGE), (2, cmg.OK)):  # binary64 holds these widths
+        cfg = cmg.config_for("poisson3d_fourier", 11, arith=arith)
+        cfg.b2 = 16
+        assert cmg.params_check(cfg) == want
