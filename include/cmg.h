@@ -172,6 +172,17 @@ cmg_status cmg_set_fast_kernels(cmg_ctx *ctx, int enable);
  * tile to the generic kernel because the tile's footprint exceeds the kernel's
  * number range; top = 1 counts only launches on level L_max.  Synchronises. */
 cmg_status cmg_fast_stats(cmg_ctx *ctx, int top, int64_t *ctas, int64_t *fallback_ctas);
+/* Two-level coarse sources (exact Poisson path with L_max >= 3): on the finest
+ * FMG level the sweeps, the residual and the decode form w_(L-1) and
+ * u^_(L-1) from the level-(L-1) section (y~ or u~) and the level-(L-2) int64
+ * temporary when a tile stages them (Sec. 6.1: only the compact sections are
+ * kept per level), so that level L_max - 1 holds no int64 copy of them
+ * (enable = 1 frees those two arrays, 16 bytes per level-(L_max - 1) node;
+ * enable = 0 allocates them again and reads them materialized).  Both give the
+ * same bits; off by default (the materialized sources take fewer instructions
+ * per value).  Synchronises the stream; call it between solves.  EUNSUPPORTED
+ * for other configurations (enable = 0 is then a no-op). */
+cmg_status cmg_set_two_level(cmg_ctx *ctx, int enable);
 
 /* Right-hand side (matrix-free, Sec. 5.1): F(x) = 2^scale_exp * sum_t prod_a
  * T[t][a][i_a], with T an int32 table [nterms][dim][2^L_max - 1] sampled at the

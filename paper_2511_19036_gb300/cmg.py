@@ -72,6 +72,7 @@ _SIGS = {
     "cmg_last_error": (ctypes.c_char_p, [_vp]),
     "cmg_set_timing": (_i32, [_vp, _i32]),
     "cmg_set_fast_kernels": (_i32, [_vp, _i32]),
+    "cmg_set_two_level": (_i32, [_vp, _i32]),
     "cmg_fast_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "cmg_set_rhs_separable": (_i32, [_vp, _i32, _vp, _i32]),
     "cmg_fmg_solve": (_i32, [_vp, ctypes.POINTER(Report)]),
@@ -187,7 +188,8 @@ def params_check(cfg: SolverConfig) -> int:
 class Solver:
     """Compact FMG context on the current CUDA device."""
 
-    def __init__(self, cfg: SolverConfig, stream=None, timing: bool = False, fast: bool = True):
+    def __init__(self, cfg: SolverConfig, stream=None, timing: bool = False, fast: bool = True,
+                 two_level=None):
         self.cfg = cfg
         self._p = to_params(cfg)
         self._stream = _stream_handle(stream)
@@ -200,6 +202,12 @@ class Solver:
             _lib.cmg_set_timing(self._h, 1)
         if not fast:
             _lib.cmg_set_fast_kernels(self._h, 0)
+        if two_level is not None:
+            self.set_two_level(two_level)
+
+    def set_two_level(self, enable: bool):
+        """Finest level's coarse sources formed on the fly (see cmg_set_two_level)."""
+        self._chk(_lib.cmg_set_two_level(self._h, 1 if enable else 0), "cmg_set_two_level")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -71,7 +71,7 @@ struct cmg_ctx {
   // exact Poisson path: on the finest FMG level (L = L_max) the level-(L-1)
   // sources w and u^ are read in two levels (section + P of level L-2), so that
   // level L_max - 1 holds no int64 copy of them
-  bool tl = false;
+  bool tl = false, tl_capable = false;
   int c_num2 = 0, c_exp2 = 0;  // omega / (2d) = c_num2 2^c_exp2 (level-free part)
   std::string msg;
   bool timing = false;
@@ -93,6 +93,14 @@ struct cmg_ctx {
 };
 
 constexpr int FB_SLOTS = 4096;
+
+// whether a new exact Poisson context starts on the two-level path
+// (cmg_set_two_level): off, since the materialized sources are faster (the
+// kernels are bound by instruction issue, not by the bytes the two-level path
+// saves)
+#ifndef CMG_TWO_LEVEL_DEFAULT
+#define CMG_TWO_LEVEL_DEFAULT 0
+#endif
 
 // ---------------------------------------------------------------- helpers
 static cmg_status fail(cmg_ctx *c, cmg_status s, const char *fmt, ...) {
@@ -251,7 +259,8 @@ extern "C" cmg_status cmg_params_check(const cmg_params *p) {
 static cmg_status alloc_sec(cmg_ctx *ctx, SecBuf &b, const Geo &g, int Wmax) {
   b.cap_words = (size_t)g.nblocks * Wmax;
   CU(cudaMalloc(&b.words, b.cap_words * sizeof(uint32_t)));
-  CU(cudaMalloc(&b.exps, (size_t)g.nblocks));
+  // whole 16-byte units: the two-level staging copies the aligned word around an exponent
+  CU(cudaMalloc(&b.exps, ((size_t)g.nblocks + 15) & ~(size_t)15));
   b.W = Wmax;
   b.meta = ctx->meta_pool;  // slot 0: empty
   return CMG_OK;
@@ -303,7 +312,8 @@ extern "C" cmg_status cmg_create(const cmg_params *p, void *stream, cmg_ctx **ou
   if (!ctx) return CMG_ENOMEM;
   ctx->P = *p;
   ctx->st = (cudaStream_t)stream;
-  ctx->tl = p->arith == CMG_ARITH_EXACT && p->coef == CMG_COEF_POISSON && p->L_max >= 3;
+  ctx->tl_capable = p->arith == CMG_ARITH_EXACT && p->coef == CMG_COEF_POISSON && p->L_max >= 3;
+  ctx->tl = ctx->tl_capable && CMG_TWO_LEVEL_DEFAULT;
   {
     int num = p->dim == 3 ? p->omega_num / 3 : p->omega_num;
     int ex = -p->omega_log2den - (p->dim == 3 ? 1 : 2);  // 2-D: /4; 3-D: /6 = /3 /2
@@ -386,6 +396,56 @@ extern "C" cmg_status cmg_set_timing(cmg_ctx *ctx, int enable) {
 extern "C" cmg_status cmg_set_fast_kernels(cmg_ctx *ctx, int enable) {
   if (!ctx) return CMG_EINVAL;
   ctx->fast = enable != 0;
+  return CMG_OK;
+}
+
+// the int64 u^ and w of level L_max - 1 (and their block descriptors)
+static void free_top_temps(cmg_ctx *ctx) {
+  Level &v = ctx->lv[ctx->P.L_max - 1];
+  cudaFree(v.uh);
+  cudaFree(v.w);
+  cudaFree(v.uhg);
+  cudaFree(v.wg);
+  v.uh = v.w = nullptr;
+  v.uhg = v.wg = nullptr;
+}
+
+static cmg_status alloc_top_temps(cmg_ctx *ctx) {
+  Level &v = ctx->lv[ctx->P.L_max - 1];
+  const Geo &g = v.g;
+  const size_t nt = (size_t)g.nz * g.n * g.R;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&v.uh, nt * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&v.w, nt * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&v.uhg, (size_t)g.nblocks * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&v.wg, (size_t)g.nblocks * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.uh, 0, nt * 8, ctx->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.w, 0, nt * 8, ctx->st);
+  if (e != cudaSuccess) {
+    free_top_temps(ctx);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? CMG_ENOMEM : CMG_ECUDA, "allocation: %s",
+                cudaGetErrorString(e));
+  }
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_set_two_level(cmg_ctx *ctx, int enable) {
+  if (!ctx) return CMG_EINVAL;
+  const bool on = enable != 0;
+  if (on && !ctx->tl_capable)
+    return fail(ctx, CMG_EUNSUPPORTED, "two-level sources need the exact Poisson path and L_max >= 3");
+  if (on == ctx->tl) return CMG_OK;
+  CU(cudaStreamSynchronize(ctx->st));  // no launch in flight reads the buffers
+  if (on) {
+    free_top_temps(ctx);
+  } else {
+    cmg_status s = alloc_top_temps(ctx);
+    if (s) return s;
+  }
+  ctx->tl = on;
+  // u^ of level L_max - 1 is not materialized on the two-level path, and not yet
+  // on the other one
+  ctx->uh_upto = std::min(ctx->uh_upto, ctx->P.L_max - 2);
   return CMG_OK;
 }
 

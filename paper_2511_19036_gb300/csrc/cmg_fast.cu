@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "cmg_device.cuh"
 #include "cmg_kernels.h"
@@ -311,7 +312,7 @@ __device__ __forceinline__ TileBounds tile_bounds(const Geo &g, const Geo &gc, c
 // w_(L-1) = y~' + P w_(L-2) from it).  WY: width of rc and y~
 // known at compile time (0: run time); WU the same for u~; C1: the Jacobi
 // numerator is 1 (c = 2^c_exp).
-template <int MODE, int WY, int WU, bool C1>
+template <int MODE, int WY, int WU, bool C1, bool TL>
 __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST_RED_MINB)
     k_fast_sweep(SweepArgs a) {
   constexpr bool BLACK = MODE >= 1;
@@ -323,13 +324,14 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
   __shared__ long long ringu[WUH ? 4 * CRX : 1];  // P_l u^_(l-1), on one grid per tile
   __shared__ int cs[2][TY * CSW];
   __shared__ int ce[2][TY];
+  __shared__ std::conditional_t<TL, Two2, char> two;  // staging of the two-level w_(l-1)
   __shared__ int cs2[WYO ? 2 : 1][WYO ? TY * CSW : 1];  // the y~' codes and exponents (mode 4)
   __shared__ int ce2[WYO ? 2 : 1][WYO ? TY : 1];
   __shared__ int smb[8];
   const Geo g = a.g, gc = a.gc;
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
   const Tile T = make_tile(g);
-  const TileBounds tb = tile_bounds<BLACK, WUH>(g, gc, T, a.y_in, a.wc, a.uhc, a.rc, smb, a.tl, &a.wc2);
+  const TileBounds tb = tile_bounds<BLACK, WUH>(g, gc, T, a.y_in, a.wc, a.uhc, a.rc, smb, TL, &a.wc2);
   const Bounds bF = operand_of(tb.s, tb.t);
   const bool anyF = bF.G < GRID_NONE / 2, anyR = tb.rc_lsb < GRID_NONE / 2;
   // One output grid Gy per tile and a proof that every update fits int32:
@@ -400,10 +402,14 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
     hal = make_slot(g, Ws, hi, hj, r, x, T);
   }
   Stager st = make_stager(gc, T, tid), stu = st;
-  bool sov = false, sbad = false;  // two-level staging of w_(l-1): range and invalid-code flags
+  bool sbad = false;  // two-level staging of w_(l-1): an invalid code met
   auto load_w = [&](int c) {
-    if (a.tl) stage_load2<3>(st, a.wc2, gc, c, sov, sbad);
+    if constexpr (TL) two_step_issue(st, a.wc2, gc, T, c, two, tid);
     else stage_load(st, a.wc, gc, c);
+  };
+  auto store_w = [&](int c) {
+    if constexpr (TL) two_step_store<3>(st, a.wc2, gc, T, c, two, ring, GF + 1, tid, sbad);
+    else stage_store<int>(st, ring, c, GF + 1, tid);
   };
   const CodePos cprc = code_pos(lane, Wrc), cpu = code_pos(lane, Wui);
   // the red / black colour of node (i, j, k): i + j + k + 1 even is red
@@ -496,9 +502,12 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
   };
 
   // ring planes (k0 - 2)/2 .. k0/2 before the first decode
+  if constexpr (TL) two_prologue<3>(st, a.wc2, gc, T, (T.k0 - 2) >> 1, T.k0 >> 1, two, ring, GF + 1, tid, sbad);
   for (int c = (T.k0 - 2) >> 1; c <= (T.k0 >> 1); c++) {
-    load_w(c);
-    stage_store<int>(st, ring, c, GF + 1, tid);
+    if (!TL) {
+      load_w(c);
+      store_w(c);
+    }
     if (WUH) {
       stage_load(stu, a.uhc, gc, c);
       stage_store<long long>(stu, ringu, c, G1u, tid);
@@ -548,7 +557,7 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
     const int S = 6 * F0 - Fm - Fp - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
     out_step(k, S, s0, F0);
     if (stage) {
-      stage_store<int>(st, ring, cn, GF + 1, tid);
+      store_w(cn);
       if (WUH) stage_store<long long>(stu, ringu, cn, G1u, tid);
       staged_hi = cn;
     }
@@ -566,8 +575,8 @@ __global__ void __launch_bounds__(NT, MODE >= 1 ? CMG_FAST_BLACK_MINB : CMG_FAST
     packer_flush(pk2, a.y_out.meta, a.err);
   }
   if (WUH) ovf_flush(ovf, a.err, 113);
-  if (a.tl) {
-    ovf_flush(sov, a.err, 122);
+  if constexpr (TL) {
+    cp_async_wait_all();  // the step issued ahead past the tile's last plane
     corrupt_flush(sbad, a.err);
   }
 }
@@ -629,12 +638,13 @@ __device__ __forceinline__ int enc_norm(int ts, bool stk, int bmax, int dn, int 
 // right-hand side is formed exactly from the separable tables with 32 x 32-bit
 // multiply-adds; x-adjacent contributions to the same coarse node are added in
 // the warp before the atomics.
-template <int NTERMS, int WR>  // right-hand-side terms and r~ width (0: run time)
+template <int NTERMS, int WR, bool TL>  // right-hand-side terms, r~ width (0: run time), two-level u^_(L-1)
 __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArgs a) {
   const int nterms = NTERMS ? NTERMS : a.nterms;
   __shared__ long long Fs[2][PLANE];
   __shared__ long long ring[4 * CRX];
   __shared__ RhsTab rs;
+  __shared__ std::conditional_t<TL, Two2, char> two;  // staging of the two-level u^_(L-1)
   __shared__ int cs[2][TY * CSW];
   __shared__ int ce[2][TY];
   __shared__ int smb[6];
@@ -657,7 +667,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     }
   }
   Bounds bs, bt, bu;
-  footprint_bounds<3>(g, gc, T, a.u, true, a.uhc, true, a.uhc, false, smb, bs, bt, bu, a.tl ? &a.uhc2 : nullptr);
+  footprint_bounds<3>(g, gc, T, a.u, true, a.uhc, true, a.uhc, false, smb, bs, bt, bu, TL ? &a.uhc2 : nullptr);
   const Bounds bF = operand_of(bs, bt);
   const bool anyF = bF.G < GRID_NONE / 2;
   const int GF = anyF ? bF.G : 0;
@@ -707,10 +717,14 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     hal = make_slot(g, Ws, hi, hj, r, x, T);
   }
   Stager st = make_stager(gc, T, tid);
-  bool sov = false, sbad = false;  // two-level staging of u^_(L-1): range and invalid-code flags
+  bool sbad = false;  // two-level staging of u^_(L-1): an invalid code met
   auto load_u = [&](int c) {
-    if (a.tl) stage_load2<3>(st, a.uhc2, gc, c, sov, sbad);
+    if constexpr (TL) two_step_issue(st, a.uhc2, gc, T, c, two, tid);
     else stage_load(st, a.uhc, gc, c);
+  };
+  auto store_u = [&](int c) {
+    if constexpr (TL) two_step_store<3>(st, a.uhc2, gc, T, c, two, ring, GF + 1, tid, sbad);
+    else stage_store<long long>(st, ring, c, GF + 1, tid);
   };
   auto raw_at = [&](const Slot &sl, int kf) -> Raw {
     return raw_load(a.u, kf * pb + sl.bip, sl.cp, sl.ok && (unsigned)kf < (unsigned)g.nz);
@@ -807,9 +821,13 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
       atomicAdd(accB + (long long)(zb - 1) * cplane, (unsigned long long)vB);
   };
 
-  for (int c = (T.k0 - 2) >> 1; c <= (T.k0 >> 1); c++) {
-    load_u(c);
-    stage_store<long long>(st, ring, c, GF + 1, tid);
+  if constexpr (TL) {
+    two_prologue<3>(st, a.uhc2, gc, T, (T.k0 - 2) >> 1, T.k0 >> 1, two, ring, GF + 1, tid, sbad);
+  } else {
+    for (int c = (T.k0 - 2) >> 1; c <= (T.k0 >> 1); c++) {
+      load_u(c);
+      store_u(c);
+    }
   }
   int staged_hi = T.k0 >> 1;
   const Raw rm = raw_at(own, T.k0 - 1);
@@ -843,7 +861,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     const long long S = 6 * F0 - Fm - Fp - P[own.sm - 1] - P[own.sm + 1] - P[own.sm - PW] - P[own.sm + PW];
     out_step(k, S);
     if (stage) {
-      stage_store<long long>(st, ring, cn, GF + 1, tid);
+      store_u(cn);
       staged_hi = cn;
     }
     Fm = F0;
@@ -856,8 +874,8 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
   packer_flush(pk, a.r_out.meta, a.err);
   ovf_flush(ovf, a.err, 202);
   if (__any_sync(FULL, bad_exp) && lane == 0) atomicOr(a.err, ERR_EXP);
-  if (a.tl) {
-    ovf_flush(sov, a.err, 123);
+  if constexpr (TL) {
+    cp_async_wait_all();  // the step issued ahead past the tile's last plane
     corrupt_flush(sbad, a.err);
   }
 }
@@ -884,27 +902,37 @@ bool launch_sweep_fast(const SweepArgs &a, cudaStream_t st) {
   // cycles (r~, y~ at b2 = 3..5 bits, u~ at b1 = 5 or 6)
   const int wy = a.rc.W, wu = mode ? a.u_in.W : 0;
   const bool same = mode == 0 ? a.y_out.W == wy : (a.y_in.W == wy && a.u_out.W == wu && a.Wy == wy);
-  if (mode == 0) {
-    if (same && c1 && wy == 4) k_fast_sweep<0, 4, 0, true><<<grid, b, 0, st>>>(a);
-    else if (same && c1 && wy == 3) k_fast_sweep<0, 3, 0, true><<<grid, b, 0, st>>>(a);
-    else if (same && c1 && wy == 5) k_fast_sweep<0, 5, 0, true><<<grid, b, 0, st>>>(a);
-    else if (c1) k_fast_sweep<0, 0, 0, true><<<grid, b, 0, st>>>(a);
-    else k_fast_sweep<0, 0, 0, false><<<grid, b, 0, st>>>(a);
+  if (mode <= 1 && a.tl) {  // the finest level on the two-level path
+    if (mode == 0) {
+      if (same && c1 && wy == 4) k_fast_sweep<0, 4, 0, true, true><<<grid, b, 0, st>>>(a);
+      else if (c1) k_fast_sweep<0, 0, 0, true, true><<<grid, b, 0, st>>>(a);
+      else k_fast_sweep<0, 0, 0, false, true><<<grid, b, 0, st>>>(a);
+    } else {
+      if (same && c1 && wy == 4 && wu == 5) k_fast_sweep<1, 4, 5, true, true><<<grid, b, 0, st>>>(a);
+      else if (c1) k_fast_sweep<1, 0, 0, true, true><<<grid, b, 0, st>>>(a);
+      else k_fast_sweep<1, 0, 0, false, true><<<grid, b, 0, st>>>(a);
+    }
+  } else if (mode == 0) {
+    if (same && c1 && wy == 4) k_fast_sweep<0, 4, 0, true, false><<<grid, b, 0, st>>>(a);
+    else if (same && c1 && wy == 3) k_fast_sweep<0, 3, 0, true, false><<<grid, b, 0, st>>>(a);
+    else if (same && c1 && wy == 5) k_fast_sweep<0, 5, 0, true, false><<<grid, b, 0, st>>>(a);
+    else if (c1) k_fast_sweep<0, 0, 0, true, false><<<grid, b, 0, st>>>(a);
+    else k_fast_sweep<0, 0, 0, false, false><<<grid, b, 0, st>>>(a);
   } else if (mode == 1) {
-    if (same && c1 && wy == 4 && wu == 5) k_fast_sweep<1, 4, 5, true><<<grid, b, 0, st>>>(a);
-    else if (same && c1 && wy == 3 && wu == 5) k_fast_sweep<1, 3, 5, true><<<grid, b, 0, st>>>(a);
-    else if (c1) k_fast_sweep<1, 0, 0, true><<<grid, b, 0, st>>>(a);
-    else k_fast_sweep<1, 0, 0, false><<<grid, b, 0, st>>>(a);
+    if (same && c1 && wy == 4 && wu == 5) k_fast_sweep<1, 4, 5, true, false><<<grid, b, 0, st>>>(a);
+    else if (same && c1 && wy == 3 && wu == 5) k_fast_sweep<1, 3, 5, true, false><<<grid, b, 0, st>>>(a);
+    else if (c1) k_fast_sweep<1, 0, 0, true, false><<<grid, b, 0, st>>>(a);
+    else k_fast_sweep<1, 0, 0, false, false><<<grid, b, 0, st>>>(a);
   } else if (mode == 2) {
-    if (c1) k_fast_sweep<2, 0, 0, true><<<grid, b, 0, st>>>(a);
-    else k_fast_sweep<2, 0, 0, false><<<grid, b, 0, st>>>(a);
+    if (c1) k_fast_sweep<2, 0, 0, true, false><<<grid, b, 0, st>>>(a);
+    else k_fast_sweep<2, 0, 0, false, false><<<grid, b, 0, st>>>(a);
   } else if (mode == 3) {
-    if (same && c1 && wy == 4 && wu == 5) k_fast_sweep<3, 4, 5, true><<<grid, b, 0, st>>>(a);
-    else if (c1) k_fast_sweep<3, 0, 0, true><<<grid, b, 0, st>>>(a);
-    else k_fast_sweep<3, 0, 0, false><<<grid, b, 0, st>>>(a);
+    if (same && c1 && wy == 4 && wu == 5) k_fast_sweep<3, 4, 5, true, false><<<grid, b, 0, st>>>(a);
+    else if (c1) k_fast_sweep<3, 0, 0, true, false><<<grid, b, 0, st>>>(a);
+    else k_fast_sweep<3, 0, 0, false, false><<<grid, b, 0, st>>>(a);
   } else {
-    if (c1) k_fast_sweep<4, 0, 0, true><<<grid, b, 0, st>>>(a);
-    else k_fast_sweep<4, 0, 0, false><<<grid, b, 0, st>>>(a);
+    if (c1) k_fast_sweep<4, 0, 0, true, false><<<grid, b, 0, st>>>(a);
+    else k_fast_sweep<4, 0, 0, false, false><<<grid, b, 0, st>>>(a);
   }
   launch_sweep_list(3, a, st);
   return true;
@@ -918,9 +946,16 @@ bool launch_residual_fast(const ResidArgs &a, cudaStream_t st) {
     return false;
   const dim3 grid = fast_grid(a.g), b(32, TY);
   const bool w4 = a.r_out.W == 4;
-  if (a.nterms == 4 && w4) k_fast_resid<4, 4><<<grid, b, 0, st>>>(a);
-  else if (a.nterms == 8 && w4) k_fast_resid<8, 4><<<grid, b, 0, st>>>(a);
-  else k_fast_resid<0, 0><<<grid, b, 0, st>>>(a);
+  if (a.tl) {  // the finest level on the two-level path
+    if (a.nterms == 4 && w4) k_fast_resid<4, 4, true><<<grid, b, 0, st>>>(a);
+    else k_fast_resid<0, 0, true><<<grid, b, 0, st>>>(a);
+  } else if (a.nterms == 4 && w4) {
+    k_fast_resid<4, 4, false><<<grid, b, 0, st>>>(a);
+  } else if (a.nterms == 8 && w4) {
+    k_fast_resid<8, 4, false><<<grid, b, 0, st>>>(a);
+  } else {
+    k_fast_resid<0, 0, false><<<grid, b, 0, st>>>(a);
+  }
   launch_residual_list(3, a, st);
   return true;
 }

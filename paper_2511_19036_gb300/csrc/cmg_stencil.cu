@@ -57,6 +57,7 @@ struct SmemT {
   V Fs[2][PLANE];           // in-plane operand, double-buffered
   V ring[4 * CRX];          // coarse ring of the operand's P_l t
   long long ringu[4 * CRX]; // coarse ring of P_l u^_(l-1)
+  Two2 two;                 // staging of a two-level operand temporary
 };
 using SmemTile = SmemT<long long>;
 union SmemAny {  // one shared buffer for either operand width
@@ -113,14 +114,18 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
   const int pb = g.n * g.nbx;  // blocks per plane (block indices fit in int)
   const bool rings = in.has_t || in.has_u;
   Stager st0 = make_stager(gc, T, tid), st1 = st0;
-  bool sov = false, sbad = false;  // two-level staging: range and invalid-code flags
+  bool sbad = false;  // two-level staging: an invalid code met
   auto load_t = [&](int c) {
-    if (in.t2) stage_load2<DIM>(st0, *in.t2, gc, c, sov, sbad);
+    if (in.t2) two_step_issue(st0, *in.t2, gc, T, c, sm.two, tid);
     else stage_load(st0, in.t, gc, c);
+  };
+  auto store_t = [&](int c) {
+    if (in.t2) two_step_store<DIM>(st0, *in.t2, gc, T, c, sm.two, sm.ring, in.G1t, tid, sbad);
+    else stage_store(st0, sm.ring, c, in.G1t, tid);
   };
   auto staging_flush = [&]() {
     if (in.t2) {
-      ovf_flush(sov, in.err, 121);
+      cp_async_wait_all();  // the step issued ahead past the tile's last plane
       corrupt_flush(sbad, in.err);
     }
   };
@@ -144,9 +149,10 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
 
   if (DIM == 2) {
     if (rings) {
-      if (in.has_t) load_t(0);
+      if (in.has_t && in.t2) two_prologue<DIM>(st0, *in.t2, gc, T, 0, 0, sm.two, sm.ring, in.G1t, tid, sbad);
+      else if (in.has_t) load_t(0);
       if (in.has_u) stage_load(st1, in.u, gc, 0);
-      if (in.has_t) stage_store(st0, sm.ring, 0, in.G1t, tid);
+      if (in.has_t && !in.t2) store_t(0);
       if (in.has_u) stage_store(st1, sm.ringu, 0, in.G1u, tid);
     }
     body.prefetch(0);
@@ -174,10 +180,12 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
   // 3-D: ring planes (k0 - 2)/2 .. k0/2 before the first decode
   int staged_hi = -2;
   if (rings) {
+    if (in.has_t && in.t2)
+      two_prologue<DIM>(st0, *in.t2, gc, T, (T.k0 - 2) >> 1, T.k0 >> 1, sm.two, sm.ring, in.G1t, tid, sbad);
     for (int c = (T.k0 - 2) >> 1; c <= (T.k0 >> 1); c++) {
-      if (in.has_t) load_t(c);
+      if (in.has_t && !in.t2) load_t(c);
       if (in.has_u) stage_load(st1, in.u, gc, c);
-      if (in.has_t) stage_store(st0, sm.ring, c, in.G1t, tid);
+      if (in.has_t && !in.t2) store_t(c);
       if (in.has_u) stage_store(st1, sm.ringu, c, in.G1u, tid);
     }
     staged_hi = T.k0 >> 1;
@@ -224,7 +232,7 @@ __device__ __forceinline__ void march(const Geo &g, const Geo &gc, const Tile &T
       body.out(k, (long long)S, (long long)s0, (long long)F0, pu_at(k));
     }
     if (stage) {
-      if (in.has_t) stage_store(st0, sm.ring, cs, in.G1t, tid);
+      if (in.has_t) store_t(cs);
       if (in.has_u) stage_store(st1, sm.ringu, cs, in.G1u, tid);
       staged_hi = cs;
     }

@@ -202,17 +202,150 @@ __device__ __forceinline__ void stage_load(Stager &s, const Tmp &t, const Geo &g
   }
 }
 
-// the same from a two-level temporary (x = s + P x_(l-2), see Tmp2): the value
-// and its grid as a descriptor with a nonzero bits field
-template <int DIM>
-__device__ __forceinline__ void stage_load2(Stager &s, const Tmp2 &t, const Geo &gc, int c, bool &ovf, bool &bad) {
-  s.v = 0;
-  s.gb = 0;
-  if (s.ok && (unsigned)c < (unsigned)gc.nz) {
-    int G;
-    s.v = tmp2_raw<DIM>(t, gc, s.ci, s.cj, c, G, ovf, bad);
-    s.gb = s.v ? (G << 8) | 1 : 0;
+// Two-level ring entries (x = s + P x_(l-2), see Tmp2).  A second, smaller
+// ring holds the level-(l-2) parents of the tile's level-(l-1) window (5 rows x
+// 11 columns per plane, 4 planes) on the ring's grid; a level-(l-1) entry is
+// then its section code plus one or two reads of that ring.  The global loads
+// of a staging step go into shared memory by cp.async one step ahead (two
+// buffers), so that two planes of compute hide their latency.  Steps are
+// consecutive level-(l-1) planes c; step c also stages level-(l-2) plane
+// (c + 1) / 2 exactly when c is odd (the first plane its successor needs).
+// The tile's footprint bounds put every part of an entry on or above the
+// ring's grid and within the ring's integer type, so the shifts are
+// unchecked; a parent on the ring's grid is even (its own grid is at least one
+// above), so the half sum of two is exact.
+constexpr int BR2 = 5, BX2 = 11, BRX2 = BR2 * BX2;
+
+struct Two2 {
+  unsigned e4[2][CRX], w0[2][CRX], w1[2][CRX];  // raw section words of the level-(l-1) entries
+  int par[CRX];                                 // each entry's parents in the level-(l-2) ring:
+                                                // in-plane offsets a | b << 8, odd in x or y << 16
+  long long bv[2][BRX2];                        // raw level-(l-2) values
+  int bg[2][BRX2];                              // and their block descriptors
+  long long rb[4 * BRX2];                       // the level-(l-2) ring, on the ring's grid
+};
+
+// the threads that stage the level-(l-2) ring: the last two warps, which
+// stage no level-(l-1) entry
+constexpr int TB0 = NT - 64;
+static_assert(CRX <= TB0 && BRX2 <= 64, "staging thread ranges");
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// level-(l-2) window origin of a tile: the lowest parent row / column of its
+// level-(l-1) window
+__device__ __forceinline__ int two_row0(const Tile &T) { return (T.cr0 >> 1) - 1; }
+__device__ __forceinline__ int two_col0(const Tile &T) { return (T.cx0 >> 1) - 1; }
+
+// issue the loads of level-(l-1) plane c (if lc) and of level-(l-2) plane p
+// (if lb) into buffer buf
+__device__ __forceinline__ void two_issue(const Stager &s, const Tmp2 &t, const Geo &gc, const Tile &T, bool lc,
+                                          int c, bool lb, int p, Two2 &sh, int tid, int buf) {
+  if (lc && s.ok && (unsigned)c < (unsigned)gc.nz) {
+    const int blk = c * gc.n * gc.nbx + s.bip;  // block counts of a level fit in int
+    // exponent arrays are allocated in whole 16-byte units, so the aligned word is inside
+    cp_async4(&sh.e4[buf][tid], t.s.exps + (blk & ~3));
+    const int W = t.s.W, pos = (s.ci & 31) * W;
+    const uint32_t *wp = t.s.words + (long long)blk * W + (pos >> 5);
+    cp_async4(&sh.w0[buf][tid], wp);
+    if ((pos & 31) + W > 32) cp_async4(&sh.w1[buf][tid], wp + 1);
   }
+  const int tb = tid - TB0;
+  if (lb && (unsigned)tb < (unsigned)BRX2) {
+    const Geo &g = t.gb;
+    const int bi = two_col0(T) + tb % BX2, bj = two_row0(T) + tb / BX2;
+    if (inside(g, bi, bj, p)) {
+      cp_async4(&sh.bg[buf][tb], t.b.gb + blk_index(g, bi, bj, p));
+      cp_async8(&sh.bv[buf][tb], t.b.v + ((long long)p * g.n + bj) * g.R + bi);
+    } else {
+      sh.bg[buf][tb] = 0;
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// level-(l-2) plane p (if lb) into its ring, and level-(l-1) plane c (if lc)
+// into the ring, from buffer buf (its parents' planes were stored by earlier
+// steps, before a CTA barrier); ahead: a later step's loads are in flight.
+// bad: the invalid code -2^(W-1)
+template <int DIM, class V>
+__device__ __forceinline__ void two_store(const Stager &s, const Tmp2 &t, const Geo &gc, const Tile &T, bool lc,
+                                          int c, bool lb, int p, Two2 &sh, V *ring, int G1, int tid, bool &bad,
+                                          int buf, bool ahead) {
+  if (ahead) asm volatile("cp.async.wait_group 1;" ::: "memory");
+  else cp_async_wait_all();
+  const int tb = tid - TB0;
+  if (lb && (unsigned)tb < (unsigned)BRX2) {
+    const int gbv = sh.bg[buf][tb];
+    sh.rb[(p & 3) * BRX2 + tb] = (gbv & 0xff) ? shl_fast(sh.bv[buf][tb], (gbv >> 8) - G1) : 0;
+  }
+  if (!lc || !s.on) return;
+  long long x = 0;
+  if (s.ok && (unsigned)c < (unsigned)gc.nz) {
+    const int blk = c * gc.n * gc.nbx + s.bip;
+    const int e = (int)(signed char)(sh.e4[buf][tid] >> (8 * (blk & 3)));
+    const int W = t.s.W, off = ((s.ci & 31) * W) & 31;
+    if (e != -128) {
+      const uint32_t bits = __funnelshift_r(sh.w0[buf][tid], off + W > 32 ? sh.w1[buf][tid] : 0u, off);
+      const int q = ((int)(bits << (32 - W))) >> (32 - W);
+      bad |= (unsigned)q == (0xffffffffu << (W - 1));
+      x = shl_fast(q, e - W + 1 - G1);
+    }
+    // P x_(l-2): parents (I -+ s)/2 of the 1-based node, in the level-(l-2) ring
+    const int par = sh.par[tid], K = c + 1, sz = DIM == 3 ? (K & 1) : 0;
+    const int ka = DIM == 3 ? ((K - sz) >> 1) - 1 : 0, kb = DIM == 3 ? ((K + sz) >> 1) - 1 : 0;
+    const long long pa = sh.rb[(ka & 3) * BRX2 + (par & 0xff)];
+    if ((par >> 16) | sz) x += (pa + sh.rb[(kb & 3) * BRX2 + ((par >> 8) & 0xff)]) >> 1;
+    else x += pa;
+  }
+  ring[(c & 3) * CRX + tid] = (V)x;
+}
+
+// The ring planes before the first decode: level-(l-1) planes c0 .. c1 and the
+// level-(l-2) planes their parents lie in (and the next one), the latter first
+// with a CTA barrier between; then the loads of the first step of the march
+// (plane c1 + 1) are issued.
+template <int DIM, class V>
+__device__ __forceinline__ void two_prologue(const Stager &s, const Tmp2 &t, const Geo &gc, const Tile &T, int c0,
+                                             int c1, Two2 &sh, V *ring, int G1, int tid, bool &bad) {
+  if (s.on && s.ok) {  // the entry's parents in the level-(l-2) ring (fixed per tile)
+    const int I = s.ci + 1, J = s.cj + 1, sx = I & 1, sy = J & 1;
+    const int r0 = two_row0(T), q0 = two_col0(T);
+    const int oa = (((J - sy) >> 1) - 1 - r0) * BX2 + ((I - sx) >> 1) - 1 - q0;
+    const int ob = (((J + sy) >> 1) - 1 - r0) * BX2 + ((I + sx) >> 1) - 1 - q0;
+    sh.par[tid] = oa | ob << 8 | (sx | sy) << 16;
+  }
+  const int p0 = DIM == 3 ? (c0 >> 1) - 1 : 0, p1 = DIM == 3 ? (c1 + 1) >> 1 : 0;
+  for (int p = p0; p <= p1; p++) {
+    two_issue(s, t, gc, T, false, 0, true, p, sh, tid, 0);
+    two_store<DIM>(s, t, gc, T, false, 0, true, p, sh, ring, G1, tid, bad, 0, false);
+  }
+  __syncthreads();
+  for (int c = c0; c <= c1; c++) {
+    two_issue(s, t, gc, T, true, c, false, 0, sh, tid, 0);
+    two_store<DIM>(s, t, gc, T, true, c, false, 0, sh, ring, G1, tid, bad, 0, false);
+  }
+  if (DIM == 3) two_issue(s, t, gc, T, true, c1 + 1, (c1 + 1) & 1, (c1 + 2) >> 1, sh, tid, (c1 + 1) & 1);
+}
+
+// one staging step of the march for level-(l-1) plane c: issue the next
+// step's loads (before the plane's compute) / store plane c (after it)
+__device__ __forceinline__ void two_step_issue(const Stager &s, const Tmp2 &t, const Geo &gc, const Tile &T, int c,
+                                               Two2 &sh, int tid) {
+  two_issue(s, t, gc, T, true, c + 1, (c + 1) & 1, (c + 2) >> 1, sh, tid, (c + 1) & 1);
+}
+template <int DIM, class V>
+__device__ __forceinline__ void two_step_store(const Stager &s, const Tmp2 &t, const Geo &gc, const Tile &T, int c,
+                                               Two2 &sh, V *ring, int G1, int tid, bool &bad) {
+  two_store<DIM>(s, t, gc, T, true, c, c & 1, (c + 1) >> 1, sh, ring, G1, tid, bad, c & 1, true);
 }
 
 // the staged value on the ring's grid G1 (a 32-bit ring only where the caller

@@ -3,11 +3,11 @@
 * The specialised 3-D kernels (cmg_fast.cu) and the generic kernels
   (cmg_stencil.cu), each on its own, give the oracle's sections bit for bit,
   for the red-black V(0,1) and the Jacobi V(2,2) cycles.
-* On the finest FMG level the level-(L-1) sources w and u^ are formed on the fly
-  from the level-(L-1) section and the level-(L-2) temporary (no int64 copy of
-  level L_max - 1): the solve still equals the oracle, and the report's
-  temporary bytes drop by two int64 arrays of level L_max - 1 against the
-  binary32 cycle, which keeps them.
+* On the finest FMG level the level-(L-1) sources w and u^ can be formed on the
+  fly from the level-(L-1) section and the level-(L-2) temporary (no int64
+  copy of level L_max - 1, cmg_set_two_level): the solve equals the oracle
+  with and without, the report's temporary bytes drop by those two int64
+  arrays, and the switch works between solves in both directions.
 * Operands whose footprints exceed the specialised kernels' 32-bit proofs send
   tiles to the generic kernels (the fallback list), and the result is
   unchanged.
@@ -34,17 +34,17 @@ def sections(s, cmg, L):
 
 
 @pytest.mark.parametrize("name,L,smoother", [("poisson3d_manufactured", 6, 1), ("poisson3d_fourier", 6, 0),
-                                             ("poisson3d_manufactured", 7, 1)])
+                                             ("poisson3d_manufactured", 7, 1), ("poisson2d_manufactured", 7, 0)])
 def test_fast_and_generic_kernels_agree_with_the_oracle(cmg, name, L, smoother):
     prob = P.make_problem(name, L)
     cfg = cmg.config_for(name, L, smoother=smoother)
     got = []
-    for fast in (True, False):
-        s = cmg.Solver(cfg, fast=fast)
+    for fast, two in ((True, True), (False, True), (True, False), (False, False)):
+        s = cmg.Solver(cfg, fast=fast, two_level=two)
         s.set_rhs(prob.tables, prob.scale_exp)
         s.fmg_solve()
         got.append((sections(s, cmg, L), s.decode_solution().cpu().numpy()))
-        if fast:
+        if fast and prob.dim == 3:
             st = s.fast_stats()
             assert st["top"]["ctas"] > 0  # the specialised kernels ran on the finest level
     o = oracle.Oracle.for_problem(prob, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1, nu2=cfg.nu2,
@@ -62,13 +62,31 @@ def test_two_level_path_drops_the_level_below_the_finest_temporaries(cmg):
     name, L = "poisson3d_fourier", 6
     prob = P.make_problem(name, L)
     rep = {}
-    for arith in (0, 1):
-        s = cmg.Solver(cmg.config_for(name, L, arith=arith))
+    for two in (True, False):
+        s = cmg.Solver(cmg.config_for(name, L), two_level=two)
         s.set_rhs(prob.tables, prob.scale_exp)
-        rep[arith] = s.fmg_solve()
+        rep[two] = s.fmg_solve()
+        secs = sections(s, cmg, L)
+        if two:
+            ref = secs
+        else:
+            assert all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(ref, secs))
     n = (1 << (L - 1)) - 1
     R = 32 * ((n + 31) // 32)
-    assert rep[1]["temp_bytes"] - rep[0]["temp_bytes"] == 2 * 8 * n * n * R
+    assert rep[False]["temp_bytes"] - rep[True]["temp_bytes"] == 2 * 8 * n * n * R
+    # switching between solves, both ways, on one context
+    s = cmg.Solver(cmg.config_for(name, L), two_level=True)
+    s.set_rhs(prob.tables, prob.scale_exp)
+    for two in (False, True, False):
+        s.set_two_level(two)
+        s.fmg_solve()
+        assert all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+                   for a, b in zip(ref, sections(s, cmg, L)))
+    # the binary32 cycle has no two-level path
+    f = cmg.Solver(cmg.config_for(name, L, arith=1))
+    with pytest.raises(cmg.CmgError) as ei:
+        f.set_two_level(True)
+    assert ei.value.status == cmg.EUNSUPPORTED
 
 
 def _rows(x, n, npts):
@@ -77,7 +95,8 @@ def _rows(x, n, npts):
     return rows.ravel()
 
 
-def test_wide_operands_take_the_fallback_tiles(cmg):
+@pytest.mark.parametrize("two", [True, False])
+def test_wide_operands_take_the_fallback_tiles(cmg, two):
     # a residual whose rows span 36 binary orders: |c rc| on the tile's finest
     # grid exceeds the red half-sweep's 32-bit proof on some tiles, which the
     # generic kernel then runs from the fallback list (red-black V(0,1), whose
@@ -85,7 +104,7 @@ def test_wide_operands_take_the_fallback_tiles(cmg):
     name, L = "poisson3d_manufactured", 6
     prob = P.make_problem(name, L)
     cfg = cmg.config_for(name, L, smoother=1)
-    s = cmg.Solver(cfg)
+    s = cmg.Solver(cfg, two_level=two)
     s.set_rhs(prob.tables, prob.scale_exp)
     o = oracle.Oracle.for_problem(prob, b1=cfg.b1, b2=cfg.b2, N=cfg.N_ir, nu1=cfg.nu1, nu2=cfg.nu2,
                                   omega=cfg.omega, smoother=1)
