@@ -159,7 +159,12 @@ cmg_status cmg_params_check(const cmg_params *p);
 cmg_status cmg_create(const cmg_params *p, void *cuda_stream, cmg_ctx **out);
 void cmg_destroy(cmg_ctx *ctx);
 const char *cmg_last_error(const cmg_ctx *ctx); /* never NULL */
-cmg_status cmg_set_timing(cmg_ctx *ctx, int enable); /* per-kernel CUDA events */
+/* Per-launch CUDA events on the context's stream, read by cmg_kernel_stats and
+ * the report: mode 0 none (the default), 1 around every launch, 2 around the
+ * launches on level L_max only (the dominant kernels; the events add a few
+ * microseconds per launch, which matters for small hierarchies).  CMG_EINVAL
+ * for another mode. */
+cmg_status cmg_set_timing(cmg_ctx *ctx, int mode);
 /* Specialised kernels (3-D exact path; on by default): the red half-sweep from
  * y~ = 0, the black half-sweep with the correction of u~ and the residual with
  * the restriction of t^_L run in kernels with 32-bit arithmetic where per-CTA
@@ -183,6 +188,25 @@ cmg_status cmg_fast_stats(cmg_ctx *ctx, int top, int64_t *ctas, int64_t *fallbac
  * per value).  Synchronises the stream; call it between solves.  EUNSUPPORTED
  * for other configurations (enable = 0 is then a no-op). */
 cmg_status cmg_set_two_level(cmg_ctx *ctx, int enable);
+/* The solve as one CUDA graph (on by default).  The host logic of cmg_fmg_solve
+ * depends only on the context's inputs and configuration, never on device
+ * data: after one eager solve of the current inputs, the next solve captures
+ * its whole launch sequence (kernels, memsets and, with timing, the event
+ * records) into a graph and launches it, and later solves launch that graph
+ * again, with the same kernels, arguments and results.  Any call that changes
+ * an input or the configuration drops the graph: the setters of timing, the
+ * specialised kernels and the two-level sources when they change the setting,
+ * cmg_set_rhs_separable unless the tables and scale are the same as before,
+ * cmg_set_coefficient / cmg_set_rhs_nodal when the pointer or scale changes
+ * (the graph reads borrowed arrays through their pointers, so new contents at
+ * the same address need no new graph), the step calls, cmg_set_section and
+ * cmg_state_load.  Not used on the legacy default stream (NULL), which cannot
+ * be captured; a capture that fails solves eagerly.  enable = 0 drops the
+ * graph and solves eagerly. */
+cmg_status cmg_set_graphs(cmg_ctx *ctx, int enable);
+/* Graphs captured, and solves run as a launch of the solve's graph (the
+ * capturing solve included), since cmg_create. */
+cmg_status cmg_graph_stats(const cmg_ctx *ctx, int64_t *captures, int64_t *graph_solves);
 
 /* Right-hand side (matrix-free, Sec. 5.1): F(x) = 2^scale_exp * sum_t prod_a
  * T[t][a][i_a], with T an int32 table [nterms][dim][2^L_max - 1] sampled at the
@@ -227,8 +251,9 @@ cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *report);
 
 /* Launch statistics of the last cmg_fmg_solve per kernel kind (CMG_KIND_*),
  * for launches on level L_max (top = 1) or on coarser levels (top = 0): total
- * device time (CUDA events on the context's stream; 0 unless cmg_set_timing
- * was enabled), number of launches and modelled algorithmic bytes. */
+ * device time (CUDA events on the context's stream; 0 for launches that
+ * cmg_set_timing leaves without events), number of launches and modelled
+ * algorithmic bytes. */
 cmg_status cmg_kernel_stats(cmg_ctx *ctx, int kind, int top, double *ms, int64_t *launches,
                             double *bytes);
 

@@ -73,6 +73,8 @@ _SIGS = {
     "cmg_set_timing": (_i32, [_vp, _i32]),
     "cmg_set_fast_kernels": (_i32, [_vp, _i32]),
     "cmg_set_two_level": (_i32, [_vp, _i32]),
+    "cmg_set_graphs": (_i32, [_vp, _i32]),
+    "cmg_graph_stats": (_i32, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "cmg_fast_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "cmg_set_rhs_separable": (_i32, [_vp, _i32, _vp, _i32]),
     "cmg_fmg_solve": (_i32, [_vp, ctypes.POINTER(Report)]),
@@ -189,7 +191,7 @@ class Solver:
     """Compact FMG context on the current CUDA device."""
 
     def __init__(self, cfg: SolverConfig, stream=None, timing: bool = False, fast: bool = True,
-                 two_level=None):
+                 two_level=None, graphs: bool = True):
         self.cfg = cfg
         self._p = to_params(cfg)
         self._stream = _stream_handle(stream)
@@ -199,11 +201,29 @@ class Solver:
             raise CmgError(st, "cmg_create")
         self._h = h
         if timing:
-            _lib.cmg_set_timing(self._h, 1)
+            self.set_timing(timing)
         if not fast:
             _lib.cmg_set_fast_kernels(self._h, 0)
         if two_level is not None:
             self.set_two_level(two_level)
+        if not graphs:
+            self.set_graphs(False)
+
+    def set_timing(self, timing):
+        """Per-launch CUDA events: False (none), True (every launch) or "top"
+        (launches on level L_max only, see cmg_set_timing)."""
+        mode = 2 if timing == "top" else (1 if timing else 0)
+        self._chk(_lib.cmg_set_timing(self._h, mode), "cmg_set_timing")
+
+    def set_graphs(self, enable: bool):
+        """Solve through a CUDA graph of the whole solve (see cmg_set_graphs)."""
+        self._chk(_lib.cmg_set_graphs(self._h, 1 if enable else 0), "cmg_set_graphs")
+
+    def graph_stats(self) -> dict:
+        """Graphs captured and solves run as a graph launch since the context was made."""
+        c, n = ctypes.c_int64(), ctypes.c_int64()
+        self._chk(_lib.cmg_graph_stats(self._h, ctypes.byref(c), ctypes.byref(n)), "cmg_graph_stats")
+        return {"captures": c.value, "graph_solves": n.value}
 
     def set_two_level(self, enable: bool):
         """Finest level's coarse sources formed on the fly (see cmg_set_two_level)."""

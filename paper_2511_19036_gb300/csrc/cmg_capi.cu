@@ -47,9 +47,31 @@ struct Level {
 
 struct KStat {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  bool borrowed = false;  // ev holds the events of the solve's CUDA graph (not ours to destroy)
   double bytes = 0;
   double ms = 0;
   long long launches = 0;
+};
+
+// The whole FMG solve as one CUDA graph.  The host logic of a solve depends only
+// on the context's inputs and configuration, never on device data, so a solve
+// captured once replays with the same kernels and arguments; the host state at
+// the end of the captured solve (buffer roles, widths, metadata slots, counters)
+// is put back before each launch of the graph.
+struct SolveGraph {
+  cudaGraphExec_t exec = nullptr;
+  bool capturing = false;
+  bool failed = false;  // a capture of the current inputs failed: solve eagerly
+  int warm = 0;         // eager solves of the current inputs
+  long long captures = 0, graph_solves = 0;
+  Level lv[MAXL + 1];
+  int L = 0, uh_upto = 0, meta_next = 1, fb_next = 0;
+  long long fast_ctas = 0, fast_ctas_top = 0, launches = 0;
+  double alg_bytes = 0;
+  std::vector<char> fb_top;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[CMG_KIND_COUNT][2];  // recorded by the graph
+  long long k_launches[CMG_KIND_COUNT][2] = {};
+  double k_bytes[CMG_KIND_COUNT][2] = {};
 };
 
 }  // namespace
@@ -74,7 +96,7 @@ struct cmg_ctx {
   bool tl = false, tl_capable = false;
   int c_num2 = 0, c_exp2 = 0;  // omega / (2d) = c_num2 2^c_exp2 (level-free part)
   std::string msg;
-  bool timing = false;
+  int timing = 0;  // per-launch CUDA events: 0 none, 1 every launch, 2 launches on level L_max only
   const float *kfield = nullptr;  // diffusion: borrowed nodal coefficient
   const double *grhs = nullptr;   // diffusion: borrowed nodal right-hand side, or null
   int grhs_log2 = 0;              // its power-of-two scale: f_L = h_L^d 2^grhs_log2 g
@@ -90,6 +112,8 @@ struct cmg_ctx {
   long long fast_ctas = 0, fast_ctas_top = 0;   // CTAs of specialised launches since cmg_start
   long long fb_done = 0, fb_done_top = 0;       // fallback tiles of slots already summed
   std::vector<char> fb_top;                     // slot on level L_max?
+  bool graphs = true;  // solve through a CUDA graph where the stream allows (cmg_set_graphs)
+  SolveGraph gr;
 };
 
 constexpr int FB_SLOTS = 4096;
@@ -183,21 +207,32 @@ static cmg_status launched(cmg_ctx *ctx, double bytes) {
 static double sec_bytes(const Geo &g, int W) { return (double)g.nblocks * (4.0 * W + 1.0); }
 static double tmp_bytes(const Geo &g) { return 8.0 * (double)g.nz * g.n * g.n; }
 
+// inside a capture the record becomes an event-record node of the graph
+static void ev_record(cmg_ctx *c, cudaEvent_t e) {
+  if (c->gr.capturing) cudaEventRecordWithFlags(e, c->st, cudaEventRecordExternal);
+  else cudaEventRecord(e, c->st);
+}
+
+// whether launches counted in k get events (stats[kind][1] holds the level-L_max launches)
+static bool ev_on(const cmg_ctx *c, const KStat &k) {
+  return c->timing == 1 || (c->timing == 2 && ((&k - &c->stats[0][0]) & 1) != 0);
+}
+
 static void ev_begin(cmg_ctx *c, KStat &k) {
-  if (!c->timing) return;
+  if (!ev_on(c, k)) return;
   if (k.ev.size() > 100000) return;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  cudaEventRecord(a, c->st);
+  ev_record(c, a);
   k.ev.push_back({a, b});
 }
 
 static void ev_end(cmg_ctx *c, KStat &k, double bytes) {
   k.launches++;
   k.bytes += bytes;
-  if (!c->timing || k.ev.empty() || k.ev.size() > 100000) return;
-  cudaEventRecord(k.ev.back().second, c->st);
+  if (!ev_on(c, k) || k.ev.empty() || k.ev.size() > 100000) return;
+  ev_record(c, k.ev.back().second);
 }
 
 // statistics slot of a kernel launch on level l
@@ -207,10 +242,13 @@ static void ev_collect(KStat &k) {
   for (auto &p : k.ev) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) k.ms += ms;
-    cudaEventDestroy(p.first);
-    cudaEventDestroy(p.second);
+    if (!k.borrowed) {
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
   }
   k.ev.clear();
+  k.borrowed = false;
 }
 
 static void stat_reset(KStat &k) {
@@ -218,6 +256,83 @@ static void stat_reset(KStat &k) {
   k.ms = 0;
   k.bytes = 0;
   k.launches = 0;
+}
+
+// ---------------------------------------------------------------- solve graph
+// Drops the captured graph (its events too) and the count of eager solves.  Every
+// launch of the graph has completed: cmg_fmg_solve synchronises before it returns.
+static void graph_drop(cmg_ctx *c) {
+  SolveGraph &g = c->gr;
+  for (int k = 0; k < CMG_KIND_COUNT; k++)
+    for (int t = 0; t < 2; t++) {
+      if (c->stats[k][t].borrowed) ev_collect(c->stats[k][t]);  // the last launch's times stay
+      for (auto &p : g.ev[k][t]) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+      }
+      g.ev[k][t].clear();
+    }
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  g.warm = 0;
+  g.failed = false;
+}
+
+// an input or the configuration of the solve changed: the graph no longer applies
+static void graph_touch(cmg_ctx *c) {
+  if (c->gr.exec || c->gr.warm || c->gr.failed) graph_drop(c);
+}
+
+// the legacy default stream cannot be captured
+static bool graph_usable(const cmg_ctx *c) {
+  return c->graphs && c->st != nullptr && c->st != cudaStreamLegacy && !c->gr.failed;
+}
+
+// the host state at the end of the captured solve, and its statistics
+static void graph_save(cmg_ctx *c) {
+  SolveGraph &g = c->gr;
+  for (int l = 0; l <= MAXL; l++) g.lv[l] = c->lv[l];
+  g.L = c->L;
+  g.uh_upto = c->uh_upto;
+  g.meta_next = c->meta_next;
+  g.fb_next = c->fb_next;
+  g.fb_top = c->fb_top;
+  g.fast_ctas = c->fast_ctas;
+  g.fast_ctas_top = c->fast_ctas_top;
+  g.launches = c->launches;
+  g.alg_bytes = c->alg_bytes;
+  for (int k = 0; k < CMG_KIND_COUNT; k++)
+    for (int t = 0; t < 2; t++) {
+      KStat &s = c->stats[k][t];
+      g.ev[k][t] = std::move(s.ev);
+      s.ev = g.ev[k][t];
+      s.borrowed = true;
+      g.k_launches[k][t] = s.launches;
+      g.k_bytes[k][t] = s.bytes;
+    }
+}
+
+static void graph_restore(cmg_ctx *c) {
+  const SolveGraph &g = c->gr;
+  for (int l = 0; l <= MAXL; l++) c->lv[l] = g.lv[l];
+  c->L = g.L;
+  c->uh_upto = g.uh_upto;
+  c->meta_next = g.meta_next;
+  c->fb_next = g.fb_next;
+  c->fb_top = g.fb_top;
+  c->fast_ctas = g.fast_ctas;
+  c->fast_ctas_top = g.fast_ctas_top;
+  c->fb_done = c->fb_done_top = 0;
+  c->launches = g.launches;
+  c->alg_bytes = g.alg_bytes;
+  for (int k = 0; k < CMG_KIND_COUNT; k++)
+    for (int t = 0; t < 2; t++) {
+      KStat &s = c->stats[k][t];
+      s.ev = g.ev[k][t];
+      s.borrowed = true;
+      s.launches = g.k_launches[k][t];
+      s.bytes = g.k_bytes[k][t];
+    }
 }
 
 // ---------------------------------------------------------------- validation
@@ -275,6 +390,7 @@ static void free_sec(SecBuf &b) {
 
 extern "C" void cmg_destroy(cmg_ctx *ctx) {
   if (!ctx) return;
+  graph_drop(ctx);
   for (int l = 1; l <= MAXL; l++) {
     Level &v = ctx->lv[l];
     free_sec(v.u);
@@ -387,15 +503,31 @@ extern "C" cmg_status cmg_create(const cmg_params *p, void *stream, cmg_ctx **ou
 
 extern "C" const char *cmg_last_error(const cmg_ctx *ctx) { return ctx ? ctx->msg.c_str() : "null context"; }
 
-extern "C" cmg_status cmg_set_timing(cmg_ctx *ctx, int enable) {
-  if (!ctx) return CMG_EINVAL;
-  ctx->timing = enable != 0;
+extern "C" cmg_status cmg_set_timing(cmg_ctx *ctx, int mode) {
+  if (!ctx || mode < 0 || mode > 2) return CMG_EINVAL;
+  if (ctx->timing != mode) graph_touch(ctx);
+  ctx->timing = mode;
   return CMG_OK;
 }
 
 extern "C" cmg_status cmg_set_fast_kernels(cmg_ctx *ctx, int enable) {
   if (!ctx) return CMG_EINVAL;
+  if (ctx->fast != (enable != 0)) graph_touch(ctx);
   ctx->fast = enable != 0;
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_set_graphs(cmg_ctx *ctx, int enable) {
+  if (!ctx) return CMG_EINVAL;
+  if (!enable) graph_drop(ctx);
+  ctx->graphs = enable != 0;
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_graph_stats(const cmg_ctx *ctx, int64_t *captures, int64_t *graph_solves) {
+  if (!ctx) return CMG_EINVAL;
+  if (captures) *captures = ctx->gr.captures;
+  if (graph_solves) *graph_solves = ctx->gr.graph_solves;
   return CMG_OK;
 }
 
@@ -436,6 +568,7 @@ extern "C" cmg_status cmg_set_two_level(cmg_ctx *ctx, int enable) {
     return fail(ctx, CMG_EUNSUPPORTED, "two-level sources need the exact Poisson path and L_max >= 3");
   if (on == ctx->tl) return CMG_OK;
   CU(cudaStreamSynchronize(ctx->st));  // no launch in flight reads the buffers
+  graph_touch(ctx);
   if (on) {
     free_top_temps(ctx);
   } else {
@@ -503,6 +636,7 @@ extern "C" cmg_status cmg_set_coefficient(cmg_ctx *ctx, const float *k_dev, int6
   if (ctx->P.coef != CMG_COEF_DIFFUSION) return fail(ctx, CMG_EINVAL, "coefficient on a Poisson context");
   const long long N = (1ll << ctx->P.L_max) + 1;
   if (n != (ctx->P.dim == 3 ? N * N * N : N * N)) return fail(ctx, CMG_EINVAL, "coefficient size");
+  if (k_dev != ctx->kfield) graph_touch(ctx);  // the graph reads the field through its pointer
   ctx->kfield = k_dev;
   if (!ctx->dbuf) {
     const Geo g = make_geo(ctx->P.dim, ctx->P.L_max);
@@ -518,6 +652,7 @@ extern "C" cmg_status cmg_set_rhs_nodal(cmg_ctx *ctx, const double *g_dev, int64
   const long long n1 = (1ll << ctx->P.L_max) - 1;
   if (n != (ctx->P.dim == 3 ? n1 * n1 * n1 : n1 * n1)) return fail(ctx, CMG_EINVAL, "right-hand side size");
   if (scale_log2 < -512 || scale_log2 > 512) return fail(ctx, CMG_EINVAL, "right-hand side scale 2^%d", scale_log2);
+  if (g_dev != ctx->grhs || scale_log2 != ctx->grhs_log2 || !ctx->have_rhs) graph_touch(ctx);
   ctx->grhs = g_dev;
   ctx->grhs_log2 = scale_log2;
   ctx->have_rhs = true;
@@ -563,6 +698,12 @@ extern "C" cmg_status cmg_set_rhs_separable(cmg_ctx *ctx, int nterms, const int3
   }
   int B = 0;
   for (unsigned __int128 t = bound; t; t >>= 1) B++;
+  // the graph of the solve holds the table pointer and values derived from the
+  // tables (the level-1 load): it stays only for the same tables
+  const bool same = ctx->have_rhs && !ctx->grhs && nterms == ctx->nterms && scale_exp == ctx->scale_exp &&
+                    ctx->tables_cap >= cnt && ctx->tables_host.size() == cnt &&
+                    std::equal(tab, tab + cnt, ctx->tables_host.begin());
+  if (!same) graph_touch(ctx);
   if (ctx->tables_cap < cnt) {  // the device buffer is kept across calls that fit in it
     cudaFree(ctx->tables);
     ctx->tables = nullptr;
@@ -1023,8 +1164,7 @@ static cmg_status need(cmg_ctx *ctx, bool cond, const char *what) {
   return cond ? CMG_OK : fail(ctx, CMG_EINVAL, "%s", what);
 }
 
-extern "C" cmg_status cmg_start(cmg_ctx *ctx) {
-  if (!ctx) return CMG_EINVAL;
+static cmg_status start_impl(cmg_ctx *ctx) {
   cmg_status s = need(ctx, ctx->have_rhs, "no right-hand side set");
   if (s) return s;
   ctx->meta_next = 1;
@@ -1047,8 +1187,13 @@ extern "C" cmg_status cmg_start(cmg_ctx *ctx) {
   return s;
 }
 
-extern "C" cmg_status cmg_prolongate(cmg_ctx *ctx) {
+extern "C" cmg_status cmg_start(cmg_ctx *ctx) {
   if (!ctx) return CMG_EINVAL;
+  graph_touch(ctx);
+  return start_impl(ctx);
+}
+
+static cmg_status prolongate_impl(cmg_ctx *ctx) {
   cmg_status s = need(ctx, ctx->L >= 1 && ctx->L < ctx->P.L_max, "cannot prolongate at this level");
   if (s) return s;
   const int L = ctx->L + 1;
@@ -1077,13 +1222,21 @@ extern "C" cmg_status cmg_prolongate(cmg_ctx *ctx) {
   return CMG_OK;
 }
 
+extern "C" cmg_status cmg_prolongate(cmg_ctx *ctx) {
+  if (!ctx) return CMG_EINVAL;
+  graph_touch(ctx);
+  return prolongate_impl(ctx);
+}
+
 extern "C" cmg_status cmg_residual(cmg_ctx *ctx) {
   if (!ctx || ctx->L < 1) return CMG_EINVAL;
+  graph_touch(ctx);
   return do_residual(ctx, false);
 }
 
 extern "C" cmg_status cmg_down(cmg_ctx *ctx, int l) {
   if (!ctx) return CMG_EINVAL;
+  graph_touch(ctx);
   cmg_status s = need(ctx, l >= 2 && l <= ctx->L, "bad level");
   if (s) return s;
   Level &v = LV(ctx, l);
@@ -1098,6 +1251,7 @@ extern "C" cmg_status cmg_down(cmg_ctx *ctx, int l) {
 
 extern "C" cmg_status cmg_coarse(cmg_ctx *ctx) {
   if (!ctx || ctx->L < 1) return CMG_EINVAL;
+  graph_touch(ctx);
   if (ctx->P.L_max == 1) return fail(ctx, CMG_EUNSUPPORTED, "cycle on a one-level hierarchy");
   return do_coarse(ctx, false, false);
 }
@@ -1117,6 +1271,7 @@ static cmg_status post_sweep(cmg_ctx *ctx, int l, SweepOpts o) {
 
 extern "C" cmg_status cmg_smooth(cmg_ctx *ctx, int l, int sweeps, int with_z) {
   if (!ctx) return CMG_EINVAL;
+  graph_touch(ctx);
   cmg_status s = need(ctx, l >= 2 && l <= ctx->L && sweeps >= 0 && (with_z == 0 || with_z == 1),
                       "bad level, sweep count or with_z");
   if (s) return s;
@@ -1141,6 +1296,7 @@ extern "C" cmg_status cmg_smooth(cmg_ctx *ctx, int l, int sweeps, int with_z) {
 
 extern "C" cmg_status cmg_restrict(cmg_ctx *ctx, int l) {
   if (!ctx) return CMG_EINVAL;
+  graph_touch(ctx);
   cmg_status s = need(ctx, l >= 2 && l <= ctx->L, "bad level");
   if (s) return s;
   if (ctx->P.nu1 == 0)
@@ -1150,6 +1306,7 @@ extern "C" cmg_status cmg_restrict(cmg_ctx *ctx, int l) {
 
 extern "C" cmg_status cmg_up(cmg_ctx *ctx, int l) {
   if (!ctx) return CMG_EINVAL;
+  graph_touch(ctx);
   cmg_status s = need(ctx, l >= 2 && l <= ctx->L, "bad level");
   if (s) return s;
   for (int k = 0; k < ctx->P.nu2; k++) {
@@ -1163,6 +1320,7 @@ extern "C" cmg_status cmg_up(cmg_ctx *ctx, int l) {
 
 extern "C" cmg_status cmg_correct(cmg_ctx *ctx) {
   if (!ctx || ctx->L < 1) return CMG_EINVAL;
+  graph_touch(ctx);
   cmg_status s;
   for (int l = 1; l <= ctx->L; l++) {
     Level &v = LV(ctx, l);
@@ -1186,6 +1344,7 @@ extern "C" cmg_status cmg_correct(cmg_ctx *ctx) {
 
 extern "C" cmg_status cmg_vcycle(cmg_ctx *ctx) {
   if (!ctx || ctx->L < 1) return CMG_EINVAL;
+  graph_touch(ctx);
   cmg_status s = CMG_OK;
   for (int l = ctx->L; l >= 2 && !s; l--) s = cmg_down(ctx, l);
   if (!s) s = cmg_coarse(ctx);
@@ -1240,6 +1399,7 @@ static cmg_status ir_fused(cmg_ctx *ctx, bool need_uh_top) {
 
 extern "C" cmg_status cmg_ir_iteration(cmg_ctx *ctx) {
   if (!ctx || ctx->L < 2) return ctx ? fail(ctx, CMG_EINVAL, "IR needs L >= 2") : CMG_EINVAL;
+  graph_touch(ctx);
   return ir_fused(ctx, need_uh_top(ctx));
 }
 
@@ -1256,6 +1416,57 @@ extern "C" cmg_status cmg_sync(cmg_ctx *ctx) {
   return CMG_OK;
 }
 
+// Algorithm 3: the FMG levels, each with N_ir iterations of refinement
+static cmg_status solve_body(cmg_ctx *ctx) {
+  cmg_status s = start_impl(ctx);
+  for (int L = 2; L <= ctx->P.L_max && !s; L++) {
+    s = prolongate_impl(ctx);
+    for (int it = 0; it < ctx->P.N_ir && !s; it++) s = ir_fused(ctx, it == ctx->P.N_ir - 1 && need_uh_top(ctx));
+  }
+  return s;
+}
+
+// Captures the solve into a graph and launches it.  Where the capture fails (a
+// call that cannot be captured, such as the synchronisation of an overflowing
+// fallback-count pool), nothing of it has run: the solve runs eagerly, and these
+// inputs are not captured again.
+static cmg_status graph_capture(cmg_ctx *ctx) {
+  SolveGraph &gr = ctx->gr;
+  CU(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeRelaxed));
+  gr.capturing = true;
+  cmg_status s = solve_body(ctx);
+  gr.capturing = false;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->st, &graph);
+  cudaGraphExec_t exec = nullptr;
+  if (!s && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (s || e != cudaSuccess) {
+    for (int k = 0; k < CMG_KIND_COUNT; k++) {  // events of the capture, never recorded
+      for (int t = 0; t < 2; t++) {
+        for (auto &p : ctx->stats[k][t].ev) {
+          cudaEventDestroy(p.first);
+          cudaEventDestroy(p.second);
+        }
+        ctx->stats[k][t].ev.clear();
+        ctx->stats[k][t].bytes = 0;
+        ctx->stats[k][t].launches = 0;
+      }
+    }
+    cudaGetLastError();
+    ctx->launches = 0;
+    ctx->alg_bytes = 0;
+    gr.failed = true;
+    return solve_body(ctx);  // also reports any error of the host logic itself
+  }
+  gr.exec = exec;
+  gr.captures++;
+  graph_save(ctx);
+  CU(cudaGraphLaunch(exec, ctx->st));
+  gr.graph_solves++;
+  return CMG_OK;
+}
+
 extern "C" cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *rep) {
   if (!ctx) return CMG_EINVAL;
   for (int k = 0; k < CMG_KIND_COUNT; k++) {
@@ -1268,10 +1479,19 @@ extern "C" cmg_status cmg_fmg_solve(cmg_ctx *ctx, cmg_report *rep) {
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   CU(cudaEventRecord(e0, ctx->st));
-  cmg_status s = cmg_start(ctx);
-  for (int L = 2; L <= ctx->P.L_max && !s; L++) {
-    s = cmg_prolongate(ctx);
-    for (int it = 0; it < ctx->P.N_ir && !s; it++) s = ir_fused(ctx, it == ctx->P.N_ir - 1 && need_uh_top(ctx));
+  // the first solve of new inputs runs eagerly, the second is captured, later
+  // ones launch the graph
+  cmg_status s = CMG_OK;
+  const bool usable = graph_usable(ctx);
+  if (usable && ctx->gr.exec) {
+    graph_restore(ctx);
+    CU(cudaGraphLaunch(ctx->gr.exec, ctx->st));
+    ctx->gr.graph_solves++;
+  } else if (usable && ctx->gr.warm > 0) {
+    s = graph_capture(ctx);
+  } else {
+    s = solve_body(ctx);
+    if (!s && usable) ctx->gr.warm++;
   }
   CU(cudaEventRecord(e1, ctx->st));
   cmg_status s2 = cmg_sync(ctx);
@@ -1363,6 +1583,7 @@ extern "C" cmg_status cmg_get_section(cmg_ctx *ctx, int which, int level, uint32
 extern "C" cmg_status cmg_set_section(cmg_ctx *ctx, int which, int level, int W, const uint32_t *words,
                                       const int8_t *exps) {
   if (!ctx || level < 1 || level > ctx->L || !words || !exps || W < 2 || W > 32) return CMG_EINVAL;
+  graph_touch(ctx);
   SecBuf *b = pick(ctx, which, level);
   if (!b) return CMG_EINVAL;
   const Geo &g = LV(ctx, level).g;
@@ -1462,6 +1683,7 @@ extern "C" cmg_status cmg_state_save(cmg_ctx *ctx, void *buf, size_t *len) {
 
 extern "C" cmg_status cmg_state_load(cmg_ctx *ctx, const void *buf, size_t len) {
   if (!ctx || !buf || len < sizeof(StateHeader)) return CMG_EINVAL;
+  graph_touch(ctx);
   StateHeader h;
   std::memcpy(&h, buf, sizeof h);
   if (std::memcmp(h.magic, "CMGSTAT1", 8) || std::memcmp(&h.P, &ctx->P, sizeof h.P) || h.L < 1 ||
