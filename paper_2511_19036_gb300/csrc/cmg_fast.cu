@@ -689,7 +689,9 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     return;
   }
   // the static bounds on t (|f| + |A F|) are loose by the smoothness of u; where they
-  // do not prove the range, every shifted value is checked (as the generic kernel does)
+  // do not prove the range, a bound from each block's largest |S| decides, and where
+  // that does not prove it either every shifted value is checked (as the generic
+  // kernel does)
   const bool fast = Mt - Gt <= 62, dfast = Mt - Gd <= 57;
   bool ovf = false, bad_exp = false;
   const int Wr = WR ? WR : a.r_out.W, Wt = a.Wt, Ws = a.u.W;
@@ -751,6 +753,16 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
 
   auto out_step = [&](int k, long long S) {
     if (!rowok) return;  // warp-uniform
+    // where the tile's static bound does not prove the range, the block's exact
+    // largest |S| (one warp reduction) bounds |A F| instead: |t| < 2^Mb
+    bool fst = fast, dfst = dfast;
+    if (!fast || !dfast) {  // CTA-uniform
+      const long long aS = pt ? (S < 0 ? -S : S) : 0;
+      const int sb = (int)__reduce_max_sync(FULL, (unsigned)(64 - __clzll(aS)));
+      const int Mb = imax(a.Gf + 51, GA + sb) + 1;
+      fst = fast || Mb - Gt <= 62;
+      dfst = dfast || Mb - Gd <= 57;
+    }
     long long t = 0;
     if (pt) {
       // F_q = sum_t (T_x T_y) T_z exactly: A 2^31 + B0 + B1, then f = RNE(F / 2^fsh)
@@ -778,7 +790,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
       const long long hi = A + (B0 >> 31) + (B1 >> 31) + (lo >> 31);
       lo &= 0x7fffffffll;
       const long long f = rne_hl(hi, lo, a.fsh);
-      if (fast) {
+      if (fst) {
         t = shl_fast(f, a.Gf - Gt) - shl_fast(S, GA - Gt);
       } else {
         t = shl_ck(f, a.Gf - Gt, ovf) - shl_ck(S, GA - Gt, ovf);
@@ -799,7 +811,7 @@ __global__ void __launch_bounds__(NT, CMG_FAST_RESID_MINB) k_fast_resid(ResidArg
     const int qt = enc_norm(ts, stk, bmax, dn, Gt, Wt, et, stt);
     // t^_L on Gd (R t^ is held on Gd - 1): q 2^(stt + Gt - Gd), or t itself when nothing dropped
     long long d = stt > 0 ? shl_fast((long long)qt, stt + Gt - Gd) : shl_fast(t, Gt - Gd);
-    if (!dfast) {  // |d| < 2^58 (a block with et - Gd > 58 has such a value, as in the generic check)
+    if (!dfst) {  // |d| < 2^58 (a block with et - Gd > 58 has such a value, as in the generic check)
       ck58(d, ovf);
       ovf |= et != -128 && et - Gd > 58;
     }
