@@ -298,6 +298,11 @@ cmg_status cmg_sync(cmg_ctx *ctx);
  * nblocks * W uint32 where W is cmg_section_width(); exps_host: nblocks int8;
  * both host memory of the caller, written before the call returns
  * (cmg_get_section takes words_host = NULL to read the exponents only).
+ * cmg_get_section writes page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister) that is 16-byte aligned with a copy kernel on the
+ * context's stream, through the GPU's mapping of the buffer (both ends of the
+ * range must be mapped), and other host memory with cudaMemcpy; the buffer
+ * must hold the sizes above either way.
  * cmg_set_section copies a caller's section in (for checkpoint restore and
  * step-wise checking); W must lie in 2..32 and not exceed the width the section
  * was allocated for.  Setting u~ invalidates the decoded u^ chain from that

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -1563,6 +1564,33 @@ extern "C" int cmg_section_width(const cmg_ctx *ctx, int which, int level) {
   return which == CMG_SEC_U ? Wu(ctx, level, L) : Wr(ctx, level, L);
 }
 
+// Device bytes into host memory.  Page-locked memory the GPU maps (the whole
+// range: both ends are checked) is written by a copy kernel through that
+// mapping on the context's stream; other host memory, or an unaligned buffer,
+// by cudaMemcpy.  The DMA copy of a large section straight after a solve ran at
+// a fraction of the link's rate on GB300, the kernel at the full rate.
+static cmg_status copy_out(cmg_ctx *ctx, void *dst, const void *src, size_t bytes) {
+  if (!bytes) return CMG_OK;
+  cudaPointerAttributes a0{}, a1{};
+  const bool mapped = cudaPointerGetAttributes(&a0, dst) == cudaSuccess && a0.type == cudaMemoryTypeHost &&
+                      a0.devicePointer &&
+                      cudaPointerGetAttributes(&a1, (const char *)dst + bytes - 1) == cudaSuccess &&
+                      a1.type == cudaMemoryTypeHost &&
+                      (const char *)a1.devicePointer == (const char *)a0.devicePointer + bytes - 1;
+  cudaGetLastError();  // an unregistered pointer is not an error here
+  if (mapped && ((uintptr_t)a0.devicePointer % 16) == 0 && ((uintptr_t)src % 16) == 0) {
+    int dev = 0, nsm = 1;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    launch_copy_out(src, a0.devicePointer, bytes, nsm, ctx->st);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(ctx->st));
+    return CMG_OK;
+  }
+  CU(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+  return CMG_OK;
+}
+
 extern "C" cmg_status cmg_get_section(cmg_ctx *ctx, int which, int level, uint32_t *words, int8_t *exps) {
   if (!ctx || level < 1 || level > ctx->L || !exps) return CMG_EINVAL;
   SecBuf *b = pick(ctx, which, level);
@@ -1575,9 +1603,9 @@ extern "C" cmg_status cmg_get_section(cmg_ctx *ctx, int which, int level, uint32
     if (words) std::memset(words, 0, (size_t)g.nblocks * Wr(ctx, level, ctx->L) * 4);
     return CMG_OK;
   }
-  CU(cudaMemcpy(exps, b->exps, (size_t)g.nblocks, cudaMemcpyDeviceToHost));
-  if (words) CU(cudaMemcpy(words, b->words, (size_t)g.nblocks * b->W * 4, cudaMemcpyDeviceToHost));
-  return CMG_OK;
+  cmg_status s2 = copy_out(ctx, exps, b->exps, (size_t)g.nblocks);
+  if (!s2 && words) s2 = copy_out(ctx, words, b->words, (size_t)g.nblocks * b->W * 4);
+  return s2;
 }
 
 extern "C" cmg_status cmg_set_section(cmg_ctx *ctx, int which, int level, int W, const uint32_t *words,

@@ -26,8 +26,10 @@
 //   k_repack    FMG level step: widen a section by appending zero bits
 //   k_chain, k_axpy, k_decode_solution: unfused pieces for step-wise use
 //   k_encode_f64, k_decode_f64: stand-alone codec
+//   k_copy_out  device bytes into page-locked host memory through its mapping
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "cmg_device.cuh"
@@ -486,6 +488,27 @@ void launch_encode_f64(const CodecArgs &a, cudaStream_t st) {
 
 void launch_decode_f64(const CodecArgs &a, cudaStream_t st) {
   k_decode_f64<<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
+}
+
+namespace {
+// Copy of device bytes into host memory the GPU maps (page-locked memory):
+// 16-byte words by a grid-stride loop, then the tail bytes.  src and dst are
+// 16-byte aligned.
+__global__ void k_copy_out(const uint4 *__restrict__ src, uint4 *__restrict__ dst, size_t n16,
+                           const unsigned char *__restrict__ tsrc, unsigned char *__restrict__ tdst, int ntail) {
+  const size_t step = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += step) dst[i] = src[i];
+  if (blockIdx.x == 0 && (int)threadIdx.x < ntail) tdst[threadIdx.x] = tsrc[threadIdx.x];
+}
+}  // namespace
+
+void launch_copy_out(const void *src, void *dst, size_t bytes, int nsm, cudaStream_t st) {
+  const size_t n16 = bytes / 16;
+  const int ntail = (int)(bytes - 16 * n16);
+  const size_t want = (n16 + 511) / 512;
+  const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>(want, (size_t)4 * nsm));
+  k_copy_out<<<blocks, 512, 0, st>>>((const uint4 *)src, (uint4 *)dst, n16, (const unsigned char *)src + 16 * n16,
+                                     (unsigned char *)dst + 16 * n16, ntail);
 }
 
 }  // namespace cmg

@@ -196,5 +196,8 @@ void launch_axpy(const AxpyArgs &a, cudaStream_t st);
 void launch_decode_solution(int dim, const DecodeSolArgs &a, cudaStream_t st);
 void launch_encode_f64(const CodecArgs &a, cudaStream_t st);
 void launch_decode_f64(const CodecArgs &a, cudaStream_t st);
+// bytes from device memory into page-locked host memory through the GPU's
+// mapping of it (dst: the device address of the host buffer; both 16-byte aligned)
+void launch_copy_out(const void *src, void *dst, size_t bytes, int nsm, cudaStream_t st);
 
 }  // namespace cmg
